@@ -1,0 +1,451 @@
+#!/usr/bin/env python
+"""Benchmark: dJFA vs JFA frames of a moving-seed Voronoi simulation on GB300.
+
+One step = one simulation timestep of the hot path on one 2048 x 2048 grid with
+16384 uniform seeds moving by uniform integers in [-2, 2] per axis: the seed
+move (Algorithm 1's SimulateParticles), the stamp and the dJFA passes of Eq. 4
+(6 passes, the first two Von Neumann).  The same trajectory is also run with a
+full JFA frame per step (11 passes, Eq. 2) for the speedup, and every 10th frame
+both are scored against each other (the paper's similarity, Section V-A) and
+against the exact diagram (distance-correct pixels).
+
+Printed: one JSON line (rank 0).  ``value`` is whole-job dJFA throughput in
+Gpixel-passes/s from CUDA events around each step (inputs resident in HBM, L2
+flushed between steps); ``e2e`` is the same metric through the Python/C API
+with host buffers (displacements in, label map out, every step).
+
+``--impl reference`` times the CPU oracle on the same workload instead.
+Under torchrun every rank runs an independent replica (its own seeds); there
+is no data-path collective.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Gpixel-passes/s and ms/frame, dJFA vs JFA at stated similarity; % of HBM peak"
+UNIT = "Gpixel-passes/s"
+FALLBACK_HBM_GBS = 6800.0
+L2_FLUSH_BYTES = 512 << 20
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="single2048")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0,
+                    help="bounded CPU-oracle sample for cpu_baseline")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", str(rank)))
+    return rank, world, local
+
+
+def workload(name):
+    from paper_2209_00117_gb300 import inputs
+
+    if name not in inputs.SINGLE:
+        raise SystemExit(f"unknown workload {name}; choose from {sorted(inputs.SINGLE)}")
+    w, h, s, steps, d = inputs.SINGLE[name]
+    return w, h, s, steps, d
+
+
+def config_dict(name, w, h, s, d, n_jfa, n_djfa, world, l2):
+    return {
+        "workload": f"{name}: {w}x{h} int32 label map, {s} uniform seeds, moves uniform in "
+                    f"[-{d},{d}] per axis, clamped; dJFA (Eq. 4) vs JFA (Eq. 2) per frame",
+        "grid": [w, h], "seeds": s, "max_disp": d,
+        "passes": {"jfa": n_jfa, "djfa": n_djfa, "djfa_von_neumann": 2},
+        "l2": l2,
+        "parallelism": "replicas" if world > 1 else "single",
+    }
+
+
+# ---------------------------------------------------------------------------
+# clocks
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.proc = None
+        self.dev = device_index
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "50", "-i", str(self.dev)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.1)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# roofline inputs
+# ---------------------------------------------------------------------------
+
+def hbm_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            v = float(json.load(f)["hbm_gbs"])
+        return v, "measured (MEASURED_PEAKS.json hbm_gbs, STREAM-style copy)"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback (6.8 TB/s, earlier GB300 copy measurement)"
+
+
+def kernel_source_hash():
+    p = os.path.join(ROOT, "paper_2209_00117_gb300", "csrc", "vd_kernels.cuh")
+    with open(p, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def recorded_traffic(kind, workload_name):
+    """DRAM bytes per launch of a kernel kind from the committed ncu summary
+    (profiles/traffic.txt), or None when absent or taken on other kernel source."""
+    p = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(p):
+        return None
+    cur = kernel_source_hash()
+    with open(p) as f:
+        for line in f:
+            t = line.split()
+            if len(t) >= 4 and not line.startswith("#") and t[0] == kind and t[1] == workload_name:
+                return float(t[2]) if t[3] == cur else None
+    return None
+
+
+# ---------------------------------------------------------------------------
+# the CPU oracle (baseline leg and reference arm)
+# ---------------------------------------------------------------------------
+
+def cpu_oracle_run(name, steps, seconds, seed=0, warmup=0):
+    """Times oracle dJFA steps on the host cores on the same trajectory; stops
+    after `steps` timed steps or `seconds` of timed work, whichever first."""
+    import oracle
+    from paper_2209_00117_gb300 import inputs
+
+    oracle.build()
+    w, h, s, _, d = workload(name)
+    xy = inputs.uniform_seeds(w, h, s, seed=seed)
+    total = warmup + steps
+    disp = inputs.displacements(s, d, total, seed=seed)
+    lab = oracle.jfa(w, h, xy)  # frame 0: the chain's start, untimed
+    n_pass = len(oracle.djfa_schedule(w, h, s, d, vn_waves=2))
+    done, t_acc = 0, 0.0
+    for i in range(total):
+        t0 = time.perf_counter()
+        xy = oracle.move(w, h, xy, disp[i])
+        lab = oracle.djfa_step(w, h, xy, lab, d_max=d, vn_waves=2)
+        dt = time.perf_counter() - t0
+        if i >= warmup:
+            done += 1
+            t_acc += dt
+            if t_acc >= seconds:
+                break
+    gpx = w * h * n_pass * done / t_acc / 1e9
+    return {"value": gpx, "unit": UNIT, "cores": oracle.get_threads(), "kind": "oracle",
+            "sample": f"{done} dJFA steps (move + stamp + {n_pass} passes) of the {name} trajectory "
+                      f"after an untimed JFA frame 0, plain C oracle with OpenMP",
+            "ms_per_step": 1e3 * t_acc / max(done, 1), "steps": done}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    w, h, s, _, d = workload(args.workload)
+    import oracle
+
+    res = cpu_oracle_run(args.workload, args.steps, float("inf"), seed=0, warmup=args.warmup)
+    n_jfa = len(oracle.jfa_schedule(w, h))
+    n_djfa = len(oracle.djfa_schedule(w, h, s, d, vn_waves=2))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": res["value"], "unit": UNIT,
+        "n_gpus": world, "steps": res["steps"], "warmup": args.warmup,
+        "ms_per_step": res["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": config_dict(args.workload, w, h, s, d, n_jfa, n_djfa, 1, "host memory"),
+        "cpu_baseline": {k: res[k] for k in ("value", "unit", "cores", "kind", "sample")},
+        "e2e": {"value": res["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# the GPU arm
+# ---------------------------------------------------------------------------
+
+def run_ours(args):
+    import torch
+
+    from paper_2209_00117_gb300 import build, inputs, vd
+
+    rank, world, local = dist_env()
+    build.build()
+    torch.cuda.set_device(local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+        pg = dist
+
+    def barrier():
+        if pg is not None:
+            pg.barrier()
+        torch.cuda.synchronize()
+
+    w, h, s, _, d = workload(args.workload)
+    K, W = args.steps, args.warmup
+    if W < 3:
+        raise SystemExit("--warmup must be >= 3")
+    total = W + K
+    seed = rank  # independent replica per rank
+    xy = inputs.uniform_seeds(w, h, s, seed=seed)
+    disp_host = inputs.displacements(s, d, total, seed=seed)
+    n_jfa = len(vd.jfa_schedule(w, h))
+    n_djfa = len(vd.djfa_schedule(w, h, s, d, vn_waves=2))
+    px = w * h
+
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    disp_dev = torch.from_numpy(disp_host).to(f"cuda:{local}")
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=f"cuda:{local}")
+    exact_dist = torch.empty((h, w), dtype=torch.int32, device=f"cuda:{local}")
+
+    dj = vd.VoronoiSim(w, h, s, stream=stream)
+    jf = vd.VoronoiSim(w, h, s, stream=stream)
+    for sim in (dj, jf):
+        sim.set_seeds(xy)
+        sim.set_option(vd.OPT_USE_GRAPHS, 1)
+    dj.jfa()  # frame 0 of the dJFA chain
+
+    def djfa_step(i):
+        dj.move(disp_dev[i])
+        dj.djfa_step(d_max=d, vn_waves=2)
+
+    def jfa_step(i):
+        jf.move(disp_dev[i])
+        jf.jfa()
+
+    for i in range(W):
+        djfa_step(i)
+        jfa_step(i)
+    torch.cuda.synchronize()
+
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(K)]
+    sims = []
+    sampler = ClockSampler(local)
+    sampler.start()
+    barrier()
+    l0 = dj.launches + jf.launches
+    t0 = time.perf_counter()
+    for j in range(K):
+        i = W + j
+        flush.zero_()
+        ev[j][0].record(stream)
+        djfa_step(i)
+        ev[j][1].record(stream)
+        flush.zero_()
+        ev[j][2].record(stream)
+        jfa_step(i)
+        ev[j][3].record(stream)
+        if (j + 1) % 10 == 0 or j == K - 1:
+            # scored between steps, outside the step events
+            dj.exact(None, exact_dist)
+            ne_d, nm = dj.similarity(exact_dist=exact_dist, ref_labels=None)
+            nm = dj.match_count(jf)
+            ne_j, _ = jf.similarity(exact_dist=exact_dist)
+            sims.append((j + 1, nm, ne_d, ne_j))
+    barrier()
+    wall = time.perf_counter() - t0
+    clocks = sampler.stop()
+    launches = dj.launches + jf.launches - l0
+    t_djfa = sum(e[0].elapsed_time(e[1]) for e in ev)  # ms
+    t_jfa = sum(e[2].elapsed_time(e[3]) for e in ev)
+
+    def max_over_ranks(v):
+        if pg is None:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device=f"cuda:{local}")
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        return float(t.item())
+
+    t_djfa_max = max_over_ranks(t_djfa)
+    t_jfa_max = max_over_ranks(t_jfa)
+    units = px * n_djfa * K * world
+    value = units / (t_djfa_max * 1e-3) / 1e9
+    jfa_value = px * n_jfa * K * world / (t_jfa_max * 1e-3) / 1e9
+
+    # --- per-kernel timing for the roofline: the same trajectory replayed with
+    #     events around every launch (eager launches, L2 flushed between steps)
+    pr = vd.VoronoiSim(w, h, s, stream=stream)
+    pr.set_seeds(xy)
+    pr.jfa()
+    for i in range(W):
+        pr.move(disp_dev[i])
+        pr.djfa_step(d_max=d, vn_waves=2)
+    pr.set_option(vd.OPT_PROFILE, 1)
+    pr.profile_reset()
+    for j in range(K):
+        flush.zero_()
+        pr.move(disp_dev[W + j])
+        pr.djfa_step(d_max=d, vn_waves=2)
+    prof = pr.profile()
+    pr.close()
+    dom = max(prof, key=lambda k: prof[k]["ms"])
+    pd = prof[dom]
+    avg_ms = pd["ms"] / max(pd["launches"], 1)
+    if dom in ("pass", "fused"):
+        alg_bytes = 8.0 * px + 8.0 * s  # read + write one int32 per pixel, the seed table once
+    elif dom == "fill":
+        alg_bytes = 4.0 * px
+    else:
+        alg_bytes = 16.0 * s
+    peak, peak_src = hbm_peak()
+    achieved = alg_bytes / (avg_ms * 1e-3) / 1e9
+    tot_ms = sum(v["ms"] for v in prof.values())
+    roofline = {
+        "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+        "traffic": recorded_traffic(dom, args.workload),
+        "kernel": dom, "alg_bytes_per_launch": alg_bytes, "avg_launch_us": avg_ms * 1e3,
+        "peak_source": peak_src,
+        "share": {k: round(v["ms"] / tot_ms, 4) for k, v in prof.items() if tot_ms > 0},
+        "measured": "CUDA events around every launch on its stream over K replayed dJFA steps",
+    }
+
+    # --- end to end through the API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        ee = vd.VoronoiSim(w, h, s, stream=stream)
+        ee.set_seeds(xy)
+        ee.set_option(vd.OPT_USE_GRAPHS, 1)
+        ee.jfa()
+        pin_disp = torch.from_numpy(disp_host).pin_memory()
+        pin_out = torch.empty((h, w), dtype=torch.int32).pin_memory()
+        for i in range(W):
+            ee.move(pin_disp[i])
+            ee.djfa_step(d_max=d, vn_waves=2)
+            ee.labels(out=pin_out)
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for j in range(K):
+            ee.move(pin_disp[W + j])
+            ee.djfa_step(d_max=d, vn_waves=2)
+            ee.labels(out=pin_out)
+        e1.record(stream)
+        barrier()
+        te = max_over_ranks(e0.elapsed_time(e1))
+        ee.close()
+        e2e = {"value": px * n_djfa * K * world / (te * 1e-3) / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": int(s * 2 * 4), "d2h_bytes_per_step": int(px * 4),
+               "ms_per_step": te / K}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        res = cpu_oracle_run(args.workload, K, args.cpu_seconds, seed=0)
+        cpu = {k: res[k] for k in ("value", "unit", "cores", "kind", "sample")}
+
+    last = sims[-1] if sims else (0, 0, 0, 0)
+    similarity = {
+        "frames_scored": [f for f, *_ in sims],
+        "djfa_vs_jfa_pct": [round(100.0 * nm / px, 4) for _, nm, _, _ in sims],
+        "djfa_exact_pct": [round(100.0 * ne / px, 4) for _, _, ne, _ in sims],
+        "jfa_exact_pct": [round(100.0 * ne / px, 4) for _, _, _, ne in sims],
+        "last_counts": {"frame": last[0], "pixels": px, "djfa_match_jfa": last[1],
+                        "djfa_distance_correct": last[2], "jfa_distance_correct": last[3]},
+    }
+    dj.close()
+    jf.close()
+    if rank != 0:
+        return 0
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+        "ms_per_step": t_djfa_max / K, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": config_dict(args.workload, w, h, s, d, n_jfa, n_djfa, world,
+                              f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MB write, outside the step events)"),
+        "ms_per_frame": {"djfa": t_djfa_max / K, "jfa": t_jfa_max / K},
+        "jfa": {"value": jfa_value, "unit": UNIT, "ms_per_step": t_jfa_max / K},
+        "speedup_djfa_vs_jfa": t_jfa_max / t_djfa_max,
+        "similarity": similarity,
+        "roofline": roofline,
+        "e2e": e2e,
+        "cpu_baseline": cpu,
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+        "wall_s_timed_region": wall,
+    }
+    print(json.dumps(line))
+    if pg is not None:
+        pg.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,257 @@
+/*
+ * vd.h -- C ABI of the GB300 (sm_103a) dynamic Voronoi diagram library.
+ *
+ * The library computes discrete 2D Voronoi diagrams (a nearest-seed index per
+ * pixel) with the Jump Flooding Algorithm (JFA) and with the dynamic JFA
+ * (dJFA) of "GPU Voronoi Diagrams for Random Moving Seeds" (Stevenson-Regla
+ * and Navarro), every step of which runs in this library's own CUDA kernels.
+ *
+ * Conventions for every call below:
+ *   - Coordinates and sizes are int32.  A grid is w columns by h rows,
+ *     1 <= w, h <= VD_MAX_SIDE; pixel (x, y) of a dense caller map is element
+ *     y * w + x (row-major, no padding).
+ *   - Seeds are int32 (x, y) pairs, seed k at xy[2k], xy[2k + 1], with
+ *     0 <= x < w and 0 <= y < h.  Seed indices are the labels.
+ *   - Label -1 means "no seed".  Distances are exact integers: squared
+ *     Euclidean (VD_METRIC_EUCLID) or Manhattan (VD_METRIC_MANHATTAN); among
+ *     equal distances the lowest seed index wins, so every result is unique
+ *     and bit-reproducible.
+ *   - A pointer flagged `on_device` is a CUDA device pointer of the current
+ *     device; otherwise it is host memory.  The caller keeps ownership of
+ *     every buffer it passes; the library copies what it needs.  Host sources
+ *     follow cudaMemcpyAsync rules: pageable memory may be reused when the
+ *     call returns, page-locked memory once the stream has passed the call
+ *     (vd_synchronize).  Calls that write to host memory synchronise the
+ *     context's stream before returning.
+ *   - Work is queued on the context's stream (vd_set_stream) and runs
+ *     asynchronously.  A context is not thread-safe.
+ *   - Every int-returning call returns VD_OK (0) or a negative VD_E* code and
+ *     then leaves a message for vd_last_error() (per host thread).  A CUDA
+ *     launch or copy error returns VD_ECUDA; the context should then be
+ *     destroyed.
+ */
+#ifndef VD_H_
+#define VD_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define VD_OK 0
+#define VD_EINVAL (-1)   /* bad argument: null handle, size or coordinate out of range */
+#define VD_ENOMEM (-2)   /* device allocation failed */
+#define VD_ECUDA (-3)    /* a CUDA runtime call or kernel launch failed */
+#define VD_ETIMEOUT (-4) /* a bounded wait in a persistent kernel expired */
+#define VD_EBUSY (-5)    /* resource exhausted (serving: no slot or budget) */
+#define VD_ENOTFOUND (-6) /* unknown id (serving) */
+
+#define VD_METRIC_EUCLID 0
+#define VD_METRIC_MANHATTAN 1
+#define VD_NB_MOORE 0
+#define VD_NB_VON_NEUMANN 1
+
+#define VD_MAX_SIDE 32768
+#define VD_MAX_PASSES 64
+
+/* Message of the last failing call on this host thread ("" if none). */
+const char* vd_last_error(void);
+
+/* ABI version of this header (increments on any incompatible change). */
+int vd_abi_version(void);
+
+/* ------------------------------------------------------------------------ */
+/* Schedules (host arithmetic, no GPU needed)                               */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * JFA step lengths, Eq. 2 (Section III): k_1 = 2^(ceil(log2 N) - 1) with
+ * N = max(w, h), then k_1/2, ..., 1 (log2(k_1) + 1 passes; none when N = 1),
+ * followed by `extra_passes` passes: 1 -> (1) [JFA+1], 2 -> (2, 1) [JFA+2].
+ * Writes up to `cap` entries to ks (step lengths) and nbs (VD_NB_* per pass;
+ * all Moore, Table I).  Returns the full pass count (may exceed cap), or
+ * VD_EINVAL for bad sizes, extra_passes outside [0, 2] or null arrays with
+ * cap > 0.
+ */
+int vd_jfa_schedule(int32_t w, int32_t h, int32_t extra_passes, int32_t* ks, int32_t* nbs,
+                    int32_t cap);
+
+/*
+ * dJFA step lengths, Eq. 3-4 (Section IV-A): delta_1 = 2^ceil(log2(max(
+ * 2 L_avg, d_max))) with L_avg = sqrt(w h / s), decided in exact integers
+ * (the least P = 2^e with P^2 s >= 4 w h and P >= d_max), capped at JFA's
+ * k_1 (Algorithm 1's k_m).  Passes delta_1, ..., 1 (log2(delta_1) + 1), the
+ * first `vn_waves` with the Von Neumann neighbourhood and the rest Moore
+ * (Section IV-B), then `extra_passes` as in vd_jfa_schedule (the optional
+ * extra step after Eq. 4).  Same output and errors as vd_jfa_schedule;
+ * vn_waves must be >= 0.
+ */
+int vd_djfa_schedule(int32_t w, int32_t h, int64_t n_seeds, int32_t d_max, int32_t vn_waves,
+                     int32_t extra_passes, int32_t* ks, int32_t* nbs, int32_t cap);
+
+/* ------------------------------------------------------------------------ */
+/* One simulation                                                            */
+/* ------------------------------------------------------------------------ */
+
+typedef struct vd_ctx vd_ctx;
+
+/*
+ * Creates a simulation on the current CUDA device: a w x h label map (two
+ * device buffers for the Jacobi passes, rows padded to 128 bytes, the
+ * padding held at -1), n_seeds seeds (all at (0, 0) until vd_set_seeds) and
+ * small scratch buffers.  Labels start at -1.  The stream is the legacy
+ * default stream until vd_set_stream.  Returns NULL on bad sizes (w, h
+ * outside [1, VD_MAX_SIDE], n_seeds < 1) or allocation failure
+ * (vd_last_error() says which).
+ */
+vd_ctx* vd_create(int32_t grid_w, int32_t grid_h, int32_t n_seeds);
+
+/* Frees every device buffer of the context after its stream is idle.
+ * NULL is accepted (VD_OK). */
+int vd_destroy(vd_ctx* ctx);
+
+/* Queues all later work of the context on `cuda_stream` (a cudaStream_t;
+ * NULL = legacy default stream).  The caller keeps the stream alive. */
+int vd_set_stream(vd_ctx* ctx, void* cuda_stream);
+
+/* Blocks until all queued work of the context has finished. */
+int vd_synchronize(vd_ctx* ctx);
+
+/* Grid and seed sizes of a context (any output pointer may be NULL). */
+int vd_get_shape(const vd_ctx* ctx, int32_t* w, int32_t* h, int32_t* n_seeds,
+                 int32_t* row_pitch);
+
+/*
+ * Replaces the seed positions with n_seeds (x, y) pairs (Section II, the set
+ * S).  VD_EINVAL if any coordinate lies outside the grid (checked on the
+ * host for host input, on the device for device input, where the check
+ * costs a synchronisation).
+ */
+int vd_set_seeds(vd_ctx* ctx, const int32_t* xy, int on_device);
+
+/* Copies the current seed positions out (n_seeds pairs). */
+int vd_get_seeds(vd_ctx* ctx, int32_t* xy, int on_device);
+
+/*
+ * SimulateParticles of Algorithm 1 under the uniform random model of
+ * Section IV-A: every seed k moves to clamp(p_k + delta_k) with the clamp
+ * keeping it on the grid.  If dxy is non-NULL it holds n_seeds integer
+ * displacement pairs (host or device per dxy_on_device; max_disp, rng_seed,
+ * stream_id and step are then ignored).  If dxy is NULL, each displacement
+ * component is drawn on the device as u - max_disp, u uniform in
+ * [0, 2 max_disp] from SplitMix64 (Steele, Lea, Flood 2014): key =
+ * splitmix64(rng_seed, stream_id), draw = splitmix64(key, step * 2^33 + 2k +
+ * axis), u = ((draw >> 32) * (2 max_disp + 1)) >> 32, where splitmix64(s, n)
+ * is the n-th output of the generator started at state s.  VD_EINVAL if
+ * max_disp < 0 or > VD_MAX_SIDE (RNG mode) or step < 0.
+ */
+int vd_move_seeds(vd_ctx* ctx, const int32_t* dxy, int dxy_on_device, int32_t max_disp,
+                  uint64_t rng_seed, uint64_t stream_id, int64_t step);
+
+/*
+ * A full JFA frame (Section III): empties the map (-1), stamps the seeds
+ * (each seed pixel gets the lowest index standing on it) and runs the passes
+ * of vd_jfa_schedule with the Moore neighbourhood of Table I.  Each pass is
+ * a gather: pixel q keeps, among itself and its in-grid neighbours at
+ * offset k that hold a label, the seed nearest to q (lowest index on ties),
+ * reading one buffer and writing the other.  VD_EINVAL for a bad metric or
+ * extra_passes outside [0, 2].
+ */
+int vd_jfa(vd_ctx* ctx, int32_t extra_passes, int32_t metric);
+
+/*
+ * One dJFA frame (Section IV, Algorithm 1 after SimulateParticles): stamps
+ * the current seeds onto the previous frame's map without clearing it, then
+ * runs the passes of vd_djfa_schedule(w, h, n_seeds, d_max, vn_waves,
+ * extra_passes).  d_max is the per-step move bound of Section IV-A (the
+ * Chebyshev bound of the moves, e.g. max_disp).  VD_EINVAL for d_max < 0,
+ * vn_waves < 0, bad metric or extra_passes outside [0, 2].
+ */
+int vd_djfa_step(vd_ctx* ctx, int32_t d_max, int32_t vn_waves, int32_t extra_passes,
+                 int32_t metric);
+
+/* The stamp alone (part of vd_jfa / vd_djfa_step): every seed pixel of the
+ * current map gets the lowest index among the seeds standing on it. */
+int vd_stamp(vd_ctx* ctx);
+
+/* One jump pass with step k >= 1 and neighbourhood nb (Table I / Section
+ * IV-B), as inside vd_jfa; exposed for tests and diagnostics. */
+int vd_pass(vd_ctx* ctx, int32_t k, int32_t nb, int32_t metric);
+
+/* Overwrites the label map with a dense w x h map (labels in [-1, n_seeds)). */
+int vd_set_labels(vd_ctx* ctx, const int32_t* labels, int on_device);
+
+/* Copies the label map out as a dense w x h map. */
+int vd_get_labels(vd_ctx* ctx, int32_t* labels, int on_device);
+
+/*
+ * Borrowed device pointer to the current label map (row pitch in elements
+ * via vd_get_shape); valid until the next call on the context.
+ */
+int vd_labels_device_ptr(vd_ctx* ctx, const int32_t** labels);
+
+/*
+ * Similarity counts of Section V-A for the current map against optional
+ * dense references (host or device per on_device):
+ *   n_match = #pixels whose label equals ref_labels (the paper's similarity
+ *             is 100 n_match / (w h) against a same-frame JFA);
+ *   n_exact = #pixels whose label's seed is at distance exact_dist from the
+ *             pixel, exact_dist being the exact minimum distance of Eq. 1 in
+ *             `metric` (the distance-correct count).
+ * A NULL reference gives a count of 0.  Synchronises (results on the host).
+ */
+int vd_similarity(vd_ctx* ctx, const int32_t* exact_dist, const int32_t* ref_labels,
+                  int on_device, int32_t metric, uint64_t* n_exact, uint64_t* n_match);
+
+/* n_match of the current maps of two contexts of the same grid size. */
+int vd_similarity_ctx(vd_ctx* ctx, vd_ctx* ref, uint64_t* n_match);
+
+/*
+ * The exact diagram of Eq. 1 on the device: for every pixel the lowest seed
+ * index at the minimum distance (labels) and that distance (dist), each
+ * written as a dense w x h map when non-NULL (host or device per on_device).
+ * Exact by construction (a uniform bucket grid searched ring by ring until
+ * no unvisited bucket can hold a seed at distance <= the best).  Does not
+ * touch the context's label map.
+ */
+int vd_exact(vd_ctx* ctx, int32_t* labels, int32_t* dist, int on_device, int32_t metric);
+
+/* Tuning and execution options (vd_set_option); values are validated. */
+#define VD_OPT_FUSE_MAX_K 1      /* largest step fused into shared-memory groups (0 = no fusion; 1..16) */
+#define VD_OPT_BAND_ORDER_MIN_K 2 /* step from which large-k passes visit rows in k-strided bands (0 = never) */
+#define VD_OPT_USE_GRAPHS 3      /* 1 = replay each frame's launches as a cached CUDA graph */
+#define VD_OPT_FUSE_TILE_X 4     /* fused-group tile width in pixels (multiple of 4, 16..256) */
+#define VD_OPT_FUSE_TILE_Y 5     /* fused-group tile height in pixels (1..128) */
+#define VD_OPT_PROFILE 6         /* 1 = bracket every kernel launch with CUDA events (frames then run
+                                    eagerly, never from a graph); read with vd_profile_read */
+int vd_set_option(vd_ctx* ctx, int32_t option, int64_t value);
+int vd_get_option(const vd_ctx* ctx, int32_t option, int64_t* value);
+
+/* Kernel kinds reported by vd_profile_read. */
+#define VD_KERNEL_PASS 0   /* one jump pass over the map (units: pixel-passes) */
+#define VD_KERNEL_FUSED 1  /* a shared-memory group of small-step passes (units: pixel-passes) */
+#define VD_KERNEL_STAMP 2  /* stamp halves (units: seeds) */
+#define VD_KERNEL_MOVE 3   /* seed move (units: seeds) */
+#define VD_KERNEL_FILL 4   /* map fill (units: pixels) */
+#define VD_KERNEL_KINDS 5
+
+/*
+ * Profiling counters (VD_OPT_PROFILE = 1): synchronises the context's stream,
+ * then adds up, per kernel kind, the GPU time between the events recorded
+ * around each launch since the last vd_profile_reset.  Outputs (arrays of
+ * VD_KERNEL_KINDS entries, any may be NULL): total milliseconds, launches and
+ * work units.  VD_EINVAL if profiling is off.
+ */
+int vd_profile_read(vd_ctx* ctx, double* total_ms, int64_t* launches, int64_t* units);
+int vd_profile_reset(vd_ctx* ctx);
+
+/* Kernel launches issued by this context since creation (for accounting). */
+int64_t vd_launch_count(const vd_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VD_H_ */

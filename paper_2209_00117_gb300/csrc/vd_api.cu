@@ -1,0 +1,942 @@
+// vd_api.cu -- the C ABI of include/vd.h for one simulation: context state,
+// schedules (Eq. 2, Eq. 3-4), launch planning of the jump passes, copies and
+// error reporting.  All pixel work runs in the kernels of vd_kernels.cuh.
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "vd.h"
+#include "vd_internal.h"
+#include "vd_kernels.cuh"
+
+namespace {
+
+thread_local std::string g_error;
+
+}  // namespace
+
+int vd_fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_error = buf;
+  return code;
+}
+
+int vd_cuda_check(cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return VD_OK;
+  return vd_fail(e == cudaErrorMemoryAllocation ? VD_ENOMEM : VD_ECUDA, "%s: %s", what,
+                 cudaGetErrorString(e));
+}
+
+extern "C" const char* vd_last_error(void) { return g_error.c_str(); }
+
+extern "C" int vd_abi_version(void) { return 1; }
+
+// ---------------------------------------------------------------------------
+// Schedules
+// ---------------------------------------------------------------------------
+
+namespace vdi {
+
+int ceil_log2(int64_t v) {
+  int e = 0;
+  while ((int64_t{1} << e) < v) ++e;
+  return e;
+}
+
+// Eq. 2: k_1 = 2^(ceil(log2 N) - 1), N = max(w, h); 0 when N = 1 (no pass).
+int32_t jfa_first_step(int32_t w, int32_t h) {
+  const int e = ceil_log2(w > h ? w : h);
+  return e == 0 ? 0 : (int32_t{1} << (e - 1));
+}
+
+// Eq. 3-4 in exact integers: the least power of two P with P^2 s >= 4 w h
+// (P >= 2 L_avg) and P >= d_max, capped at k_1.  Dense seeds can make the
+// exponent negative (no pass).
+int32_t djfa_first_step(int32_t w, int32_t h, int64_t s, int32_t d_max) {
+  const int32_t k1 = jfa_first_step(w, h);
+  if (s <= 0) return k1;
+  const int64_t area4 = 4 * static_cast<int64_t>(w) * h;
+  int e;
+  if (s >= area4) {
+    // P <= 1: find the least e <= 0 with s * 4^e >= area4, i.e. s >= area4 * 4^-e.
+    e = 0;
+    while (e > -31 && (s >> (2 * (1 - e))) >= area4) --e;
+  } else {
+    e = 0;
+    while ((s << (2 * e)) < area4) ++e;
+  }
+  if (d_max > 0) {
+    const int ed = ceil_log2(d_max);
+    if (ed > e) e = ed;
+  }
+  if (e < 0) return 0;
+  const int64_t p = int64_t{1} << e;
+  return static_cast<int32_t>(p > k1 ? k1 : p);
+}
+
+int fill_schedule(int32_t first, int32_t vn_waves, int32_t extra, int32_t* ks, int32_t* nbs,
+                  int32_t cap) {
+  int n = 0;
+  for (int32_t k = first; k >= 1; k >>= 1, ++n) {
+    if (n < cap) {
+      ks[n] = k;
+      nbs[n] = n < vn_waves ? VD_NB_VON_NEUMANN : VD_NB_MOORE;
+    }
+  }
+  for (int32_t e = extra; e >= 1; --e, ++n) {
+    if (n < cap) {
+      ks[n] = int32_t{1} << (e - 1);
+      nbs[n] = VD_NB_MOORE;
+    }
+  }
+  return n;
+}
+
+}  // namespace vdi
+
+static bool bad_side(int32_t v) { return v < 1 || v > VD_MAX_SIDE; }
+
+extern "C" int vd_jfa_schedule(int32_t w, int32_t h, int32_t extra, int32_t* ks, int32_t* nbs,
+                               int32_t cap) {
+  if (bad_side(w) || bad_side(h)) return vd_fail(VD_EINVAL, "grid %dx%d outside [1, %d]", w, h, VD_MAX_SIDE);
+  if (extra < 0 || extra > 2) return vd_fail(VD_EINVAL, "extra_passes %d outside [0, 2]", extra);
+  if (cap < 0 || (cap > 0 && (!ks || !nbs))) return vd_fail(VD_EINVAL, "bad output arrays");
+  return vdi::fill_schedule(vdi::jfa_first_step(w, h), 0, extra, ks, nbs, cap);
+}
+
+extern "C" int vd_djfa_schedule(int32_t w, int32_t h, int64_t s, int32_t d_max, int32_t vn_waves,
+                                int32_t extra, int32_t* ks, int32_t* nbs, int32_t cap) {
+  if (bad_side(w) || bad_side(h)) return vd_fail(VD_EINVAL, "grid %dx%d outside [1, %d]", w, h, VD_MAX_SIDE);
+  if (s < 1) return vd_fail(VD_EINVAL, "n_seeds %lld < 1", static_cast<long long>(s));
+  if (d_max < 0 || vn_waves < 0) return vd_fail(VD_EINVAL, "d_max/vn_waves must be >= 0");
+  if (extra < 0 || extra > 2) return vd_fail(VD_EINVAL, "extra_passes %d outside [0, 2]", extra);
+  if (cap < 0 || (cap > 0 && (!ks || !nbs))) return vd_fail(VD_EINVAL, "bad output arrays");
+  return vdi::fill_schedule(vdi::djfa_first_step(w, h, s, d_max), vn_waves, extra, ks, nbs, cap);
+}
+
+// ---------------------------------------------------------------------------
+// Launch planning shared with the batched engine
+// ---------------------------------------------------------------------------
+
+namespace vdi {
+
+int ensure_smem(const void* fn, size_t bytes, size_t* done) {
+  if (bytes <= 48 * 1024 || bytes <= *done) return VD_OK;
+  const cudaError_t e =
+      cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(bytes));
+  if (e != cudaSuccess) return vd_cuda_check(e, "cudaFuncSetAttribute(smem)");
+  *done = bytes;
+  return VD_OK;
+}
+
+template <int NB, int METRIC>
+static void launch_pass_t(int ksel, dim3 g, dim3 b, cudaStream_t st, const vdk::PassArgs& a) {
+  switch (ksel) {
+    case 0: vdk::k_pass<NB, METRIC, 0><<<g, b, 0, st>>>(a); break;
+    case 1: vdk::k_pass<NB, METRIC, 1><<<g, b, 0, st>>>(a); break;
+    case 2: vdk::k_pass<NB, METRIC, 2><<<g, b, 0, st>>>(a); break;
+    default: vdk::k_pass<NB, METRIC, 3><<<g, b, 0, st>>>(a); break;
+  }
+}
+
+int launch_pass(const MapView& m, const int32_t* src, int32_t* dst, int32_t k, int32_t nb,
+                int32_t metric, int64_t band_min_k, cudaStream_t st) {
+  vdk::PassArgs a;
+  a.src = src;
+  a.dst = dst;
+  a.seeds = m.seeds;
+  a.n_seeds = static_cast<uint32_t>(m.n);
+  a.w = m.w;
+  a.h = m.h;
+  a.pitch = m.pitch;
+  a.k = k;
+  a.band_m = 1;
+  a.band_t = 1;
+  const int quads = m.pitch / 4;
+  const int bx = quads < 64 ? quads : 64;
+  const int by = 256 / bx;
+  const int nrb = (m.h + by - 1) / by;
+  dim3 block(bx, by);
+  dim3 grid((quads + bx - 1) / bx, nrb);
+  bool band = false;
+  if (band_min_k < 0) {
+    // auto: once the rows y-k .. y+k span more than a quarter of L2
+    band = 2.0 * k * m.pitch * 4.0 >= 32.0 * 1024 * 1024;
+  } else if (band_min_k > 0) {
+    band = k >= band_min_k;
+  }
+  if (band && k % by == 0 && k / by > 1) {
+    a.band_m = k / by;
+    a.band_t = (nrb + a.band_m - 1) / a.band_m;
+    grid.y = a.band_m * a.band_t;
+  }
+  const int ksel = (k % 4 == 0) ? 0 : (k == 1 ? 1 : (k == 2 ? 2 : 3));
+  if (nb == VD_NB_MOORE) {
+    if (metric == VD_METRIC_EUCLID) launch_pass_t<vdk::kMoore, vdk::kEuclid>(ksel, grid, block, st, a);
+    else launch_pass_t<vdk::kMoore, vdk::kManhattan>(ksel, grid, block, st, a);
+  } else {
+    if (metric == VD_METRIC_EUCLID) launch_pass_t<vdk::kVonNeumann, vdk::kEuclid>(ksel, grid, block, st, a);
+    else launch_pass_t<vdk::kVonNeumann, vdk::kManhattan>(ksel, grid, block, st, a);
+  }
+  return vd_cuda_check(cudaGetLastError(), "jump pass launch");
+}
+
+int launch_fused(const MapView& m, const int32_t* src, int32_t* dst, const int32_t* ks,
+                 const int32_t* nbs, int n, int32_t metric, int tile_x, int tile_y,
+                 cudaStream_t st) {
+  static size_t smem_done[2] = {0, 0};
+  vdk::FusedArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.src = src;
+  a.dst = dst;
+  a.seeds = m.seeds;
+  a.n_seeds = static_cast<uint32_t>(m.n);
+  a.w = m.w;
+  a.h = m.h;
+  a.pitch = m.pitch;
+  a.n_pass = n;
+  a.halo = 0;
+  for (int i = 0; i < n; ++i) {
+    a.ks[i] = ks[i];
+    a.nbs[i] = nbs[i];
+    a.halo += ks[i];
+  }
+  a.tx = tile_x;
+  a.ty = tile_y;
+  const size_t smem =
+      2ull * (tile_x + 2 * a.halo) * (tile_y + 2 * a.halo) * sizeof(int32_t);
+  dim3 block(32, 8);
+  dim3 grid((m.w + tile_x - 1) / tile_x, (m.h + tile_y - 1) / tile_y);
+  int rc;
+  if (metric == VD_METRIC_EUCLID) {
+    rc = ensure_smem(reinterpret_cast<const void*>(&vdk::k_pass_fused<vdk::kEuclid>), smem, &smem_done[0]);
+    if (rc) return rc;
+    vdk::k_pass_fused<vdk::kEuclid><<<grid, block, smem, st>>>(a);
+  } else {
+    rc = ensure_smem(reinterpret_cast<const void*>(&vdk::k_pass_fused<vdk::kManhattan>), smem, &smem_done[1]);
+    if (rc) return rc;
+    vdk::k_pass_fused<vdk::kManhattan><<<grid, block, smem, st>>>(a);
+  }
+  return vd_cuda_check(cudaGetLastError(), "fused pass launch");
+}
+
+// Splits a frame's passes into launches: large steps one launch each, runs of
+// steps <= fuse_max_k into shared-memory groups (a lone small pass stays
+// unfused).  Returns the launch plan.
+std::vector<Launch> plan_passes(const int32_t* ks, const int32_t* nbs, int n, int fuse_max_k,
+                                int max_halo) {
+  std::vector<Launch> plan;
+  int i = 0;
+  while (i < n) {
+    if (fuse_max_k <= 0 || ks[i] > fuse_max_k) {
+      Launch l;
+      l.n = 1;
+      l.first = i;
+      plan.push_back(l);
+      ++i;
+      continue;
+    }
+    int j = i, halo = 0;
+    while (j < n && ks[j] <= fuse_max_k && j - i < vdk::kMaxFused && halo + ks[j] <= max_halo) {
+      halo += ks[j];
+      ++j;
+    }
+    Launch l;
+    l.first = i;
+    l.n = j - i;
+    plan.push_back(l);
+    i = j;
+  }
+  return plan;
+}
+
+int run_passes(const MapView& m, int32_t* const buf[2], int* cur, const int32_t* ks,
+               const int32_t* nbs, int n, int32_t metric, const Tuning& t, cudaStream_t st,
+               int64_t* launches, Profiler* prof) {
+  const std::vector<Launch> plan = plan_passes(ks, nbs, n, t.fuse_max_k, t.max_halo);
+  const int64_t px = static_cast<int64_t>(m.w) * m.h;
+  for (const Launch& l : plan) {
+    const int32_t* src = buf[*cur];
+    int32_t* dst = buf[*cur ^ 1];
+    int rc;
+    const int pi = prof ? prof->begin(l.n == 1 ? VD_KERNEL_PASS : VD_KERNEL_FUSED, px * l.n, st) : -1;
+    if (l.n == 1) {
+      rc = launch_pass(m, src, dst, ks[l.first], nbs[l.first], metric, t.band_min_k, st);
+    } else {
+      rc = launch_fused(m, src, dst, ks + l.first, nbs + l.first, l.n, metric, t.tile_x, t.tile_y, st);
+    }
+    if (prof) prof->end(pi, st);
+    if (rc) return rc;
+    ++*launches;
+    *cur ^= 1;
+  }
+  return VD_OK;
+}
+
+static int grid1d(int64_t n, int block) { return static_cast<int>((n + block - 1) / block); }
+
+int launch_fill(int32_t* buf, int64_t n_elems, int32_t v, cudaStream_t st) {
+  const int64_t n4 = n_elems / 4;
+  int blocks = grid1d(n4, 256);
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  if (blocks < 1) blocks = 1;
+  vdk::k_fill<<<blocks, 256, 0, st>>>(reinterpret_cast<int4*>(buf), n4, v);
+  return vd_cuda_check(cudaGetLastError(), "fill launch");
+}
+
+int launch_stamp(const MapView& m, int32_t* labels, bool mark, cudaStream_t st, int64_t* launches) {
+  const int blocks = grid1d(m.n, 256);
+  if (mark) {
+    vdk::k_stamp_mark<<<blocks, 256, 0, st>>>(labels, m.pitch, m.seeds, m.n);
+    ++*launches;
+  }
+  vdk::k_stamp_min<<<blocks, 256, 0, st>>>(labels, m.pitch, m.seeds, m.n);
+  ++*launches;
+  return vd_cuda_check(cudaGetLastError(), "stamp launch");
+}
+
+int launch_move(int2* seeds, int n, const int2* dxy, int w, int h, int max_disp, uint64_t key,
+                uint64_t step, cudaStream_t st) {
+  vdk::k_move<<<grid1d(n, 256), 256, 0, st>>>(seeds, n, dxy, w, h, max_disp, key, step);
+  return vd_cuda_check(cudaGetLastError(), "move launch");
+}
+
+uint64_t rng_key(uint64_t rng_seed, uint64_t stream_id) { return vdk::splitmix64(rng_seed, stream_id); }
+
+cudaEvent_t Profiler::take() {
+  if (!spare.empty()) {
+    cudaEvent_t e = spare.back();
+    spare.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return e;
+}
+
+int Profiler::begin(int kind, int64_t u, cudaStream_t st) {
+  Rec r;
+  r.kind = kind;
+  r.units = u;
+  r.a = take();
+  r.b = take();
+  if (!r.a || !r.b) return -1;
+  cudaEventRecord(r.a, st);
+  pending.push_back(r);
+  return static_cast<int>(pending.size()) - 1;
+}
+
+void Profiler::end(int idx, cudaStream_t st) {
+  if (idx >= 0) cudaEventRecord(pending[idx].b, st);
+}
+
+int Profiler::collect(cudaStream_t st) {
+  const int rc = vd_cuda_check(cudaStreamSynchronize(st), "synchronize");
+  if (rc) return rc;
+  for (const Rec& r : pending) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess) {
+      ms[r.kind] += t;
+      launches[r.kind] += 1;
+      units[r.kind] += r.units;
+    } else {
+      cudaGetLastError();
+    }
+    spare.push_back(r.a);
+    spare.push_back(r.b);
+  }
+  pending.clear();
+  return VD_OK;
+}
+
+void Profiler::reset() {
+  for (const Rec& r : pending) {
+    spare.push_back(r.a);
+    spare.push_back(r.b);
+  }
+  pending.clear();
+  for (int i = 0; i < 8; ++i) {
+    ms[i] = 0;
+    launches[i] = 0;
+    units[i] = 0;
+  }
+}
+
+void Profiler::destroy() {
+  reset();
+  for (cudaEvent_t e : spare) cudaEventDestroy(e);
+  spare.clear();
+}
+
+}  // namespace vdi
+
+// ---------------------------------------------------------------------------
+// The context
+// ---------------------------------------------------------------------------
+
+struct vd_ctx {
+  int device = 0;
+  int32_t w = 0, h = 0, n = 0, pitch = 0;
+  cudaStream_t stream = nullptr;
+  int32_t* buf[2] = {nullptr, nullptr};
+  int cur = 0;
+  int2* seeds = nullptr;
+  int2* dxy_stage = nullptr;
+  unsigned long long* counters = nullptr;      // [0] n_exact, [1] n_match, [2] flag
+  unsigned long long* host_counters = nullptr;  // pinned mirror
+  int32_t* stage_a = nullptr;  // dense w*h staging (exact distances / exact labels)
+  int32_t* stage_b = nullptr;  // dense w*h staging (reference labels / exact distances)
+  // bucket grid of vd_exact
+  int* bk_count = nullptr;
+  int* bk_start = nullptr;
+  int* bk_ids = nullptr;
+  int64_t bk_cells = 0;
+  vdi::Tuning tune;
+  vdi::Profiler prof;
+  int64_t launches = 0;
+  std::map<std::tuple<int, int, int, int, int, int, int>, cudaGraphExec_t> graphs;
+};
+
+static vdi::Profiler* prof_of(vd_ctx* c) { return c->tune.profile ? &c->prof : nullptr; }
+
+static vdi::MapView view(const vd_ctx* c) {
+  vdi::MapView m;
+  m.w = c->w;
+  m.h = c->h;
+  m.pitch = c->pitch;
+  m.n = c->n;
+  m.seeds = c->seeds;
+  return m;
+}
+
+static int ctx_alloc(void** p, size_t bytes, const char* what) {
+  const cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    cudaGetLastError();
+    return vd_fail(VD_ENOMEM, "cudaMalloc(%zu bytes) for %s: %s", bytes, what, cudaGetErrorString(e));
+  }
+  return VD_OK;
+}
+
+static void ctx_free(vd_ctx* c) {
+  c->prof.destroy();
+  for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
+  c->graphs.clear();
+  cudaFree(c->buf[0]);
+  cudaFree(c->buf[1]);
+  cudaFree(c->seeds);
+  cudaFree(c->dxy_stage);
+  cudaFree(c->counters);
+  cudaFreeHost(c->host_counters);
+  cudaFree(c->stage_a);
+  cudaFree(c->stage_b);
+  cudaFree(c->bk_count);
+  cudaFree(c->bk_start);
+  cudaFree(c->bk_ids);
+}
+
+extern "C" vd_ctx* vd_create(int32_t w, int32_t h, int32_t n) {
+  if (bad_side(w) || bad_side(h)) {
+    vd_fail(VD_EINVAL, "grid %dx%d outside [1, %d]", w, h, VD_MAX_SIDE);
+    return nullptr;
+  }
+  if (n < 1) {
+    vd_fail(VD_EINVAL, "n_seeds %d < 1", n);
+    return nullptr;
+  }
+  vd_ctx* c = new vd_ctx();
+  cudaGetDevice(&c->device);
+  c->w = w;
+  c->h = h;
+  c->n = n;
+  c->pitch = (w + 31) / 32 * 32;
+  const size_t map_bytes = static_cast<size_t>(c->pitch) * h * sizeof(int32_t);
+  int rc = VD_OK;
+  rc = rc ? rc : ctx_alloc(reinterpret_cast<void**>(&c->buf[0]), map_bytes, "label map");
+  rc = rc ? rc : ctx_alloc(reinterpret_cast<void**>(&c->buf[1]), map_bytes, "label map");
+  rc = rc ? rc : ctx_alloc(reinterpret_cast<void**>(&c->seeds), sizeof(int2) * n, "seeds");
+  rc = rc ? rc : ctx_alloc(reinterpret_cast<void**>(&c->dxy_stage), sizeof(int2) * n, "moves");
+  rc = rc ? rc : ctx_alloc(reinterpret_cast<void**>(&c->counters), 4 * sizeof(unsigned long long), "counters");
+  if (!rc) {
+    const cudaError_t e = cudaMallocHost(reinterpret_cast<void**>(&c->host_counters), 4 * sizeof(unsigned long long));
+    if (e != cudaSuccess) rc = vd_cuda_check(e, "cudaMallocHost(counters)");
+  }
+  if (!rc) rc = vd_cuda_check(cudaMemset(c->buf[0], 0xFF, map_bytes), "init map");
+  if (!rc) rc = vd_cuda_check(cudaMemset(c->buf[1], 0xFF, map_bytes), "init map");
+  if (!rc) rc = vd_cuda_check(cudaMemset(c->seeds, 0, sizeof(int2) * n), "init seeds");
+  if (!rc) rc = vd_cuda_check(cudaDeviceSynchronize(), "create");
+  if (rc) {
+    ctx_free(c);
+    delete c;
+    return nullptr;
+  }
+  return c;
+}
+
+extern "C" int vd_destroy(vd_ctx* c) {
+  if (!c) return VD_OK;
+  cudaStreamSynchronize(c->stream);
+  ctx_free(c);
+  delete c;
+  return VD_OK;
+}
+
+#define VD_CHECK_CTX(c) \
+  if (!(c)) return vd_fail(VD_EINVAL, "null context")
+
+extern "C" int vd_set_stream(vd_ctx* c, void* stream) {
+  VD_CHECK_CTX(c);
+  c->stream = static_cast<cudaStream_t>(stream);
+  for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
+  c->graphs.clear();
+  return VD_OK;
+}
+
+extern "C" int vd_synchronize(vd_ctx* c) {
+  VD_CHECK_CTX(c);
+  return vd_cuda_check(cudaStreamSynchronize(c->stream), "synchronize");
+}
+
+extern "C" int vd_get_shape(const vd_ctx* c, int32_t* w, int32_t* h, int32_t* n, int32_t* pitch) {
+  VD_CHECK_CTX(c);
+  if (w) *w = c->w;
+  if (h) *h = c->h;
+  if (n) *n = c->n;
+  if (pitch) *pitch = c->pitch;
+  return VD_OK;
+}
+
+static cudaMemcpyKind kind_from(int on_device) {
+  return on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+}
+
+extern "C" int vd_set_seeds(vd_ctx* c, const int32_t* xy, int on_device) {
+  VD_CHECK_CTX(c);
+  if (!xy) return vd_fail(VD_EINVAL, "null seeds");
+  if (!on_device) {
+    for (int32_t k = 0; k < c->n; ++k) {
+      const int32_t x = xy[2 * k], y = xy[2 * k + 1];
+      if (x < 0 || x >= c->w || y < 0 || y >= c->h)
+        return vd_fail(VD_EINVAL, "seed %d at (%d, %d) outside the %dx%d grid", k, x, y, c->w, c->h);
+    }
+  }
+  if (!on_device)
+    return vd_cuda_check(cudaMemcpyAsync(c->seeds, xy, sizeof(int2) * c->n, cudaMemcpyHostToDevice, c->stream),
+                         "copy seeds");
+  // device input: validate in the staging buffer so that rejected seeds never
+  // reach the kernels that index the map with them
+  int rc = vd_cuda_check(cudaMemcpyAsync(c->dxy_stage, xy, sizeof(int2) * c->n, cudaMemcpyDeviceToDevice, c->stream),
+                         "copy seeds");
+  if (!rc) rc = vd_cuda_check(cudaMemsetAsync(c->counters + 2, 0, sizeof(unsigned long long), c->stream), "memset");
+  if (rc) return rc;
+  vdk::k_check_seeds<<<(c->n + 255) / 256, 256, 0, c->stream>>>(c->dxy_stage, c->n, c->w, c->h, c->counters + 2);
+  ++c->launches;
+  rc = vd_cuda_check(cudaGetLastError(), "check seeds");
+  if (!rc) rc = vd_cuda_check(cudaMemcpyAsync(c->host_counters + 2, c->counters + 2, sizeof(unsigned long long),
+                                              cudaMemcpyDeviceToHost, c->stream), "copy flag");
+  if (!rc) rc = vd_cuda_check(cudaStreamSynchronize(c->stream), "synchronize");
+  if (rc) return rc;
+  if (c->host_counters[2] != 0)
+    return vd_fail(VD_EINVAL, "%llu device seeds outside the %dx%d grid", c->host_counters[2], c->w, c->h);
+  return vd_cuda_check(cudaMemcpyAsync(c->seeds, c->dxy_stage, sizeof(int2) * c->n, cudaMemcpyDeviceToDevice, c->stream),
+                       "copy seeds");
+}
+
+extern "C" int vd_get_seeds(vd_ctx* c, int32_t* xy, int on_device) {
+  VD_CHECK_CTX(c);
+  if (!xy) return vd_fail(VD_EINVAL, "null output");
+  int rc = vd_cuda_check(cudaMemcpyAsync(xy, c->seeds, sizeof(int2) * c->n,
+                                         on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                         c->stream), "copy seeds out");
+  if (rc || on_device) return rc;
+  return vd_cuda_check(cudaStreamSynchronize(c->stream), "synchronize");
+}
+
+extern "C" int vd_move_seeds(vd_ctx* c, const int32_t* dxy, int dxy_on_device, int32_t max_disp,
+                             uint64_t rng_seed, uint64_t stream_id, int64_t step) {
+  VD_CHECK_CTX(c);
+  const int2* d = nullptr;
+  if (dxy) {
+    if (dxy_on_device) {
+      d = reinterpret_cast<const int2*>(dxy);
+    } else {
+      const int rc = vd_cuda_check(cudaMemcpyAsync(c->dxy_stage, dxy, sizeof(int2) * c->n,
+                                                   cudaMemcpyHostToDevice, c->stream), "copy moves");
+      if (rc) return rc;
+      d = c->dxy_stage;
+    }
+  } else {
+    if (max_disp < 0 || max_disp > VD_MAX_SIDE) return vd_fail(VD_EINVAL, "max_disp %d outside [0, %d]", max_disp, VD_MAX_SIDE);
+    if (step < 0) return vd_fail(VD_EINVAL, "step %lld < 0", static_cast<long long>(step));
+  }
+  vdi::Profiler* pr = prof_of(c);
+  const int pi = pr ? pr->begin(VD_KERNEL_MOVE, c->n, c->stream) : -1;
+  const int rc = vdi::launch_move(c->seeds, c->n, d, c->w, c->h, max_disp, vdi::rng_key(rng_seed, stream_id),
+                                  static_cast<uint64_t>(step), c->stream);
+  if (pr) pr->end(pi, c->stream);
+  ++c->launches;
+  return rc;
+}
+
+static int check_metric(int32_t metric) {
+  if (metric != VD_METRIC_EUCLID && metric != VD_METRIC_MANHATTAN) return vd_fail(VD_EINVAL, "metric %d", metric);
+  return VD_OK;
+}
+
+// Runs a frame body either eagerly or as a cached CUDA graph.  `key` must
+// identify the launch sequence completely (it includes the buffer parity).
+template <typename F>
+static int run_frame(vd_ctx* c, const std::tuple<int, int, int, int, int, int, int>& key, int n_launch,
+                     int cur_after, F&& body) {
+  if (!c->tune.use_graphs || c->tune.profile || c->stream == nullptr) {
+    return body();
+  }
+  auto it = c->graphs.find(key);
+  if (it == c->graphs.end()) {
+    cudaGraph_t g = nullptr;
+    int rc = vd_cuda_check(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+    if (rc) return rc;
+    const int cur0 = c->cur;
+    const int64_t l0 = c->launches;
+    const int brc = body();
+    const cudaError_t ee = cudaStreamEndCapture(c->stream, &g);
+    c->cur = cur0;
+    c->launches = l0;
+    if (brc) {
+      if (g) cudaGraphDestroy(g);
+      return brc;
+    }
+    rc = vd_cuda_check(ee, "end capture");
+    if (rc) return rc;
+    cudaGraphExec_t ex = nullptr;
+    rc = vd_cuda_check(cudaGraphInstantiate(&ex, g, 0), "graph instantiate");
+    cudaGraphDestroy(g);
+    if (rc) return rc;
+    it = c->graphs.emplace(key, ex).first;
+  }
+  const int rc = vd_cuda_check(cudaGraphLaunch(it->second, c->stream), "graph launch");
+  if (rc) return rc;
+  c->cur = cur_after;
+  c->launches += n_launch;
+  return VD_OK;
+}
+
+static int count_launches(const int32_t* ks, const int32_t* nbs, int n, const vdi::Tuning& t) {
+  return static_cast<int>(vdi::plan_passes(ks, nbs, n, t.fuse_max_k, t.max_halo).size());
+}
+
+extern "C" int vd_jfa(vd_ctx* c, int32_t extra, int32_t metric) {
+  VD_CHECK_CTX(c);
+  if (check_metric(metric)) return VD_EINVAL;
+  int32_t ks[VD_MAX_PASSES], nbs[VD_MAX_PASSES];
+  const int n = vd_jfa_schedule(c->w, c->h, extra, ks, nbs, VD_MAX_PASSES);
+  if (n < 0) return n;
+  const int nl = count_launches(ks, nbs, n, c->tune);
+  const int cur_after = c->cur ^ (nl & 1);
+  auto body = [&]() -> int {
+    vdi::Profiler* pr = prof_of(c);
+    int pi = pr ? pr->begin(VD_KERNEL_FILL, static_cast<int64_t>(c->w) * c->h, c->stream) : -1;
+    int rc = vdi::launch_fill(c->buf[c->cur], static_cast<int64_t>(c->pitch) * c->h, -1, c->stream);
+    if (pr) pr->end(pi, c->stream);
+    ++c->launches;
+    if (rc) return rc;
+    pi = pr ? pr->begin(VD_KERNEL_STAMP, c->n, c->stream) : -1;
+    rc = vdi::launch_stamp(view(c), c->buf[c->cur], false, c->stream, &c->launches);
+    if (pr) pr->end(pi, c->stream);
+    if (rc) return rc;
+    return vdi::run_passes(view(c), c->buf, &c->cur, ks, nbs, n, metric, c->tune, c->stream, &c->launches, pr);
+  };
+  return run_frame(c, std::make_tuple(0, c->cur, extra, metric, 0, 0, 0), nl + 2, cur_after, body);
+}
+
+extern "C" int vd_djfa_step(vd_ctx* c, int32_t d_max, int32_t vn_waves, int32_t extra, int32_t metric) {
+  VD_CHECK_CTX(c);
+  if (check_metric(metric)) return VD_EINVAL;
+  int32_t ks[VD_MAX_PASSES], nbs[VD_MAX_PASSES];
+  const int n = vd_djfa_schedule(c->w, c->h, c->n, d_max, vn_waves, extra, ks, nbs, VD_MAX_PASSES);
+  if (n < 0) return n;
+  const int nl = count_launches(ks, nbs, n, c->tune);
+  const int cur_after = c->cur ^ (nl & 1);
+  auto body = [&]() -> int {
+    vdi::Profiler* pr = prof_of(c);
+    const int pi = pr ? pr->begin(VD_KERNEL_STAMP, 2 * static_cast<int64_t>(c->n), c->stream) : -1;
+    const int rc = vdi::launch_stamp(view(c), c->buf[c->cur], true, c->stream, &c->launches);
+    if (pr) pr->end(pi, c->stream);
+    if (rc) return rc;
+    return vdi::run_passes(view(c), c->buf, &c->cur, ks, nbs, n, metric, c->tune, c->stream, &c->launches, pr);
+  };
+  return run_frame(c, std::make_tuple(1, c->cur, d_max, vn_waves, extra, metric, 0), nl + 2, cur_after, body);
+}
+
+extern "C" int vd_stamp(vd_ctx* c) {
+  VD_CHECK_CTX(c);
+  return vdi::launch_stamp(view(c), c->buf[c->cur], true, c->stream, &c->launches);
+}
+
+extern "C" int vd_pass(vd_ctx* c, int32_t k, int32_t nb, int32_t metric) {
+  VD_CHECK_CTX(c);
+  if (check_metric(metric)) return VD_EINVAL;
+  if (k < 1) return vd_fail(VD_EINVAL, "step %d < 1", k);
+  if (nb != VD_NB_MOORE && nb != VD_NB_VON_NEUMANN) return vd_fail(VD_EINVAL, "neighbourhood %d", nb);
+  const int rc = vdi::launch_pass(view(c), c->buf[c->cur], c->buf[c->cur ^ 1], k, nb, metric,
+                                  c->tune.band_min_k, c->stream);
+  if (rc) return rc;
+  ++c->launches;
+  c->cur ^= 1;
+  return VD_OK;
+}
+
+extern "C" int vd_set_labels(vd_ctx* c, const int32_t* labels, int on_device) {
+  VD_CHECK_CTX(c);
+  if (!labels) return vd_fail(VD_EINVAL, "null labels");
+  if (!on_device) {
+    const int64_t total = static_cast<int64_t>(c->w) * c->h;
+    for (int64_t i = 0; i < total; ++i)
+      if (labels[i] < -1 || labels[i] >= c->n)
+        return vd_fail(VD_EINVAL, "label %d at %lld outside [-1, %d)", labels[i], static_cast<long long>(i), c->n);
+  }
+  return vd_cuda_check(cudaMemcpy2DAsync(c->buf[c->cur], sizeof(int32_t) * c->pitch, labels, sizeof(int32_t) * c->w,
+                                         sizeof(int32_t) * c->w, c->h, kind_from(on_device), c->stream),
+                       "copy labels in");
+}
+
+extern "C" int vd_get_labels(vd_ctx* c, int32_t* labels, int on_device) {
+  VD_CHECK_CTX(c);
+  if (!labels) return vd_fail(VD_EINVAL, "null output");
+  int rc = vd_cuda_check(cudaMemcpy2DAsync(labels, sizeof(int32_t) * c->w, c->buf[c->cur], sizeof(int32_t) * c->pitch,
+                                           sizeof(int32_t) * c->w, c->h,
+                                           on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream),
+                         "copy labels out");
+  if (rc || on_device) return rc;
+  return vd_cuda_check(cudaStreamSynchronize(c->stream), "synchronize");
+}
+
+extern "C" int vd_labels_device_ptr(vd_ctx* c, const int32_t** labels) {
+  VD_CHECK_CTX(c);
+  if (!labels) return vd_fail(VD_EINVAL, "null output");
+  *labels = c->buf[c->cur];
+  return VD_OK;
+}
+
+static int ensure_stage(vd_ctx* c, int32_t** p) {
+  if (*p) return VD_OK;
+  return ctx_alloc(reinterpret_cast<void**>(p), sizeof(int32_t) * static_cast<size_t>(c->w) * c->h, "staging map");
+}
+
+static int similarity_launch(vd_ctx* c, const int32_t* exact, int exact_pitch, const int32_t* ref, int ref_pitch,
+                             int32_t metric, uint64_t* ne, uint64_t* nm) {
+  int rc = vd_cuda_check(cudaMemsetAsync(c->counters, 0, 2 * sizeof(unsigned long long), c->stream), "memset");
+  if (rc) return rc;
+  const int64_t total = static_cast<int64_t>(c->w) * c->h;
+  int blocks = static_cast<int>((total + 255) / 256);
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  if (metric == VD_METRIC_EUCLID)
+    vdk::k_similarity<vdk::kEuclid><<<blocks, 256, 0, c->stream>>>(c->buf[c->cur], c->pitch, c->seeds, c->n, c->w, c->h,
+                                                                    exact, exact_pitch, ref, ref_pitch, c->counters);
+  else
+    vdk::k_similarity<vdk::kManhattan><<<blocks, 256, 0, c->stream>>>(c->buf[c->cur], c->pitch, c->seeds, c->n, c->w,
+                                                                       c->h, exact, exact_pitch, ref, ref_pitch, c->counters);
+  ++c->launches;
+  rc = vd_cuda_check(cudaGetLastError(), "similarity launch");
+  if (rc) return rc;
+  rc = vd_cuda_check(cudaMemcpyAsync(c->host_counters, c->counters, 2 * sizeof(unsigned long long),
+                                     cudaMemcpyDeviceToHost, c->stream), "copy counts");
+  if (rc) return rc;
+  rc = vd_cuda_check(cudaStreamSynchronize(c->stream), "synchronize");
+  if (rc) return rc;
+  if (ne) *ne = c->host_counters[0];
+  if (nm) *nm = c->host_counters[1];
+  return VD_OK;
+}
+
+extern "C" int vd_similarity(vd_ctx* c, const int32_t* exact, const int32_t* ref, int on_device, int32_t metric,
+                             uint64_t* ne, uint64_t* nm) {
+  VD_CHECK_CTX(c);
+  if (check_metric(metric)) return VD_EINVAL;
+  const size_t bytes = sizeof(int32_t) * static_cast<size_t>(c->w) * c->h;
+  const int32_t* de = exact;
+  const int32_t* dr = ref;
+  if (!on_device) {
+    if (exact) {
+      int rc = ensure_stage(c, &c->stage_a);
+      if (!rc) rc = vd_cuda_check(cudaMemcpyAsync(c->stage_a, exact, bytes, cudaMemcpyHostToDevice, c->stream), "copy exact");
+      if (rc) return rc;
+      de = c->stage_a;
+    }
+    if (ref) {
+      int rc = ensure_stage(c, &c->stage_b);
+      if (!rc) rc = vd_cuda_check(cudaMemcpyAsync(c->stage_b, ref, bytes, cudaMemcpyHostToDevice, c->stream), "copy ref");
+      if (rc) return rc;
+      dr = c->stage_b;
+    }
+  }
+  return similarity_launch(c, de, c->w, dr, c->w, metric, ne, nm);
+}
+
+extern "C" int vd_similarity_ctx(vd_ctx* c, vd_ctx* ref, uint64_t* nm) {
+  VD_CHECK_CTX(c);
+  VD_CHECK_CTX(ref);
+  if (ref->w != c->w || ref->h != c->h) return vd_fail(VD_EINVAL, "grid sizes differ");
+  if (ref->stream != c->stream) {
+    const int rc = vd_cuda_check(cudaStreamSynchronize(ref->stream), "synchronize reference");
+    if (rc) return rc;
+  }
+  return similarity_launch(c, nullptr, 0, ref->buf[ref->cur], ref->pitch, VD_METRIC_EUCLID, nullptr, nm);
+}
+
+extern "C" int vd_exact(vd_ctx* c, int32_t* labels, int32_t* dist, int on_device, int32_t metric) {
+  VD_CHECK_CTX(c);
+  if (check_metric(metric)) return VD_EINVAL;
+  // bucket side ~ sqrt(area / seeds): about one seed per bucket
+  int cell = 1;
+  const double per = static_cast<double>(c->w) * c->h / c->n;
+  while (static_cast<double>(cell + 1) * (cell + 1) <= per) ++cell;
+  int gw = (c->w + cell - 1) / cell, gh = (c->h + cell - 1) / cell;
+  const int64_t cells = static_cast<int64_t>(gw) * gh;
+  int rc = VD_OK;
+  if (cells > c->bk_cells) {
+    cudaFree(c->bk_count);
+    cudaFree(c->bk_start);
+    c->bk_count = c->bk_start = nullptr;
+    c->bk_cells = 0;
+    rc = ctx_alloc(reinterpret_cast<void**>(&c->bk_count), sizeof(int) * cells, "bucket counts");
+    if (!rc) rc = ctx_alloc(reinterpret_cast<void**>(&c->bk_start), sizeof(int) * (cells + 1), "bucket starts");
+    if (rc) return rc;
+    c->bk_cells = cells;
+  }
+  if (!c->bk_ids) rc = ctx_alloc(reinterpret_cast<void**>(&c->bk_ids), sizeof(int) * c->n, "bucket ids");
+  if (rc) return rc;
+  int32_t* dl = labels;
+  int32_t* dd = dist;
+  if (!on_device) {
+    if (labels) {
+      rc = ensure_stage(c, &c->stage_a);
+      if (rc) return rc;
+      dl = c->stage_a;
+    }
+    if (dist) {
+      rc = ensure_stage(c, &c->stage_b);
+      if (rc) return rc;
+      dd = c->stage_b;
+    }
+  }
+  const int sb = (c->n + 255) / 256;
+  rc = vd_cuda_check(cudaMemsetAsync(c->bk_count, 0, sizeof(int) * cells, c->stream), "memset");
+  if (rc) return rc;
+  vdk::k_bucket_count<<<sb, 256, 0, c->stream>>>(c->seeds, c->n, cell, gw, c->bk_count);
+  vdk::k_scan<<<1, 1024, 0, c->stream>>>(c->bk_count, static_cast<int>(cells), c->bk_start);
+  rc = vd_cuda_check(cudaMemsetAsync(c->bk_count, 0, sizeof(int) * cells, c->stream), "memset");
+  if (rc) return rc;
+  vdk::k_bucket_fill<<<sb, 256, 0, c->stream>>>(c->seeds, c->n, cell, gw, c->bk_start, c->bk_count, c->bk_ids);
+  vdk::Buckets b;
+  b.cell = cell;
+  b.gw = gw;
+  b.gh = gh;
+  b.start = c->bk_start;
+  b.ids = c->bk_ids;
+  dim3 block(32, 8), grid((c->w + 31) / 32, (c->h + 7) / 8);
+  if (metric == VD_METRIC_EUCLID)
+    vdk::k_exact<vdk::kEuclid><<<grid, block, 0, c->stream>>>(b, c->seeds, c->w, c->h, dl, dd);
+  else
+    vdk::k_exact<vdk::kManhattan><<<grid, block, 0, c->stream>>>(b, c->seeds, c->w, c->h, dl, dd);
+  c->launches += 4;
+  rc = vd_cuda_check(cudaGetLastError(), "exact launch");
+  if (rc) return rc;
+  if (on_device) return VD_OK;
+  const size_t bytes = sizeof(int32_t) * static_cast<size_t>(c->w) * c->h;
+  if (labels) rc = vd_cuda_check(cudaMemcpyAsync(labels, dl, bytes, cudaMemcpyDeviceToHost, c->stream), "copy out");
+  if (!rc && dist) rc = vd_cuda_check(cudaMemcpyAsync(dist, dd, bytes, cudaMemcpyDeviceToHost, c->stream), "copy out");
+  if (rc) return rc;
+  return vd_cuda_check(cudaStreamSynchronize(c->stream), "synchronize");
+}
+
+extern "C" int vd_set_option(vd_ctx* c, int32_t option, int64_t value) {
+  VD_CHECK_CTX(c);
+  vdi::Tuning t = c->tune;
+  switch (option) {
+    case VD_OPT_FUSE_MAX_K:
+      if (value < 0 || value > 16) return vd_fail(VD_EINVAL, "fuse_max_k %lld outside [0, 16]", static_cast<long long>(value));
+      t.fuse_max_k = static_cast<int>(value);
+      break;
+    case VD_OPT_BAND_ORDER_MIN_K:
+      if (value < -1) return vd_fail(VD_EINVAL, "band_min_k %lld < -1", static_cast<long long>(value));
+      t.band_min_k = value;
+      break;
+    case VD_OPT_USE_GRAPHS:
+      if (value != 0 && value != 1) return vd_fail(VD_EINVAL, "use_graphs must be 0 or 1");
+      t.use_graphs = static_cast<int>(value);
+      break;
+    case VD_OPT_FUSE_TILE_X:
+      if (value < 16 || value > 256 || value % 4) return vd_fail(VD_EINVAL, "tile_x %lld", static_cast<long long>(value));
+      t.tile_x = static_cast<int>(value);
+      break;
+    case VD_OPT_FUSE_TILE_Y:
+      if (value < 1 || value > 128) return vd_fail(VD_EINVAL, "tile_y %lld", static_cast<long long>(value));
+      t.tile_y = static_cast<int>(value);
+      break;
+    case VD_OPT_PROFILE:
+      if (value != 0 && value != 1) return vd_fail(VD_EINVAL, "profile must be 0 or 1");
+      t.profile = static_cast<int>(value);
+      break;
+    default:
+      return vd_fail(VD_EINVAL, "unknown option %d", option);
+  }
+  const size_t smem = 2ull * (t.tile_x + 2 * t.max_halo) * (t.tile_y + 2 * t.max_halo) * sizeof(int32_t);
+  if (smem > 220 * 1024) return vd_fail(VD_EINVAL, "fused tile needs %zu bytes of shared memory", smem);
+  c->tune = t;
+  for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
+  c->graphs.clear();
+  return VD_OK;
+}
+
+extern "C" int vd_get_option(const vd_ctx* c, int32_t option, int64_t* value) {
+  VD_CHECK_CTX(c);
+  if (!value) return vd_fail(VD_EINVAL, "null output");
+  switch (option) {
+    case VD_OPT_FUSE_MAX_K: *value = c->tune.fuse_max_k; break;
+    case VD_OPT_BAND_ORDER_MIN_K: *value = c->tune.band_min_k; break;
+    case VD_OPT_USE_GRAPHS: *value = c->tune.use_graphs; break;
+    case VD_OPT_FUSE_TILE_X: *value = c->tune.tile_x; break;
+    case VD_OPT_FUSE_TILE_Y: *value = c->tune.tile_y; break;
+    case VD_OPT_PROFILE: *value = c->tune.profile; break;
+    default: return vd_fail(VD_EINVAL, "unknown option %d", option);
+  }
+  return VD_OK;
+}
+
+extern "C" int64_t vd_launch_count(const vd_ctx* c) { return c ? c->launches : -1; }
+
+extern "C" int vd_profile_read(vd_ctx* c, double* total_ms, int64_t* launches, int64_t* units) {
+  VD_CHECK_CTX(c);
+  if (!c->tune.profile) return vd_fail(VD_EINVAL, "profiling is off (VD_OPT_PROFILE)");
+  const int rc = c->prof.collect(c->stream);
+  if (rc) return rc;
+  for (int k = 0; k < VD_KERNEL_KINDS; ++k) {
+    if (total_ms) total_ms[k] = c->prof.ms[k];
+    if (launches) launches[k] = c->prof.launches[k];
+    if (units) units[k] = c->prof.units[k];
+  }
+  return VD_OK;
+}
+
+extern "C" int vd_profile_reset(vd_ctx* c) {
+  VD_CHECK_CTX(c);
+  const int rc = vd_cuda_check(cudaStreamSynchronize(c->stream), "synchronize");
+  if (rc) return rc;
+  c->prof.reset();
+  return VD_OK;
+}

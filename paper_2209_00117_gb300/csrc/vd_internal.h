@@ -1,0 +1,85 @@
+// vd_internal.h -- host-side helpers shared by the translation units of the
+// CUDA library (not part of the public ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <vector>
+
+// Records a message for vd_last_error() and returns `code`.
+int vd_fail(int code, const char* fmt, ...);
+// VD_OK, or VD_ENOMEM / VD_ECUDA with the CUDA error text recorded.
+int vd_cuda_check(cudaError_t e, const char* what);
+
+namespace vdi {
+
+// What a jump pass needs to know about one map.
+struct MapView {
+  int32_t w = 0, h = 0, pitch = 0, n = 0;
+  const int2* seeds = nullptr;
+};
+
+// Launch-shape choices of the jump passes.
+struct Tuning {
+  int fuse_max_k = 8;     // steps <= this run in shared-memory groups
+  int max_halo = 32;      // largest sum of steps in one group
+  int64_t band_min_k = -1;  // -1 auto, 0 never, else from this step up
+  int use_graphs = 0;
+  int tile_x = 64;
+  int tile_y = 32;
+  int profile = 0;
+};
+
+// Event pairs bracketing kernel launches (profiling mode).  Records are kept
+// until read; events are recycled afterwards.
+struct Profiler {
+  struct Rec {
+    int kind;
+    int64_t units;
+    cudaEvent_t a, b;
+  };
+  std::vector<Rec> pending;
+  std::vector<cudaEvent_t> spare;
+  double ms[8] = {0};
+  int64_t launches[8] = {0};
+  int64_t units[8] = {0};
+  cudaEvent_t take();
+  // Records the opening event of a launch of `kind`; returns its index.
+  int begin(int kind, int64_t units, cudaStream_t st);
+  void end(int idx, cudaStream_t st);
+  int collect(cudaStream_t st);  // synchronises and folds pending records in
+  void reset();
+  void destroy();
+};
+
+// One launch of a frame's plan: passes [first, first + n).
+struct Launch {
+  int first = 0;
+  int n = 0;
+};
+
+int ceil_log2(int64_t v);
+int32_t jfa_first_step(int32_t w, int32_t h);
+int32_t djfa_first_step(int32_t w, int32_t h, int64_t s, int32_t d_max);
+int fill_schedule(int32_t first, int32_t vn_waves, int32_t extra, int32_t* ks, int32_t* nbs,
+                  int32_t cap);
+
+std::vector<Launch> plan_passes(const int32_t* ks, const int32_t* nbs, int n, int fuse_max_k,
+                                int max_halo);
+int launch_pass(const MapView& m, const int32_t* src, int32_t* dst, int32_t k, int32_t nb,
+                int32_t metric, int64_t band_min_k, cudaStream_t st);
+int launch_fused(const MapView& m, const int32_t* src, int32_t* dst, const int32_t* ks,
+                 const int32_t* nbs, int n, int32_t metric, int tile_x, int tile_y,
+                 cudaStream_t st);
+int run_passes(const MapView& m, int32_t* const buf[2], int* cur, const int32_t* ks,
+               const int32_t* nbs, int n, int32_t metric, const Tuning& t, cudaStream_t st,
+               int64_t* launches, Profiler* prof);
+int launch_fill(int32_t* buf, int64_t n_elems, int32_t v, cudaStream_t st);
+int launch_stamp(const MapView& m, int32_t* labels, bool mark, cudaStream_t st, int64_t* launches);
+int launch_move(int2* seeds, int n, const int2* dxy, int w, int h, int max_disp, uint64_t key,
+                uint64_t step, cudaStream_t st);
+uint64_t rng_key(uint64_t rng_seed, uint64_t stream_id);
+int ensure_smem(const void* fn, size_t bytes, size_t* done);
+
+}  // namespace vdi

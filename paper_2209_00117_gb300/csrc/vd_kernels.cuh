@@ -1,0 +1,510 @@
+// vd_kernels.cuh -- sm_103a kernels of the jump-flooding hot path.
+//
+// Label maps are row-major int32 with a row pitch that is a multiple of 32
+// elements (128 bytes); columns in [w, pitch) always hold -1, so a neighbour
+// that falls into the padding reads as "empty" without a bounds test.  Seeds
+// are int2 (x, y).  Every kernel here is a pure gather or a per-seed scatter:
+// nothing waits on anything, so no launch can hang.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace vdk {
+
+constexpr int kEuclid = 0;
+constexpr int kManhattan = 1;
+constexpr int kMoore = 0;
+constexpr int kVonNeumann = 1;
+
+// Distance of Section II (squared Euclidean) or Section IV-C (Manhattan),
+// exact in 32 bits for grid sides up to 32768 (2 * 32767^2 < 2^31).
+template <int METRIC>
+__device__ __forceinline__ uint32_t seed_dist(int2 s, int x, int y) {
+  const int dx = s.x - x;
+  const int dy = s.y - y;
+  if (METRIC == kManhattan) return static_cast<uint32_t>(abs(dx) + abs(dy));
+  return static_cast<uint32_t>(dx * dx + dy * dy);
+}
+
+// The distance comparison of Section III as a total order: a candidate seed c
+// replaces the incumbent (bd, bl) when it is nearer to the pixel, or equally
+// near with a lower index.  Labels outside [0, n) (-1 = empty) are skipped.
+template <int METRIC>
+__device__ __forceinline__ void consider(int c, const int2* __restrict__ seeds, uint32_t n, int x,
+                                         int y, uint32_t& bd, int& bl) {
+  if (static_cast<uint32_t>(c) < n && c != bl) {
+    const uint32_t d = seed_dist<METRIC>(__ldg(&seeds[c]), x, y);
+    if (d < bd || (d == bd && c < bl)) {
+      bd = d;
+      bl = c;
+    }
+  }
+}
+
+template <int METRIC>
+__device__ __forceinline__ void init_best(int c, const int2* __restrict__ seeds, uint32_t n, int x,
+                                          int y, uint32_t& bd, int& bl) {
+  if (static_cast<uint32_t>(c) < n) {
+    bl = c;
+    bd = seed_dist<METRIC>(__ldg(&seeds[c]), x, y);
+  } else {
+    bl = -1;
+    bd = 0xFFFFFFFFu;
+  }
+}
+
+__device__ __forceinline__ int4 ld4(const int32_t* p) {
+  return __ldg(reinterpret_cast<const int4*>(p));
+}
+
+__device__ __forceinline__ int elem(const int4& v, int i) {
+  return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w));
+}
+
+// Element j in [0, 12) of the concatenation a | b | c.
+__device__ __forceinline__ int elem3(const int4& a, const int4& b, const int4& c, int j) {
+  return j < 4 ? elem(a, j) : (j < 8 ? elem(b, j - 4) : elem(c, j - 8));
+}
+
+struct PassArgs {
+  const int32_t* __restrict__ src;
+  int32_t* __restrict__ dst;
+  const int2* __restrict__ seeds;
+  uint32_t n_seeds;
+  int w, h, pitch, k;
+  int band_m;  // > 1: visit row-blocks in k-strided bands (band_m = k / rows per block)
+  int band_t;  // row-blocks per band residue class
+};
+
+// The three label vectors of one source row seen by a thread that owns the
+// four pixels x0 .. x0+3: left[i] = L(x0+i-k), mid[i] = L(x0+i), right[i] =
+// L(x0+i+k).  KSEL 0: k is a multiple of 4 (aligned vector loads); KSEL 1/2:
+// k = 1/2 (three aligned vectors, shifted); KSEL 3: any other k (scalar).
+template <int KSEL>
+__device__ __forceinline__ void load_row(const int32_t* __restrict__ row, int x0, int k, int w,
+                                         int pitch, bool need_sides, int4& left, int4& mid,
+                                         int4& right) {
+  const int4 neg = make_int4(-1, -1, -1, -1);
+  mid = ld4(row + x0);
+  if (!need_sides) {
+    left = neg;
+    right = neg;
+    return;
+  }
+  if (KSEL == 0) {
+    left = (x0 - k >= 0) ? ld4(row + x0 - k) : neg;
+    right = (x0 + k < pitch) ? ld4(row + x0 + k) : neg;
+  } else if (KSEL == 1 || KSEL == 2) {
+    const int4 a = (x0 >= 4) ? ld4(row + x0 - 4) : neg;
+    const int4 c = (x0 + 4 < pitch) ? ld4(row + x0 + 4) : neg;
+    left.x = elem3(a, mid, c, 4 - KSEL);
+    left.y = elem3(a, mid, c, 5 - KSEL);
+    left.z = elem3(a, mid, c, 6 - KSEL);
+    left.w = elem3(a, mid, c, 7 - KSEL);
+    right.x = elem3(a, mid, c, 4 + KSEL);
+    right.y = elem3(a, mid, c, 5 + KSEL);
+    right.z = elem3(a, mid, c, 6 + KSEL);
+    right.w = elem3(a, mid, c, 7 + KSEL);
+  } else {
+    int l[4], r[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int xl = x0 + i - k;
+      const int xr = x0 + i + k;
+      l[i] = (xl >= 0 && xl < w) ? __ldg(row + xl) : -1;
+      r[i] = (xr >= 0 && xr < w) ? __ldg(row + xr) : -1;
+    }
+    left = make_int4(l[0], l[1], l[2], l[3]);
+    right = make_int4(r[0], r[1], r[2], r[3]);
+  }
+}
+
+// One jump pass (Table I / Section IV-B) over the whole map: every thread
+// owns four horizontally adjacent pixels, reads the 3 x 3 (Moore) or plus
+// (Von Neumann) pattern of label vectors at offset k with 16-byte loads and
+// writes four labels with one 16-byte store.
+template <int NB, int METRIC, int KSEL>
+__global__ void __launch_bounds__(256) k_pass(PassArgs a) {
+  const int x0 = 4 * static_cast<int>(blockIdx.x * blockDim.x + threadIdx.x);
+  int rb = blockIdx.y;
+  if (a.band_m > 1) rb = (blockIdx.y % a.band_t) * a.band_m + blockIdx.y / a.band_t;
+  const int y = rb * static_cast<int>(blockDim.y) + static_cast<int>(threadIdx.y);
+  if (x0 >= a.pitch || y >= a.h) return;
+
+  const int4 neg = make_int4(-1, -1, -1, -1);
+  int4 uL, uM, uR, cL, cM, cR, dL, dM, dR;
+  const bool moore = (NB == kMoore);
+  const int64_t pitch = a.pitch;
+  load_row<KSEL>(a.src + y * pitch, x0, a.k, a.w, a.pitch, true, cL, cM, cR);
+  if (y - a.k >= 0) {
+    load_row<KSEL>(a.src + (y - a.k) * pitch, x0, a.k, a.w, a.pitch, moore, uL, uM, uR);
+  } else {
+    uL = uM = uR = neg;
+  }
+  if (y + a.k < a.h) {
+    load_row<KSEL>(a.src + (y + a.k) * pitch, x0, a.k, a.w, a.pitch, moore, dL, dM, dR);
+  } else {
+    dL = dM = dR = neg;
+  }
+
+  int out[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int x = x0 + i;
+    if (x >= a.w) {
+      out[i] = -1;
+      continue;
+    }
+    uint32_t bd;
+    int bl;
+    init_best<METRIC>(elem(cM, i), a.seeds, a.n_seeds, x, y, bd, bl);
+    consider<METRIC>(elem(cR, i), a.seeds, a.n_seeds, x, y, bd, bl);
+    consider<METRIC>(elem(cL, i), a.seeds, a.n_seeds, x, y, bd, bl);
+    consider<METRIC>(elem(dM, i), a.seeds, a.n_seeds, x, y, bd, bl);
+    consider<METRIC>(elem(uM, i), a.seeds, a.n_seeds, x, y, bd, bl);
+    if (NB == kMoore) {
+      consider<METRIC>(elem(dR, i), a.seeds, a.n_seeds, x, y, bd, bl);
+      consider<METRIC>(elem(dL, i), a.seeds, a.n_seeds, x, y, bd, bl);
+      consider<METRIC>(elem(uL, i), a.seeds, a.n_seeds, x, y, bd, bl);
+      consider<METRIC>(elem(uR, i), a.seeds, a.n_seeds, x, y, bd, bl);
+    }
+    out[i] = bl;
+  }
+  *reinterpret_cast<int4*>(a.dst + y * pitch + x0) = make_int4(out[0], out[1], out[2], out[3]);
+}
+
+// ---------------------------------------------------------------------------
+// Fused group of small-step passes in shared memory.
+// ---------------------------------------------------------------------------
+
+constexpr int kMaxFused = 8;
+
+struct FusedArgs {
+  const int32_t* __restrict__ src;
+  int32_t* __restrict__ dst;
+  const int2* __restrict__ seeds;
+  uint32_t n_seeds;
+  int w, h, pitch;
+  int n_pass;
+  int ks[kMaxFused];
+  int nbs[kMaxFused];
+  int halo;      // sum of ks
+  int tx, ty;    // output tile
+};
+
+// A tile of (tx + 2 halo) x (ty + 2 halo) labels is loaded once; pass j then
+// recomputes the tile grown by the steps still to come, so its neighbours at
+// offset k_j always lie inside the region the previous pass produced.
+// Out-of-grid cells hold -1 in every pass, exactly as an unfused pass skips
+// out-of-grid neighbours, so the result equals the unfused passes bit for bit.
+template <int METRIC>
+__global__ void __launch_bounds__(256) k_pass_fused(FusedArgs a) {
+  extern __shared__ int32_t smem[];
+  const int H = a.halo;
+  const int SW = a.tx + 2 * H;
+  const int SH = a.ty + 2 * H;
+  int32_t* A = smem;
+  int32_t* B = smem + SW * SH;
+  const int gx0 = static_cast<int>(blockIdx.x) * a.tx - H;  // grid coords of smem (0, 0)
+  const int gy0 = static_cast<int>(blockIdx.y) * a.ty - H;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int bx = blockDim.x, by = blockDim.y;
+  const int64_t pitch = a.pitch;
+
+  for (int sy = ty; sy < SH; sy += by) {
+    const int gy = gy0 + sy;
+    const bool row_ok = gy >= 0 && gy < a.h;
+    const int32_t* row = a.src + (row_ok ? gy : 0) * pitch;
+    for (int sx = tx; sx < SW; sx += bx) {
+      const int gx = gx0 + sx;
+      A[sy * SW + sx] = (row_ok && gx >= 0 && gx < a.w) ? __ldg(row + gx) : -1;
+    }
+  }
+  __syncthreads();
+
+  int rem = H;
+  for (int p = 0; p < a.n_pass; ++p) {
+    const int k = a.ks[p];
+    const bool moore = a.nbs[p] == kMoore;
+    rem -= k;
+    const int lo = H - rem;            // first smem row/col of this pass's region
+    const int rw = a.tx + 2 * rem;
+    const int rh = a.ty + 2 * rem;
+    for (int ry = ty; ry < rh; ry += by) {
+      const int sy = lo + ry;
+      const int y = gy0 + sy;
+      for (int rx = tx; rx < rw; rx += bx) {
+        const int sx = lo + rx;
+        const int x = gx0 + sx;
+        int res = -1;
+        if (x >= 0 && x < a.w && y >= 0 && y < a.h) {
+          const int32_t* c = A + sy * SW + sx;
+          uint32_t bd;
+          int bl;
+          init_best<METRIC>(c[0], a.seeds, a.n_seeds, x, y, bd, bl);
+          consider<METRIC>(c[k], a.seeds, a.n_seeds, x, y, bd, bl);
+          consider<METRIC>(c[-k], a.seeds, a.n_seeds, x, y, bd, bl);
+          consider<METRIC>(c[k * SW], a.seeds, a.n_seeds, x, y, bd, bl);
+          consider<METRIC>(c[-k * SW], a.seeds, a.n_seeds, x, y, bd, bl);
+          if (moore) {
+            consider<METRIC>(c[k * SW + k], a.seeds, a.n_seeds, x, y, bd, bl);
+            consider<METRIC>(c[k * SW - k], a.seeds, a.n_seeds, x, y, bd, bl);
+            consider<METRIC>(c[-k * SW - k], a.seeds, a.n_seeds, x, y, bd, bl);
+            consider<METRIC>(c[-k * SW + k], a.seeds, a.n_seeds, x, y, bd, bl);
+          }
+          res = bl;
+        }
+        B[sy * SW + sx] = res;
+      }
+    }
+    __syncthreads();
+    int32_t* t = A;
+    A = B;
+    B = t;
+  }
+
+  // write the tile (columns up to the pitch, so the padding stays -1)
+  for (int ry = ty; ry < a.ty; ry += by) {
+    const int y = gy0 + H + ry;
+    if (y >= a.h) break;
+    for (int rx = tx; rx < a.tx; rx += bx) {
+      const int x = gx0 + H + rx;
+      if (x < a.pitch) a.dst[y * pitch + x] = (x < a.w) ? A[(H + ry) * SW + H + rx] : -1;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Seeds: move, stamp
+// ---------------------------------------------------------------------------
+
+// SplitMix64 (Steele, Lea, Flood 2014): n-th output of the generator started
+// at `state`.
+__host__ __device__ __forceinline__ uint64_t splitmix64(uint64_t state, uint64_t n) {
+  uint64_t z = state + (n + 1) * 0x9E3779B97F4A7C15ULL;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ int rng_disp(uint64_t key, uint64_t step, uint64_t k, int axis, int max_disp) {
+  const uint64_t draw = splitmix64(key, (step << 33) + 2 * k + static_cast<uint64_t>(axis));
+  const uint64_t m = static_cast<uint64_t>(2 * max_disp + 1);
+  return static_cast<int>(((draw >> 32) * m) >> 32) - max_disp;
+}
+
+// SimulateParticles (Algorithm 1): p_k <- clamp(p_k + delta_k) on the grid.
+__global__ void k_move(int2* __restrict__ seeds, int n, const int2* __restrict__ dxy, int w, int h,
+                       int max_disp, uint64_t key, uint64_t step) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  int2 p = seeds[k];
+  long long dx, dy;
+  if (dxy != nullptr) {
+    const int2 d = dxy[k];
+    dx = d.x;
+    dy = d.y;
+  } else {
+    dx = rng_disp(key, step, static_cast<uint64_t>(k), 0, max_disp);
+    dy = rng_disp(key, step, static_cast<uint64_t>(k), 1, max_disp);
+  }
+  long long x = p.x + dx, y = p.y + dy;
+  x = x < 0 ? 0 : (x > w - 1 ? w - 1 : x);
+  y = y < 0 ? 0 : (y > h - 1 ? h - 1 : y);
+  p.x = static_cast<int>(x);
+  p.y = static_cast<int>(y);
+  seeds[k] = p;
+}
+
+// Stamp, first half: every seed pixel is overwritten with one of the indices
+// standing on it (which one does not matter), replacing any stale label.
+__global__ void k_stamp_mark(int32_t* __restrict__ labels, int pitch, const int2* __restrict__ seeds,
+                             int n) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const int2 p = seeds[k];
+  labels[static_cast<int64_t>(p.y) * pitch + p.x] = k;
+}
+
+// Stamp, second half: the lowest index standing on the pixel wins.  As
+// unsigned, -1 is the largest value, so this also stamps an emptied map.
+__global__ void k_stamp_min(int32_t* __restrict__ labels, int pitch, const int2* __restrict__ seeds,
+                            int n) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const int2 p = seeds[k];
+  atomicMin(reinterpret_cast<unsigned int*>(labels + static_cast<int64_t>(p.y) * pitch + p.x),
+            static_cast<unsigned int>(k));
+}
+
+__global__ void k_fill(int4* __restrict__ p, int64_t n4, int v) {
+  const int4 val = make_int4(v, v, v, v);
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n4;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    p[i] = val;
+}
+
+// Flags any seed outside the grid (device-side input validation).
+__global__ void k_check_seeds(const int2* __restrict__ seeds, int n, int w, int h,
+                              unsigned long long* __restrict__ bad) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const int2 p = seeds[k];
+  if (p.x < 0 || p.x >= w || p.y < 0 || p.y >= h) atomicAdd(bad, 1ULL);
+}
+
+// ---------------------------------------------------------------------------
+// Similarity counts (Section V-A)
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xFFFFFFFFu, v, o);
+  return v;
+}
+
+template <int METRIC>
+__global__ void __launch_bounds__(256) k_similarity(const int32_t* __restrict__ labels, int pitch,
+                                                    const int2* __restrict__ seeds, uint32_t n, int w,
+                                                    int h, const int32_t* __restrict__ exact,
+                                                    int exact_pitch, const int32_t* __restrict__ ref,
+                                                    int ref_pitch,
+                                                    unsigned long long* __restrict__ counters) {
+  unsigned long long ne = 0, nm = 0;
+  const int64_t total = static_cast<int64_t>(w) * h;
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < total;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int y = static_cast<int>(i / w);
+    const int x = static_cast<int>(i - static_cast<int64_t>(y) * w);
+    const int l = labels[static_cast<int64_t>(y) * pitch + x];
+    if (exact != nullptr && static_cast<uint32_t>(l) < n) {
+      const uint32_t d = seed_dist<METRIC>(seeds[l], x, y);
+      ne += (d == static_cast<uint32_t>(exact[static_cast<int64_t>(y) * exact_pitch + x])) ? 1 : 0;
+    }
+    if (ref != nullptr) nm += (l == ref[static_cast<int64_t>(y) * ref_pitch + x]) ? 1 : 0;
+  }
+  __shared__ unsigned long long s_e[8], s_m[8];
+  ne = warp_sum(ne);
+  nm = warp_sum(nm);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) {
+    s_e[wid] = ne;
+    s_m[wid] = nm;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long te = 0, tm = 0;
+    for (int j = 0; j < static_cast<int>(blockDim.x >> 5); ++j) {
+      te += s_e[j];
+      tm += s_m[j];
+    }
+    if (te) atomicAdd(&counters[0], te);
+    if (tm) atomicAdd(&counters[1], tm);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Exact diagram (Eq. 1) through a uniform bucket grid
+// ---------------------------------------------------------------------------
+
+struct Buckets {
+  int cell;          // bucket side in pixels
+  int gw, gh;        // buckets per row / column
+  const int* start;  // gw*gh + 1 offsets into `ids`
+  const int* ids;    // seed indices grouped by bucket
+};
+
+__global__ void k_bucket_count(const int2* __restrict__ seeds, int n, int cell, int gw,
+                               int* __restrict__ count) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const int2 p = seeds[k];
+  atomicAdd(&count[(p.y / cell) * gw + p.x / cell], 1);
+}
+
+__global__ void k_bucket_fill(const int2* __restrict__ seeds, int n, int cell, int gw,
+                              const int* __restrict__ start, int* __restrict__ cursor,
+                              int* __restrict__ ids) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const int2 p = seeds[k];
+  const int b = (p.y / cell) * gw + p.x / cell;
+  ids[start[b] + atomicAdd(&cursor[b], 1)] = k;
+}
+
+// Exclusive scan of `count` (length m) into `start` (length m + 1), one
+// block of 1024 threads walking the array in chunks with a running carry.
+__global__ void __launch_bounds__(1024) k_scan(const int* __restrict__ count, int m,
+                                               int* __restrict__ start) {
+  __shared__ int s[1024];
+  __shared__ int carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int base = 0; base < m; base += 1024) {
+    const int i = base + threadIdx.x;
+    const int v = i < m ? count[i] : 0;
+    s[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+      const int t = threadIdx.x >= o ? s[threadIdx.x - o] : 0;
+      __syncthreads();
+      s[threadIdx.x] += t;
+      __syncthreads();
+    }
+    if (i < m) start[i] = carry + s[threadIdx.x] - v;
+    __syncthreads();
+    if (threadIdx.x == 1023) carry += s[1023];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) start[m] = carry;
+}
+
+template <int METRIC>
+__device__ __forceinline__ void scan_bucket(const Buckets& b, const int2* __restrict__ seeds, int bi,
+                                            int x, int y, uint32_t& bd, int& bl) {
+  for (int j = b.start[bi]; j < b.start[bi + 1]; ++j) {
+    const int c = b.ids[j];
+    const uint32_t d = seed_dist<METRIC>(__ldg(&seeds[c]), x, y);
+    if (d < bd || (d == bd && c < bl)) {
+      bd = d;
+      bl = c;
+    }
+  }
+}
+
+template <int METRIC>
+__global__ void __launch_bounds__(256) k_exact(Buckets b, const int2* __restrict__ seeds, int w, int h,
+                                               int32_t* __restrict__ out_label,
+                                               int32_t* __restrict__ out_dist) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  if (x >= w || y >= h) return;
+  const int cx = x / b.cell, cy = y / b.cell;
+  const int ox = x - cx * b.cell, oy = y - cy * b.cell;
+  const int edge = min(min(ox, b.cell - 1 - ox), min(oy, b.cell - 1 - oy));
+  uint32_t bd = 0xFFFFFFFFu;
+  int bl = -1;
+  const int rmax = max(b.gw, b.gh);
+  for (int r = 0; r <= rmax; ++r) {
+    const int y0 = cy - r, y1 = cy + r, x0 = cx - r, x1 = cx + r;
+    for (int by = max(y0, 0); by <= min(y1, b.gh - 1); ++by) {
+      if (by == y0 || by == y1) {
+        for (int bx = max(x0, 0); bx <= min(x1, b.gw - 1); ++bx)
+          scan_bucket<METRIC>(b, seeds, by * b.gw + bx, x, y, bd, bl);
+      } else {
+        if (x0 >= 0) scan_bucket<METRIC>(b, seeds, by * b.gw + x0, x, y, bd, bl);
+        if (x1 < b.gw) scan_bucket<METRIC>(b, seeds, by * b.gw + x1, x, y, bd, bl);
+      }
+    }
+    // any seed in ring r+1 or beyond is at least this far along one axis
+    const long long lb1 = static_cast<long long>(r) * b.cell + 1 + edge;
+    const long long lb = (METRIC == kManhattan) ? lb1 : lb1 * lb1;
+    if (bl >= 0 && static_cast<long long>(bd) < lb) break;
+  }
+  const int64_t i = static_cast<int64_t>(y) * w + x;
+  if (out_label) out_label[i] = bl;
+  if (out_dist) out_dist[i] = static_cast<int32_t>(bd);
+}
+
+}  // namespace vdk

@@ -1,0 +1,243 @@
+"""Python binding of the C ABI: one :class:`VoronoiSim` per simulation.
+
+Argument marshalling only -- every step runs in ``libvd.so``.  Arrays may be
+numpy arrays (host) or torch tensors (host or CUDA); they must be contiguous
+int32.  PyTorch supplies device memory and streams; it computes nothing here.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _native as N
+
+EUCLID, MANHATTAN = 0, 1
+MOORE, VON_NEUMANN = 0, 1
+
+OPT_FUSE_MAX_K = 1
+OPT_BAND_ORDER_MIN_K = 2
+OPT_USE_GRAPHS = 3
+OPT_FUSE_TILE_X = 4
+OPT_FUSE_TILE_Y = 5
+OPT_PROFILE = 6
+
+KERNEL_KINDS = ("pass", "fused", "stamp", "move", "fill")
+
+MAX_PASSES = 64
+
+
+def _is_torch(a) -> bool:
+    return type(a).__module__.startswith("torch")
+
+
+def _buf(a, n_elems: int | None = None, writable: bool = False):
+    """(pointer, on_device) of a contiguous int32 numpy array or torch tensor."""
+    if a is None:
+        return None, 0
+    if _is_torch(a):
+        import torch
+
+        if a.dtype != torch.int32 or not a.is_contiguous():
+            raise TypeError("tensor must be contiguous int32")
+        if n_elems is not None and a.numel() != n_elems:
+            raise ValueError(f"expected {n_elems} elements, got {a.numel()}")
+        return a.data_ptr(), 1 if a.is_cuda else 0
+    if not isinstance(a, np.ndarray) or a.dtype != np.int32 or not a.flags.c_contiguous:
+        raise TypeError("array must be a C-contiguous int32 numpy array")
+    if writable and not a.flags.writeable:
+        raise ValueError("output array is read-only")
+    if n_elems is not None and a.size != n_elems:
+        raise ValueError(f"expected {n_elems} elements, got {a.size}")
+    return a.ctypes.data, 0
+
+
+def _schedule(fn, *args):
+    ks = np.zeros(MAX_PASSES, np.int32)
+    nbs = np.zeros(MAX_PASSES, np.int32)
+    n = N.check(fn(*args, ks.ctypes.data, nbs.ctypes.data, MAX_PASSES))
+    return [(int(ks[i]), int(nbs[i])) for i in range(min(n, MAX_PASSES))]
+
+
+def jfa_schedule(w: int, h: int, extra: int = 0):
+    """[(k, neighbourhood)] of a JFA frame (Eq. 2)."""
+    return _schedule(N.lib().vd_jfa_schedule, w, h, extra)
+
+
+def djfa_schedule(w: int, h: int, n_seeds: int, d_max: int, vn_waves: int = 2, extra: int = 0):
+    """[(k, neighbourhood)] of a dJFA frame (Eq. 3-4, Section IV-B)."""
+    return _schedule(N.lib().vd_djfa_schedule, w, h, n_seeds, d_max, vn_waves, extra)
+
+
+def _current_stream_handle():
+    try:
+        import torch
+
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except ImportError:
+        pass
+    return 0
+
+
+class VoronoiSim:
+    """A w x h label map with n_seeds moving seeds resident on the GPU."""
+
+    def __init__(self, w: int, h: int, n_seeds: int, stream=None):
+        self._lib = N.lib()
+        handle = self._lib.vd_create(int(w), int(h), int(n_seeds))
+        if not handle:
+            raise N.VDError(N.VD_EINVAL, N.last_error())
+        self._h = ctypes.c_void_p(handle)
+        self.w, self.h, self.n_seeds = int(w), int(h), int(n_seeds)
+        p = ctypes.c_int32()
+        N.check(self._lib.vd_get_shape(self._h, None, None, None, ctypes.byref(p)))
+        self.pitch = p.value
+        self.set_stream(stream)
+
+    # -- lifetime -------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            self._lib.vd_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def handle(self):
+        return self._h
+
+    def set_stream(self, stream=None):
+        """Queue work on ``stream`` (a torch.cuda.Stream, a raw handle, or None =
+        torch's current stream)."""
+        if stream is None:
+            handle = _current_stream_handle()
+        elif hasattr(stream, "cuda_stream"):
+            handle = stream.cuda_stream
+        else:
+            handle = int(stream)
+        self.stream_handle = handle
+        N.check(self._lib.vd_set_stream(self._h, ctypes.c_void_p(handle)))
+
+    def synchronize(self):
+        N.check(self._lib.vd_synchronize(self._h))
+
+    def set_option(self, option: int, value: int):
+        N.check(self._lib.vd_set_option(self._h, option, int(value)))
+
+    def get_option(self, option: int) -> int:
+        v = ctypes.c_int64()
+        N.check(self._lib.vd_get_option(self._h, option, ctypes.byref(v)))
+        return v.value
+
+    def profile(self, reset: bool = False) -> dict:
+        """Per kernel kind: {"ms": total GPU ms, "launches": n, "units": work units}
+        over the launches bracketed since the last reset (needs OPT_PROFILE=1)."""
+        k = len(KERNEL_KINDS)
+        ms = np.zeros(k, np.float64)
+        nl = np.zeros(k, np.int64)
+        un = np.zeros(k, np.int64)
+        N.check(self._lib.vd_profile_read(self._h, ms.ctypes.data, nl.ctypes.data, un.ctypes.data))
+        out = {name: {"ms": float(ms[i]), "launches": int(nl[i]), "units": int(un[i])}
+               for i, name in enumerate(KERNEL_KINDS)}
+        if reset:
+            N.check(self._lib.vd_profile_reset(self._h))
+        return out
+
+    def profile_reset(self):
+        N.check(self._lib.vd_profile_reset(self._h))
+
+    @property
+    def launches(self) -> int:
+        return int(self._lib.vd_launch_count(self._h))
+
+    # -- seeds ----------------------------------------------------------
+    def set_seeds(self, xy):
+        ptr, dev = _buf(xy, 2 * self.n_seeds)
+        N.check(self._lib.vd_set_seeds(self._h, ptr, dev))
+
+    def get_seeds(self, out=None):
+        if out is None:
+            out = np.empty((self.n_seeds, 2), np.int32)
+        ptr, dev = _buf(out, 2 * self.n_seeds, writable=True)
+        N.check(self._lib.vd_get_seeds(self._h, ptr, dev))
+        return out
+
+    def move(self, dxy=None, max_disp: int = 0, rng_seed: int = 0, stream_id: int = 0, step: int = 0):
+        """SimulateParticles: given displacements, or SplitMix64 draws in [-max_disp, max_disp]."""
+        ptr, dev = _buf(dxy, 2 * self.n_seeds)
+        N.check(self._lib.vd_move_seeds(self._h, ptr, dev, int(max_disp), int(rng_seed) & (2**64 - 1),
+                                        int(stream_id) & (2**64 - 1), int(step)))
+
+    # -- frames ---------------------------------------------------------
+    def jfa(self, extra: int = 0, metric: int = EUCLID):
+        N.check(self._lib.vd_jfa(self._h, int(extra), int(metric)))
+
+    def djfa_step(self, d_max: int, vn_waves: int = 2, extra: int = 0, metric: int = EUCLID):
+        N.check(self._lib.vd_djfa_step(self._h, int(d_max), int(vn_waves), int(extra), int(metric)))
+
+    def stamp(self):
+        N.check(self._lib.vd_stamp(self._h))
+
+    def jump_pass(self, k: int, nb: int = MOORE, metric: int = EUCLID):
+        N.check(self._lib.vd_pass(self._h, int(k), int(nb), int(metric)))
+
+    # -- maps -----------------------------------------------------------
+    def set_labels(self, labels):
+        ptr, dev = _buf(labels, self.w * self.h)
+        N.check(self._lib.vd_set_labels(self._h, ptr, dev))
+
+    def labels(self, out=None):
+        """The current label map as a dense (h, w) int32 array (or into ``out``)."""
+        if out is None:
+            out = np.empty((self.h, self.w), np.int32)
+        ptr, dev = _buf(out, self.w * self.h, writable=True)
+        N.check(self._lib.vd_get_labels(self._h, ptr, dev))
+        return out
+
+    def labels_device_ptr(self) -> int:
+        p = ctypes.c_void_p()
+        N.check(self._lib.vd_labels_device_ptr(self._h, ctypes.byref(p)))
+        return int(p.value or 0)
+
+    def similarity(self, exact_dist=None, ref_labels=None, metric: int = EUCLID):
+        """(n_exact, n_match) counts of Section V-A."""
+        n = self.w * self.h
+        pe, de = _buf(exact_dist, n)
+        pr, dr = _buf(ref_labels, n)
+        if exact_dist is not None and ref_labels is not None and de != dr:
+            raise ValueError("both references must live on the same side")
+        on_dev = de if exact_dist is not None else dr
+        ne, nm = ctypes.c_uint64(), ctypes.c_uint64()
+        N.check(self._lib.vd_similarity(self._h, pe, pr, on_dev, int(metric), ctypes.byref(ne), ctypes.byref(nm)))
+        return int(ne.value), int(nm.value)
+
+    def match_count(self, other: "VoronoiSim") -> int:
+        """Pixels whose label equals ``other``'s current label (same grid)."""
+        nm = ctypes.c_uint64()
+        N.check(self._lib.vd_similarity_ctx(self._h, other._h, ctypes.byref(nm)))
+        return int(nm.value)
+
+    def exact(self, labels_out=None, dist_out=None, metric: int = EUCLID):
+        """The exact diagram of Eq. 1 computed on the GPU: (labels, dist)."""
+        if labels_out is None and dist_out is None:
+            labels_out = np.empty((self.h, self.w), np.int32)
+            dist_out = np.empty((self.h, self.w), np.int32)
+        n = self.w * self.h
+        pl, dl = _buf(labels_out, n, writable=True)
+        pd, dd = _buf(dist_out, n, writable=True)
+        if labels_out is not None and dist_out is not None and dl != dd:
+            raise ValueError("both outputs must live on the same side")
+        on_dev = dl if labels_out is not None else dd
+        N.check(self._lib.vd_exact(self._h, pl, pd, on_dev, int(metric)))
+        return labels_out, dist_out

@@ -1,0 +1,277 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+All arithmetic is integer (exact squared distances, lowest-index ties), so every
+comparison is bit-exact: tolerance 0.  Sizes span several tiles and ragged
+edges (widths not a multiple of 4 or 32, odd heights), the degenerate grids
+(1 x 1, 1 x N, N x 1), coinciding seeds, and the full 2048 x 2048, 16384-seed
+workload in the launch configuration the benchmark times.
+"""
+import numpy as np
+import pytest
+
+from paper_2209_00117_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+E, L1 = 0, 1
+M, VN = 0, 1
+
+
+@pytest.fixture(scope="module")
+def vd():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2209_00117_gb300 import build
+
+    build.build()
+    from paper_2209_00117_gb300 import vd as _vd
+
+    return _vd
+
+
+def _sim(vd, w, h, xy, **opts):
+    sim = vd.VoronoiSim(w, h, len(xy))
+    sim.set_seeds(np.ascontiguousarray(xy, np.int32))
+    for k, v in opts.items():
+        sim.set_option(getattr(vd, "OPT_" + k.upper()), v)
+    return sim
+
+
+SHAPES = [(1, 1), (1, 9), (13, 1), (5, 3), (37, 29), (64, 64), (100, 37), (257, 129), (300, 200)]
+
+
+@pytest.mark.parametrize("w,h", SHAPES)
+def test_single_pass_matches_oracle(vd, orc, w, h):
+    g = np.random.default_rng(w * 1000 + h)
+    s = max(1, min(40, w * h // 3))
+    xy = inputs.uniform_seeds(w, h, s, seed=w + h)
+    src = g.integers(-1, s, size=(h, w), dtype=np.int32)
+    sim = _sim(vd, w, h, xy)
+    for k in [1, 2, 3, 4, 5, 6, 8, 12, 16, 64, 256, 1024]:
+        for nb in [M, VN]:
+            for metric in [E, L1]:
+                sim.set_labels(src)
+                sim.jump_pass(k, nb, metric)
+                want = orc.jump_pass(w, h, xy, src, k, nb, metric)
+                got = sim.labels()
+                assert np.array_equal(got, want), (k, nb, metric, int((got != want).sum()))
+    sim.close()
+
+
+@pytest.mark.parametrize("fuse", [0, 2, 4, 8, 16])
+@pytest.mark.parametrize("w,h,s", [(37, 29, 7), (257, 129, 60), (300, 200, 500), (640, 480, 100)])
+def test_jfa_frame_fused_and_unfused(vd, orc, fuse, w, h, s):
+    xy = inputs.uniform_seeds(w, h, s, seed=s)
+    xy[s // 2] = xy[0]  # coinciding seeds
+    for metric in [E, L1]:
+        want = orc.jfa(w, h, xy, metric=metric)
+        for tile in [(64, 32), (32, 8), (128, 16)]:
+            sim = _sim(vd, w, h, xy, fuse_max_k=fuse, fuse_tile_x=tile[0], fuse_tile_y=tile[1])
+            sim.jfa(metric=metric)
+            got = sim.labels()
+            assert np.array_equal(got, want), (fuse, tile, metric, int((got != want).sum()))
+            sim.close()
+
+
+@pytest.mark.parametrize("extra", [0, 1, 2])
+def test_jfa_extra_passes(vd, orc, extra):
+    w, h, s = 333, 222, 90
+    xy = inputs.uniform_seeds(w, h, s, seed=3)
+    sim = _sim(vd, w, h, xy)
+    sim.jfa(extra=extra)
+    np.testing.assert_array_equal(sim.labels(), orc.jfa(w, h, xy, extra=extra))
+    sim.close()
+
+
+def test_degenerate_grids(vd, orc):
+    for w, h, s in [(1, 1, 1), (1, 1, 5), (1, 50, 3), (70, 1, 4), (2, 2, 9), (3, 5, 15)]:
+        xy = inputs.uniform_seeds(w, h, s, seed=w * 7 + h)
+        sim = _sim(vd, w, h, xy)
+        sim.jfa()
+        np.testing.assert_array_equal(sim.labels(), orc.jfa(w, h, xy))
+        prev = sim.labels()
+        sim.djfa_step(d_max=1)
+        np.testing.assert_array_equal(sim.labels(), orc.djfa_step(w, h, xy, prev, d_max=1))
+        sim.close()
+
+
+def test_all_seeds_on_one_pixel(vd, orc):
+    w, h, s = 91, 47, 33
+    xy = np.tile(np.array([[40, 20]], np.int32), (s, 1))
+    sim = _sim(vd, w, h, xy)
+    sim.jfa()
+    lab = sim.labels()
+    assert (lab == 0).all()
+    sim.close()
+
+
+def test_stamp_collisions_lowest_index(vd, orc):
+    w, h = 64, 40
+    g = np.random.default_rng(0)
+    xy = inputs.uniform_seeds(8, 5, 300, seed=1)  # many collisions in an 8 x 5 corner
+    prev = g.integers(0, 300, size=(h, w), dtype=np.int32)
+    sim = _sim(vd, w, h, xy)
+    sim.set_labels(prev)
+    sim.stamp()
+    np.testing.assert_array_equal(sim.labels(), orc.stamp(w, h, xy, prev))
+    sim.close()
+
+
+def test_move_given_and_rng(vd, orc):
+    w, h, s = 500, 300, 4000
+    xy = inputs.uniform_seeds(w, h, s, seed=2)
+    sim = _sim(vd, w, h, xy)
+    d = inputs.displacements(s, 40, 1, seed=2)[0]
+    sim.move(d)
+    cur = orc.move(w, h, xy, d)
+    np.testing.assert_array_equal(sim.get_seeds(), cur)
+    for step in range(3):
+        sim.move(None, max_disp=7, rng_seed=12345, stream_id=9, step=step)
+        cur = orc.move_rng(w, h, cur, 7, 12345, 9, step)
+        np.testing.assert_array_equal(sim.get_seeds(), cur)
+    sim.close()
+
+
+@pytest.mark.parametrize("metric", [E, L1])
+def test_single256_trajectory(vd, orc, metric):
+    """The 256 x 256, 64-seed, 10-step workload: every frame of JFA and of the
+    dJFA chain bit-exact, and the distance-correct counts equal."""
+    w, h, s, steps, D = inputs.SINGLE["single256"]
+    xy = inputs.uniform_seeds(w, h, s, seed=0)
+    disp = inputs.displacements(s, D, steps, seed=0)
+    dj = _sim(vd, w, h, xy)
+    jf = _sim(vd, w, h, xy)
+    dj.jfa(metric=metric)
+    lab = orc.jfa(w, h, xy, metric=metric)
+    np.testing.assert_array_equal(dj.labels(), lab)
+    for t in range(steps):
+        dj.move(disp[t])
+        jf.move(disp[t])
+        xy = orc.move(w, h, xy, disp[t])
+        dj.djfa_step(d_max=D, vn_waves=2, metric=metric)
+        jf.jfa(metric=metric)
+        lab = orc.djfa_step(w, h, xy, lab, d_max=D, vn_waves=2, metric=metric)
+        ref = orc.jfa(w, h, xy, metric=metric)
+        assert np.array_equal(dj.labels(), lab), t
+        assert np.array_equal(jf.labels(), ref), t
+        ed = orc.exact_dist_edt(w, h, xy, metric)
+        assert dj.similarity(exact_dist=ed, ref_labels=ref, metric=metric) == \
+            orc.similarity(w, h, xy, lab, exact_dist=ed, ref_label=ref, metric=metric)
+        assert dj.match_count(jf) == orc.similarity(w, h, xy, lab, ref_label=ref)[1]
+    dj.close()
+    jf.close()
+
+
+def test_graphs_and_band_order_equal_eager(vd, orc):
+    import torch
+
+    w, h, s = 1024, 768, 3000
+    xy = inputs.uniform_seeds(w, h, s, seed=5)
+    disp = inputs.displacements(s, 2, 4, seed=5)
+    stream = torch.cuda.Stream()
+    a = _sim(vd, w, h, xy)
+    b = _sim(vd, w, h, xy, use_graphs=1, band_order_min_k=8)
+    b.set_stream(stream)
+    a.jfa()
+    b.jfa()
+    np.testing.assert_array_equal(a.labels(), b.labels())
+    for t in range(4):
+        for sim in (a, b):
+            sim.move(disp[t])
+            sim.djfa_step(d_max=2)
+        np.testing.assert_array_equal(a.labels(), b.labels())
+        b.jfa()
+        a.jfa()
+        np.testing.assert_array_equal(a.labels(), b.labels())
+    np.testing.assert_array_equal(a.labels(), orc.jfa(w, h, orc.move(w, h, a.get_seeds(), np.zeros((s, 2), np.int32))))
+    a.close()
+    b.close()
+
+
+@pytest.mark.parametrize("w,h,s", [(1, 1, 1), (17, 9, 3), (200, 150, 1), (256, 256, 64),
+                                   (300, 211, 2000), (512, 512, 40000)])
+def test_exact_diagram_matches_brute_force(vd, orc, w, h, s):
+    xy = inputs.uniform_seeds(w, h, s, seed=s)
+    xy[-1] = xy[0]
+    sim = _sim(vd, w, h, xy)
+    for metric in [E, L1]:
+        lab, dist = sim.exact(metric=metric)
+        want_l, want_d = orc.exact_brute(w, h, xy, metric)
+        np.testing.assert_array_equal(dist, want_d)
+        np.testing.assert_array_equal(lab, want_l)
+    sim.close()
+
+
+def test_single2048_full_size(vd, orc):
+    """The 2048 x 2048, 16384-seed, [-2, 2] workload in the benchmark's launch
+    configuration: frame 0 (JFA) and a chain of dJFA steps bit-exact against
+    the oracle, similarity counts equal, distance-correct count vs the EDT."""
+    import torch
+
+    w, h, s, _, D = inputs.SINGLE["single2048"]
+    steps = 4
+    xy = inputs.uniform_seeds(w, h, s, seed=0)
+    disp = inputs.displacements(s, D, steps, seed=0)
+    stream = torch.cuda.Stream()
+    sim = _sim(vd, w, h, xy, use_graphs=1)
+    sim.set_stream(stream)
+    sim.jfa()
+    lab = orc.jfa(w, h, xy)
+    np.testing.assert_array_equal(sim.labels(), lab)
+    for t in range(steps):
+        sim.move(disp[t])
+        sim.djfa_step(d_max=D, vn_waves=2)
+        xy = orc.move(w, h, xy, disp[t])
+        lab = orc.djfa_step(w, h, xy, lab, d_max=D, vn_waves=2)
+        got = sim.labels()
+        assert np.array_equal(got, lab), (t, int((got != lab).sum()))
+    ed = orc.exact_dist_edt(w, h, xy)
+    _, gpu_d = sim.exact()
+    np.testing.assert_array_equal(gpu_d, ed)
+    ref = orc.jfa(w, h, xy)
+    assert sim.similarity(exact_dist=ed, ref_labels=ref) == orc.similarity(w, h, xy, lab, exact_dist=ed, ref_label=ref)
+    sim.close()
+
+
+@pytest.mark.parametrize("s,D", [(1 << 14, 4), (1 << 22, 16)])
+def test_sweep8192_first_frames(vd, orc, s, D):
+    """8192 x 8192 sweep points: JFA frame 0 and dJFA frame 1 bit-exact."""
+    w = h = inputs.SWEEP8192["side"]
+    xy = inputs.uniform_seeds(w, h, s, seed=1)
+    disp = inputs.displacements(s, D, 1, seed=1)[0]
+    sim = _sim(vd, w, h, xy)
+    sim.jfa()
+    lab = orc.jfa(w, h, xy)
+    assert np.array_equal(sim.labels(), lab)
+    sim.move(disp)
+    sim.djfa_step(d_max=D)
+    xy = orc.move(w, h, xy, disp)
+    lab = orc.djfa_step(w, h, xy, lab, d_max=D)
+    assert np.array_equal(sim.labels(), lab)
+    sim.close()
+
+
+def test_invalid_arguments(vd):
+    from paper_2209_00117_gb300._native import VDError
+
+    sim = vd.VoronoiSim(10, 10, 3)
+    with pytest.raises(VDError):
+        sim.set_seeds(np.array([[0, 0], [10, 0], [1, 1]], np.int32))
+    with pytest.raises(VDError):
+        sim.set_labels(np.full((10, 10), 3, np.int32))
+    with pytest.raises(VDError):
+        sim.djfa_step(d_max=-1)
+    with pytest.raises(VDError):
+        sim.jfa(metric=7)
+    with pytest.raises(VDError):
+        sim.set_option(vd.OPT_FUSE_MAX_K, 99)
+    with pytest.raises(VDError):
+        sim.jump_pass(0)
+    import torch
+
+    bad = torch.tensor([[0, 0], [3, 30], [1, 1]], dtype=torch.int32, device="cuda")
+    with pytest.raises(VDError):
+        sim.set_seeds(bad)
+    sim.close()
