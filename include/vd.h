@@ -180,7 +180,9 @@ int vd_stamp(vd_ctx* ctx);
  * IV-B), as inside vd_jfa; exposed for tests and diagnostics. */
 int vd_pass(vd_ctx* ctx, int32_t k, int32_t nb, int32_t metric);
 
-/* Overwrites the label map with a dense w x h map (labels in [-1, n_seeds)). */
+/* Overwrites the label map with a dense w x h map.  Every label must lie in
+ * [-1, n_seeds): VD_EINVAL otherwise (checked on the host for host input, by a
+ * kernel plus a synchronisation for device input) and the map is unchanged. */
 int vd_set_labels(vd_ctx* ctx, const int32_t* labels, int on_device);
 
 /* Copies the label map out as a dense w x h map. */
@@ -219,7 +221,8 @@ int vd_similarity_ctx(vd_ctx* ctx, vd_ctx* ref, uint64_t* n_match);
 int vd_exact(vd_ctx* ctx, int32_t* labels, int32_t* dist, int on_device, int32_t metric);
 
 /* Tuning and execution options (vd_set_option); values are validated. */
-#define VD_OPT_FUSE_MAX_K 1      /* largest step fused into shared-memory groups (0 = no fusion; 1..16) */
+#define VD_OPT_FUSE_MAX_K 1      /* largest step fused into shared-memory groups (0 = no fusion, the
+                                    default; 1..16) */
 #define VD_OPT_BAND_ORDER_MIN_K 2 /* step from which large-k passes visit rows in k-strided bands (0 = never) */
 #define VD_OPT_USE_GRAPHS 3      /* 1 = replay each frame's launches as a cached CUDA graph */
 #define VD_OPT_FUSE_TILE_X 4     /* fused-group tile width in pixels (multiple of 4, 16..256) */

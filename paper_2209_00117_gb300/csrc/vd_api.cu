@@ -154,7 +154,7 @@ int launch_pass(const MapView& m, const int32_t* src, int32_t* dst, int32_t k, i
   vdk::PassArgs a;
   a.src = src;
   a.dst = dst;
-  a.seeds = m.seeds;
+  a.table = m.table;
   a.n_seeds = static_cast<uint32_t>(m.n);
   a.w = m.w;
   a.h = m.h;
@@ -199,7 +199,7 @@ int launch_fused(const MapView& m, const int32_t* src, int32_t* dst, const int32
   std::memset(&a, 0, sizeof(a));
   a.src = src;
   a.dst = dst;
-  a.seeds = m.seeds;
+  a.table = m.table;
   a.n_seeds = static_cast<uint32_t>(m.n);
   a.w = m.w;
   a.h = m.h;
@@ -305,10 +305,15 @@ int launch_stamp(const MapView& m, int32_t* labels, bool mark, cudaStream_t st, 
   return vd_cuda_check(cudaGetLastError(), "stamp launch");
 }
 
-int launch_move(int2* seeds, int n, const int2* dxy, int w, int h, int max_disp, uint64_t key,
-                uint64_t step, cudaStream_t st) {
-  vdk::k_move<<<grid1d(n, 256), 256, 0, st>>>(seeds, n, dxy, w, h, max_disp, key, step);
+int launch_move(int2* seeds, int2* table, int n, const int2* dxy, int w, int h, int max_disp,
+                uint64_t key, uint64_t step, cudaStream_t st) {
+  vdk::k_move<<<grid1d(n, 256), 256, 0, st>>>(seeds, table, n, dxy, w, h, max_disp, key, step);
   return vd_cuda_check(cudaGetLastError(), "move launch");
+}
+
+int launch_build_table(const int2* seeds, int n, int2* table, cudaStream_t st) {
+  vdk::k_build_table<<<grid1d(n, 256), 256, 0, st>>>(seeds, n, table);
+  return vd_cuda_check(cudaGetLastError(), "table launch");
 }
 
 uint64_t rng_key(uint64_t rng_seed, uint64_t stream_id) { return vdk::splitmix64(rng_seed, stream_id); }
@@ -394,6 +399,7 @@ struct vd_ctx {
   int32_t* buf[2] = {nullptr, nullptr};
   int cur = 0;
   int2* seeds = nullptr;
+  int2* table = nullptr;  // n + 1 entries, [0] = sentinel
   int2* dxy_stage = nullptr;
   unsigned long long* counters = nullptr;      // [0] n_exact, [1] n_match, [2] flag
   unsigned long long* host_counters = nullptr;  // pinned mirror
@@ -419,6 +425,7 @@ static vdi::MapView view(const vd_ctx* c) {
   m.pitch = c->pitch;
   m.n = c->n;
   m.seeds = c->seeds;
+  m.table = c->table + 1;
   return m;
 }
 
@@ -439,6 +446,7 @@ static void ctx_free(vd_ctx* c) {
   cudaFree(c->buf[0]);
   cudaFree(c->buf[1]);
   cudaFree(c->seeds);
+  cudaFree(c->table);
   cudaFree(c->dxy_stage);
   cudaFree(c->counters);
   cudaFreeHost(c->host_counters);
@@ -469,6 +477,7 @@ extern "C" vd_ctx* vd_create(int32_t w, int32_t h, int32_t n) {
   rc = rc ? rc : ctx_alloc(reinterpret_cast<void**>(&c->buf[0]), map_bytes, "label map");
   rc = rc ? rc : ctx_alloc(reinterpret_cast<void**>(&c->buf[1]), map_bytes, "label map");
   rc = rc ? rc : ctx_alloc(reinterpret_cast<void**>(&c->seeds), sizeof(int2) * n, "seeds");
+  rc = rc ? rc : ctx_alloc(reinterpret_cast<void**>(&c->table), sizeof(int2) * (static_cast<size_t>(n) + 1), "seed table");
   rc = rc ? rc : ctx_alloc(reinterpret_cast<void**>(&c->dxy_stage), sizeof(int2) * n, "moves");
   rc = rc ? rc : ctx_alloc(reinterpret_cast<void**>(&c->counters), 4 * sizeof(unsigned long long), "counters");
   if (!rc) {
@@ -478,6 +487,7 @@ extern "C" vd_ctx* vd_create(int32_t w, int32_t h, int32_t n) {
   if (!rc) rc = vd_cuda_check(cudaMemset(c->buf[0], 0xFF, map_bytes), "init map");
   if (!rc) rc = vd_cuda_check(cudaMemset(c->buf[1], 0xFF, map_bytes), "init map");
   if (!rc) rc = vd_cuda_check(cudaMemset(c->seeds, 0, sizeof(int2) * n), "init seeds");
+  if (!rc) rc = vdi::launch_build_table(c->seeds, n, c->table, nullptr);
   if (!rc) rc = vd_cuda_check(cudaDeviceSynchronize(), "create");
   if (rc) {
     ctx_free(c);
@@ -534,9 +544,13 @@ extern "C" int vd_set_seeds(vd_ctx* c, const int32_t* xy, int on_device) {
         return vd_fail(VD_EINVAL, "seed %d at (%d, %d) outside the %dx%d grid", k, x, y, c->w, c->h);
     }
   }
-  if (!on_device)
-    return vd_cuda_check(cudaMemcpyAsync(c->seeds, xy, sizeof(int2) * c->n, cudaMemcpyHostToDevice, c->stream),
-                         "copy seeds");
+  if (!on_device) {
+    const int rc = vd_cuda_check(cudaMemcpyAsync(c->seeds, xy, sizeof(int2) * c->n, cudaMemcpyHostToDevice, c->stream),
+                                 "copy seeds");
+    if (rc) return rc;
+    ++c->launches;
+    return vdi::launch_build_table(c->seeds, c->n, c->table, c->stream);
+  }
   // device input: validate in the staging buffer so that rejected seeds never
   // reach the kernels that index the map with them
   int rc = vd_cuda_check(cudaMemcpyAsync(c->dxy_stage, xy, sizeof(int2) * c->n, cudaMemcpyDeviceToDevice, c->stream),
@@ -552,8 +566,11 @@ extern "C" int vd_set_seeds(vd_ctx* c, const int32_t* xy, int on_device) {
   if (rc) return rc;
   if (c->host_counters[2] != 0)
     return vd_fail(VD_EINVAL, "%llu device seeds outside the %dx%d grid", c->host_counters[2], c->w, c->h);
-  return vd_cuda_check(cudaMemcpyAsync(c->seeds, c->dxy_stage, sizeof(int2) * c->n, cudaMemcpyDeviceToDevice, c->stream),
-                       "copy seeds");
+  rc = vd_cuda_check(cudaMemcpyAsync(c->seeds, c->dxy_stage, sizeof(int2) * c->n, cudaMemcpyDeviceToDevice, c->stream),
+                     "copy seeds");
+  if (rc) return rc;
+  ++c->launches;
+  return vdi::launch_build_table(c->seeds, c->n, c->table, c->stream);
 }
 
 extern "C" int vd_get_seeds(vd_ctx* c, int32_t* xy, int on_device) {
@@ -585,8 +602,8 @@ extern "C" int vd_move_seeds(vd_ctx* c, const int32_t* dxy, int dxy_on_device, i
   }
   vdi::Profiler* pr = prof_of(c);
   const int pi = pr ? pr->begin(VD_KERNEL_MOVE, c->n, c->stream) : -1;
-  const int rc = vdi::launch_move(c->seeds, c->n, d, c->w, c->h, max_disp, vdi::rng_key(rng_seed, stream_id),
-                                  static_cast<uint64_t>(step), c->stream);
+  const int rc = vdi::launch_move(c->seeds, c->table, c->n, d, c->w, c->h, max_disp,
+                                  vdi::rng_key(rng_seed, stream_id), static_cast<uint64_t>(step), c->stream);
   if (pr) pr->end(pi, c->stream);
   ++c->launches;
   return rc;
@@ -703,11 +720,27 @@ extern "C" int vd_pass(vd_ctx* c, int32_t k, int32_t nb, int32_t metric) {
 extern "C" int vd_set_labels(vd_ctx* c, const int32_t* labels, int on_device) {
   VD_CHECK_CTX(c);
   if (!labels) return vd_fail(VD_EINVAL, "null labels");
+  const int64_t total = static_cast<int64_t>(c->w) * c->h;
   if (!on_device) {
-    const int64_t total = static_cast<int64_t>(c->w) * c->h;
     for (int64_t i = 0; i < total; ++i)
       if (labels[i] < -1 || labels[i] >= c->n)
         return vd_fail(VD_EINVAL, "label %d at %lld outside [-1, %d)", labels[i], static_cast<long long>(i), c->n);
+  } else {
+    // the passes index the seed table with every label: reject out-of-range
+    // device labels before they reach the map
+    int rc = vd_cuda_check(cudaMemsetAsync(c->counters + 2, 0, sizeof(unsigned long long), c->stream), "memset");
+    if (rc) return rc;
+    int blocks = static_cast<int>((total + 255) / 256);
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    vdk::k_check_labels<<<blocks, 256, 0, c->stream>>>(labels, total, c->n, c->counters + 2);
+    ++c->launches;
+    rc = vd_cuda_check(cudaGetLastError(), "check labels");
+    if (!rc) rc = vd_cuda_check(cudaMemcpyAsync(c->host_counters + 2, c->counters + 2, sizeof(unsigned long long),
+                                                cudaMemcpyDeviceToHost, c->stream), "copy flag");
+    if (!rc) rc = vd_cuda_check(cudaStreamSynchronize(c->stream), "synchronize");
+    if (rc) return rc;
+    if (c->host_counters[2] != 0)
+      return vd_fail(VD_EINVAL, "%llu device labels outside [-1, %d)", c->host_counters[2], c->n);
   }
   return vd_cuda_check(cudaMemcpy2DAsync(c->buf[c->cur], sizeof(int32_t) * c->pitch, labels, sizeof(int32_t) * c->w,
                                          sizeof(int32_t) * c->w, c->h, kind_from(on_device), c->stream),

@@ -18,11 +18,12 @@ namespace vdi {
 struct MapView {
   int32_t w = 0, h = 0, pitch = 0, n = 0;
   const int2* seeds = nullptr;
+  const int2* table = nullptr;  // pass table, entry -1 = sentinel
 };
 
 // Launch-shape choices of the jump passes.
 struct Tuning {
-  int fuse_max_k = 8;     // steps <= this run in shared-memory groups
+  int fuse_max_k = 0;     // steps <= this run in shared-memory groups (0 = none)
   int max_halo = 32;      // largest sum of steps in one group
   int64_t band_min_k = -1;  // -1 auto, 0 never, else from this step up
   int use_graphs = 0;
@@ -77,8 +78,9 @@ int run_passes(const MapView& m, int32_t* const buf[2], int* cur, const int32_t*
                int64_t* launches, Profiler* prof);
 int launch_fill(int32_t* buf, int64_t n_elems, int32_t v, cudaStream_t st);
 int launch_stamp(const MapView& m, int32_t* labels, bool mark, cudaStream_t st, int64_t* launches);
-int launch_move(int2* seeds, int n, const int2* dxy, int w, int h, int max_disp, uint64_t key,
-                uint64_t step, cudaStream_t st);
+int launch_move(int2* seeds, int2* table, int n, const int2* dxy, int w, int h, int max_disp,
+                uint64_t key, uint64_t step, cudaStream_t st);
+int launch_build_table(const int2* seeds, int n, int2* table, cudaStream_t st);
 uint64_t rng_key(uint64_t rng_seed, uint64_t stream_id);
 int ensure_smem(const void* fn, size_t bytes, size_t* done);
 

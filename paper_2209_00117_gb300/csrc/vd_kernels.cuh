@@ -27,9 +27,58 @@ __device__ __forceinline__ uint32_t seed_dist(int2 s, int x, int y) {
   return static_cast<uint32_t>(dx * dx + dy * dy);
 }
 
-// The distance comparison of Section III as a total order: a candidate seed c
-// replaces the incumbent (bd, bl) when it is nearer to the pixel, or equally
-// near with a lower index.  Labels outside [0, n) (-1 = empty) are skipped.
+// Seed table entry used by the jump passes: {x | y << 16, x^2 + y^2}, 8 bytes
+// (the passes are bound by the bytes that gathers return to registers, so
+// the entry is kept as small as the key allows).  The table is stored with one
+// sentinel entry in front, so entry -1 (the empty label) reads {0, INT32_MAX}:
+// an empty candidate then loses every Euclidean comparison without a branch.
+//
+// Euclidean pass key for pixel q = (x, y) and seed s:
+//   key = |s|^2 - 2 x s.x - 2 y s.y = d^2(s, q) - |q|^2,
+// which orders the candidates of one pixel exactly as d^2 does (|q|^2 is the
+// same for all of them), costs two multiply-adds and fits in int32.
+// Manhattan key: |s.x - x| + |s.y - y|, with the empty label forced to a key
+// above any real one.
+constexpr int kSentinelNorm = 0x7FFFFFFF;
+
+__device__ __forceinline__ int2 table_entry(int2 p) {
+  return make_int2(p.x | (p.y << 16), p.x * p.x + p.y * p.y);
+}
+
+template <int METRIC>
+__device__ __forceinline__ int table_key(int2 e, int c, int m2x, int m2y, int x, int y) {
+  const int sx = e.x & 0xFFFF;
+  const int sy = static_cast<int>(static_cast<unsigned int>(e.x) >> 16);
+  if (METRIC == kManhattan) return c < 0 ? 0x40000000 : abs(sx - x) + abs(sy - y);
+  // two's-complement wrap of the intermediate sums is harmless: the final
+  // value is exact (|key| < 2^31)
+  return static_cast<int>(static_cast<uint32_t>(e.y) + static_cast<uint32_t>(m2x) * static_cast<uint32_t>(sx) +
+                          static_cast<uint32_t>(m2y) * static_cast<uint32_t>(sy));
+}
+
+// (key, label) packed into one int64: the signed high word orders by key, the
+// low word (label as unsigned) breaks ties toward the lowest index, so the
+// distance comparison of Section III with its lowest-index tie rule is one
+// 64-bit minimum.  Label -1 only ever comes with the sentinel key.
+__device__ __forceinline__ long long pack_key(int key, int c) {
+  return (static_cast<long long>(key) << 32) | static_cast<unsigned int>(c);
+}
+
+template <int METRIC>
+__device__ __forceinline__ long long cand(int c, const int2* __restrict__ table, int m2x, int m2y, int x,
+                                          int y) {
+  const int2 e = __ldg(&table[c]);
+  return pack_key(table_key<METRIC>(e, c, m2x, m2y, x, y), c);
+}
+
+// Folds candidate c into the packed best b.
+template <int METRIC>
+__device__ __forceinline__ long long fold(long long b, int c, const int2* __restrict__ table, int m2x,
+                                          int m2y, int x, int y) {
+  return min(b, cand<METRIC>(c, table, m2x, m2y, x, y));
+}
+
+// Kept for the kernels that read plain int2 positions (similarity, exact).
 template <int METRIC>
 __device__ __forceinline__ void consider(int c, const int2* __restrict__ seeds, uint32_t n, int x,
                                          int y, uint32_t& bd, int& bl) {
@@ -42,136 +91,155 @@ __device__ __forceinline__ void consider(int c, const int2* __restrict__ seeds, 
   }
 }
 
-template <int METRIC>
-__device__ __forceinline__ void init_best(int c, const int2* __restrict__ seeds, uint32_t n, int x,
-                                          int y, uint32_t& bd, int& bl) {
-  if (static_cast<uint32_t>(c) < n) {
-    bl = c;
-    bd = seed_dist<METRIC>(__ldg(&seeds[c]), x, y);
-  } else {
-    bl = -1;
-    bd = 0xFFFFFFFFu;
-  }
-}
-
 __device__ __forceinline__ int4 ld4(const int32_t* p) {
   return __ldg(reinterpret_cast<const int4*>(p));
-}
-
-__device__ __forceinline__ int elem(const int4& v, int i) {
-  return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w));
-}
-
-// Element j in [0, 12) of the concatenation a | b | c.
-__device__ __forceinline__ int elem3(const int4& a, const int4& b, const int4& c, int j) {
-  return j < 4 ? elem(a, j) : (j < 8 ? elem(b, j - 4) : elem(c, j - 8));
 }
 
 struct PassArgs {
   const int32_t* __restrict__ src;
   int32_t* __restrict__ dst;
-  const int2* __restrict__ seeds;
+  const int2* __restrict__ table;  // entry -1 is the sentinel
   uint32_t n_seeds;
   int w, h, pitch, k;
   int band_m;  // > 1: visit row-blocks in k-strided bands (band_m = k / rows per block)
   int band_t;  // row-blocks per band residue class
 };
 
-// The three label vectors of one source row seen by a thread that owns the
-// four pixels x0 .. x0+3: left[i] = L(x0+i-k), mid[i] = L(x0+i), right[i] =
-// L(x0+i+k).  KSEL 0: k is a multiple of 4 (aligned vector loads); KSEL 1/2:
-// k = 1/2 (three aligned vectors, shifted); KSEL 3: any other k (scalar).
-template <int KSEL>
-__device__ __forceinline__ void load_row(const int32_t* __restrict__ row, int x0, int k, int w,
-                                         int pitch, bool need_sides, int4& left, int4& mid,
-                                         int4& right) {
-  const int4 neg = make_int4(-1, -1, -1, -1);
-  mid = ld4(row + x0);
-  if (!need_sides) {
-    left = neg;
-    right = neg;
-    return;
-  }
-  if (KSEL == 0) {
-    left = (x0 - k >= 0) ? ld4(row + x0 - k) : neg;
-    right = (x0 + k < pitch) ? ld4(row + x0 + k) : neg;
-  } else if (KSEL == 1 || KSEL == 2) {
-    const int4 a = (x0 >= 4) ? ld4(row + x0 - 4) : neg;
-    const int4 c = (x0 + 4 < pitch) ? ld4(row + x0 + 4) : neg;
-    left.x = elem3(a, mid, c, 4 - KSEL);
-    left.y = elem3(a, mid, c, 5 - KSEL);
-    left.z = elem3(a, mid, c, 6 - KSEL);
-    left.w = elem3(a, mid, c, 7 - KSEL);
-    right.x = elem3(a, mid, c, 4 + KSEL);
-    right.y = elem3(a, mid, c, 5 + KSEL);
-    right.z = elem3(a, mid, c, 6 + KSEL);
-    right.w = elem3(a, mid, c, 7 + KSEL);
-  } else {
-    int l[4], r[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int xl = x0 + i - k;
-      const int xr = x0 + i + k;
-      l[i] = (xl >= 0 && xl < w) ? __ldg(row + xl) : -1;
-      r[i] = (xr >= 0 && xr < w) ? __ldg(row + xr) : -1;
-    }
-    left = make_int4(l[0], l[1], l[2], l[3]);
-    right = make_int4(r[0], r[1], r[2], r[3]);
-  }
+// Stops the compiler from hoisting later loads above this point, which keeps
+// only one neighbour group's gathers in flight per thread (the register
+// budget of 6 blocks/SM) and leaves latency hiding to the many resident warps.
+__device__ __forceinline__ void group_fence() { asm volatile("" ::: "memory"); }
+
+__device__ __forceinline__ int4 shift_left_by(const int4& l, const int4& m, int kk) {
+  // labels at x0 - kk + i, i = 0..3, from the vectors at x0 - 4 (l) and x0 (m)
+  return kk == 1 ? make_int4(l.w, m.x, m.y, m.z) : make_int4(l.z, l.w, m.x, m.y);
 }
 
-// One jump pass (Table I / Section IV-B) over the whole map: every thread
-// owns four horizontally adjacent pixels, reads the 3 x 3 (Moore) or plus
-// (Von Neumann) pattern of label vectors at offset k with 16-byte loads and
-// writes four labels with one 16-byte store.
+__device__ __forceinline__ int4 shift_right_by(const int4& m, const int4& r, int kk) {
+  // labels at x0 + kk + i from the vectors at x0 (m) and x0 + 4 (r)
+  return kk == 1 ? make_int4(m.y, m.z, m.w, r.x) : make_int4(m.z, m.w, r.x, r.y);
+}
+
+// The four pixels (x0 .. x0+3, y) owned by one thread and their packed
+// best (key, label) so far.
+template <int METRIC>
+struct Quad {
+  long long b0, b1, b2, b3;
+  int m2x, m2y, x0, y;
+  __device__ __forceinline__ void init(const int4& L, const int2* __restrict__ table) {
+    b0 = cand<METRIC>(L.x, table, m2x, m2y, x0, y);
+    b1 = cand<METRIC>(L.y, table, m2x - 2, m2y, x0 + 1, y);
+    b2 = cand<METRIC>(L.z, table, m2x - 4, m2y, x0 + 2, y);
+    b3 = cand<METRIC>(L.w, table, m2x - 6, m2y, x0 + 3, y);
+  }
+  __device__ __forceinline__ void fold4(const int4& L, const int2* __restrict__ table) {
+    b0 = fold<METRIC>(b0, L.x, table, m2x, m2y, x0, y);
+    b1 = fold<METRIC>(b1, L.y, table, m2x - 2, m2y, x0 + 1, y);
+    b2 = fold<METRIC>(b2, L.z, table, m2x - 4, m2y, x0 + 2, y);
+    b3 = fold<METRIC>(b3, L.w, table, m2x - 6, m2y, x0 + 3, y);
+  }
+};
+
+// Labels at columns x0 + dx .. x0 + dx + 3 of one row for |dx| = k, a multiple
+// of 4 (one aligned 16-byte load); columns outside [0, pitch) read as -1 and
+// the row padding [w, pitch) holds -1 already.
+__device__ __forceinline__ int4 load_side(const int32_t* __restrict__ row, int x0, int dx, int pitch) {
+  const int xs = x0 + dx;
+  return (xs >= 0 && xs < pitch) ? ld4(row + xs) : make_int4(-1, -1, -1, -1);
+}
+
+__device__ __forceinline__ int4 load_scalar4(const int32_t* __restrict__ row, int xs, int w) {
+  int v[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) v[i] = (xs + i >= 0 && xs + i < w) ? __ldg(row + xs + i) : -1;
+  return make_int4(v[0], v[1], v[2], v[3]);
+}
+
+// The side candidates (x -/+ k) of one source row for the four pixels of a
+// thread; `mid` is that row's aligned vector at x0 when already loaded.
+template <int KSEL, int METRIC>
+__device__ __forceinline__ void fold_sides(Quad<METRIC>& q, const int32_t* __restrict__ row, const int4& mid,
+                                           const PassArgs& a, const int2* __restrict__ table) {
+  const int x0 = q.x0;
+  if (KSEL == 0) {
+    const int4 L = load_side(row, x0, -a.k, a.pitch);
+    const int4 R = load_side(row, x0, a.k, a.pitch);
+    q.fold4(L, table);
+    group_fence();
+    q.fold4(R, table);
+  } else if (KSEL == 1 || KSEL == 2) {
+    const int4 neg = make_int4(-1, -1, -1, -1);
+    const int4 lv = (x0 >= 4) ? ld4(row + x0 - 4) : neg;
+    const int4 rv = (x0 + 4 < a.pitch) ? ld4(row + x0 + 4) : neg;
+    q.fold4(shift_left_by(lv, mid, KSEL), table);
+    group_fence();
+    q.fold4(shift_right_by(mid, rv, KSEL), table);
+  } else {
+    const int4 L = load_scalar4(row, x0 - a.k, a.w);
+    const int4 R = load_scalar4(row, x0 + a.k, a.w);
+    q.fold4(L, table);
+    group_fence();
+    q.fold4(R, table);
+  }
+  group_fence();
+}
+
+// One jump pass (Table I / Section IV-B) over the whole map.  Every thread
+// owns four horizontally adjacent pixels: it starts from their own labels and
+// folds in the neighbour offsets one source row at a time (16-byte label
+// loads, four seed-table gathers and four packed-key minimums per offset).
+// Candidate order does not matter: the packed minimum is a total order.
 template <int NB, int METRIC, int KSEL>
-__global__ void __launch_bounds__(256) k_pass(PassArgs a) {
+__global__ void __launch_bounds__(256, 6) k_pass(PassArgs a) {
   const int x0 = 4 * static_cast<int>(blockIdx.x * blockDim.x + threadIdx.x);
   int rb = blockIdx.y;
   if (a.band_m > 1) rb = (blockIdx.y % a.band_t) * a.band_m + blockIdx.y / a.band_t;
   const int y = rb * static_cast<int>(blockDim.y) + static_cast<int>(threadIdx.y);
   if (x0 >= a.pitch || y >= a.h) return;
 
-  const int4 neg = make_int4(-1, -1, -1, -1);
-  int4 uL, uM, uR, cL, cM, cR, dL, dM, dR;
-  const bool moore = (NB == kMoore);
   const int64_t pitch = a.pitch;
-  load_row<KSEL>(a.src + y * pitch, x0, a.k, a.w, a.pitch, true, cL, cM, cR);
-  if (y - a.k >= 0) {
-    load_row<KSEL>(a.src + (y - a.k) * pitch, x0, a.k, a.w, a.pitch, moore, uL, uM, uR);
-  } else {
-    uL = uM = uR = neg;
-  }
-  if (y + a.k < a.h) {
-    load_row<KSEL>(a.src + (y + a.k) * pitch, x0, a.k, a.w, a.pitch, moore, dL, dM, dR);
-  } else {
-    dL = dM = dR = neg;
-  }
-
-  int out[4];
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int x = x0 + i;
-    if (x >= a.w) {
-      out[i] = -1;
-      continue;
+  const int2* __restrict__ table = a.table;
+  Quad<METRIC> q;
+  q.m2y = -2 * y;
+  q.m2x = -2 * x0;
+  q.x0 = x0;
+  q.y = y;
+  const int32_t* crow = a.src + y * pitch;
+  const int4 own = ld4(crow + x0);
+  // the first up-row vector is in flight while the own labels are scored
+  const bool up_ok = y - a.k >= 0;
+  const bool dn_ok = y + a.k < a.h;
+  const int32_t* urow = a.src + (y - a.k) * pitch;
+  const int32_t* drow = a.src + (y + a.k) * pitch;
+  const int4 neg = make_int4(-1, -1, -1, -1);
+  const int4 um = up_ok ? ld4(urow + x0) : neg;
+  q.init(own, table);
+  group_fence();
+  // centre row: (-k, 0), (+k, 0)
+  fold_sides<KSEL, METRIC>(q, crow, own, a, table);
+  // up row: (0, -k) and, for Moore, (-k, -k), (+k, -k)
+  if (up_ok) {
+    const int4 dm = dn_ok ? ld4(drow + x0) : neg;
+    q.fold4(um, table);
+    group_fence();
+    if (NB == kMoore) fold_sides<KSEL, METRIC>(q, urow, um, a, table);
+    if (dn_ok) {
+      q.fold4(dm, table);
+      group_fence();
+      if (NB == kMoore) fold_sides<KSEL, METRIC>(q, drow, dm, a, table);
     }
-    uint32_t bd;
-    int bl;
-    init_best<METRIC>(elem(cM, i), a.seeds, a.n_seeds, x, y, bd, bl);
-    consider<METRIC>(elem(cR, i), a.seeds, a.n_seeds, x, y, bd, bl);
-    consider<METRIC>(elem(cL, i), a.seeds, a.n_seeds, x, y, bd, bl);
-    consider<METRIC>(elem(dM, i), a.seeds, a.n_seeds, x, y, bd, bl);
-    consider<METRIC>(elem(uM, i), a.seeds, a.n_seeds, x, y, bd, bl);
-    if (NB == kMoore) {
-      consider<METRIC>(elem(dR, i), a.seeds, a.n_seeds, x, y, bd, bl);
-      consider<METRIC>(elem(dL, i), a.seeds, a.n_seeds, x, y, bd, bl);
-      consider<METRIC>(elem(uL, i), a.seeds, a.n_seeds, x, y, bd, bl);
-      consider<METRIC>(elem(uR, i), a.seeds, a.n_seeds, x, y, bd, bl);
-    }
-    out[i] = bl;
+  } else if (dn_ok) {
+    const int4 dm = ld4(drow + x0);
+    q.fold4(dm, table);
+    group_fence();
+    if (NB == kMoore) fold_sides<KSEL, METRIC>(q, drow, dm, a, table);
   }
-  *reinterpret_cast<int4*>(a.dst + y * pitch + x0) = make_int4(out[0], out[1], out[2], out[3]);
+  int4 out;
+  out.x = (x0 < a.w) ? static_cast<int>(static_cast<unsigned int>(q.b0)) : -1;
+  out.y = (x0 + 1 < a.w) ? static_cast<int>(static_cast<unsigned int>(q.b1)) : -1;
+  out.z = (x0 + 2 < a.w) ? static_cast<int>(static_cast<unsigned int>(q.b2)) : -1;
+  out.w = (x0 + 3 < a.w) ? static_cast<int>(static_cast<unsigned int>(q.b3)) : -1;
+  *reinterpret_cast<int4*>(a.dst + y * pitch + x0) = out;
 }
 
 // ---------------------------------------------------------------------------
@@ -183,7 +251,7 @@ constexpr int kMaxFused = 8;
 struct FusedArgs {
   const int32_t* __restrict__ src;
   int32_t* __restrict__ dst;
-  const int2* __restrict__ seeds;
+  const int2* __restrict__ table;  // entry -1 is the sentinel
   uint32_t n_seeds;
   int w, h, pitch;
   int n_pass;
@@ -240,20 +308,19 @@ __global__ void __launch_bounds__(256) k_pass_fused(FusedArgs a) {
         int res = -1;
         if (x >= 0 && x < a.w && y >= 0 && y < a.h) {
           const int32_t* c = A + sy * SW + sx;
-          uint32_t bd;
-          int bl;
-          init_best<METRIC>(c[0], a.seeds, a.n_seeds, x, y, bd, bl);
-          consider<METRIC>(c[k], a.seeds, a.n_seeds, x, y, bd, bl);
-          consider<METRIC>(c[-k], a.seeds, a.n_seeds, x, y, bd, bl);
-          consider<METRIC>(c[k * SW], a.seeds, a.n_seeds, x, y, bd, bl);
-          consider<METRIC>(c[-k * SW], a.seeds, a.n_seeds, x, y, bd, bl);
+          const int m2x = -2 * x, m2y = -2 * y;
+          long long b = cand<METRIC>(c[0], a.table, m2x, m2y, x, y);
+          b = fold<METRIC>(b, c[k], a.table, m2x, m2y, x, y);
+          b = fold<METRIC>(b, c[-k], a.table, m2x, m2y, x, y);
+          b = fold<METRIC>(b, c[k * SW], a.table, m2x, m2y, x, y);
+          b = fold<METRIC>(b, c[-k * SW], a.table, m2x, m2y, x, y);
           if (moore) {
-            consider<METRIC>(c[k * SW + k], a.seeds, a.n_seeds, x, y, bd, bl);
-            consider<METRIC>(c[k * SW - k], a.seeds, a.n_seeds, x, y, bd, bl);
-            consider<METRIC>(c[-k * SW - k], a.seeds, a.n_seeds, x, y, bd, bl);
-            consider<METRIC>(c[-k * SW + k], a.seeds, a.n_seeds, x, y, bd, bl);
+            b = fold<METRIC>(b, c[k * SW + k], a.table, m2x, m2y, x, y);
+            b = fold<METRIC>(b, c[k * SW - k], a.table, m2x, m2y, x, y);
+            b = fold<METRIC>(b, c[-k * SW - k], a.table, m2x, m2y, x, y);
+            b = fold<METRIC>(b, c[-k * SW + k], a.table, m2x, m2y, x, y);
           }
-          res = bl;
+          res = static_cast<int>(static_cast<unsigned int>(b));
         }
         B[sy * SW + sx] = res;
       }
@@ -294,9 +361,28 @@ __device__ __forceinline__ int rng_disp(uint64_t key, uint64_t step, uint64_t k,
   return static_cast<int>(((draw >> 32) * m) >> 32) - max_disp;
 }
 
-// SimulateParticles (Algorithm 1): p_k <- clamp(p_k + delta_k) on the grid.
-__global__ void k_move(int2* __restrict__ seeds, int n, const int2* __restrict__ dxy, int w, int h,
-                       int max_disp, uint64_t key, uint64_t step) {
+// Rebuilds the pass table (entry k + 1 for seed k; entry 0 the sentinel).
+__global__ void k_build_table(const int2* __restrict__ seeds, int n, int2* __restrict__ table) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k == 0) table[0] = make_int2(0, kSentinelNorm);
+  if (k < n) table[k + 1] = table_entry(seeds[k]);
+}
+
+// Flags any label outside [-1, n) (device-side input validation).
+__global__ void k_check_labels(const int32_t* __restrict__ labels, int64_t count, int n,
+                               unsigned long long* __restrict__ bad) {
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < count;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int l = labels[i];
+    if (l < -1 || l >= n) atomicAdd(bad, 1ULL);
+  }
+}
+
+// SimulateParticles (Algorithm 1): p_k <- clamp(p_k + delta_k) on the grid;
+// also refreshes the seed's pass-table entry.
+__global__ void k_move(int2* __restrict__ seeds, int2* __restrict__ table, int n,
+                       const int2* __restrict__ dxy, int w, int h, int max_disp, uint64_t key,
+                       uint64_t step) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n) return;
   int2 p = seeds[k];
@@ -315,6 +401,7 @@ __global__ void k_move(int2* __restrict__ seeds, int n, const int2* __restrict__
   p.x = static_cast<int>(x);
   p.y = static_cast<int>(y);
   seeds[k] = p;
+  table[k + 1] = table_entry(p);
 }
 
 // Stamp, first half: every seed pixel is overwritten with one of the indices
