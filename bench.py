@@ -1,8 +1,10 @@
 #!/usr/bin/env python
 """Benchmark: dJFA vs JFA frames of a moving-seed Voronoi simulation on GB300.
 
-One step = one simulation timestep of the hot path on one 2048 x 2048 grid with
-16384 uniform seeds moving by uniform integers in [-2, 2] per axis: the seed
+One step = one simulation timestep of the hot path.  By default (``single2048``)
+that is one 2048 x 2048 grid with 16384 uniform seeds moving by uniform
+integers in [-2, 2] per axis (``--workload sweep8192 --seeds S --max-disp D``
+selects a point of the 8192 x 8192 sweep instead): the seed
 move (Algorithm 1's SimulateParticles), the stamp and the dJFA passes of Eq. 4
 (6 passes, the first two Von Neumann).  The same trajectory is also run with a
 full JFA frame per step (11 passes, Eq. 2) for the speedup, and every 10th frame
@@ -47,7 +49,10 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="single2048")
+    ap.add_argument("--workload", default="single2048",
+                    help="single2048 (default), single256, or sweep8192 with --seeds and --max-disp")
+    ap.add_argument("--seeds", type=int, default=None, help="sweep8192: seed count (2^10, 2^14, 2^18, 2^22)")
+    ap.add_argument("--max-disp", type=int, default=None, help="sweep8192: maximum move per axis (1, 4, 16)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="bounded CPU-oracle sample for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -62,11 +67,22 @@ def dist_env():
     return rank, world, local
 
 
+_SWEEP = {}
+
+
 def workload(name):
+    """(w, h, seeds, timesteps, max displacement) of a named workload."""
     from paper_2209_00117_gb300 import inputs
 
+    if name == "sweep8192":
+        sw = inputs.SWEEP8192
+        s = _SWEEP.get("seeds") or sw["seeds"][1]
+        d = _SWEEP.get("max_disp") or sw["max_disp"][1]
+        if s not in sw["seeds"] or d not in sw["max_disp"]:
+            raise SystemExit(f"sweep8192 takes --seeds in {sw['seeds']} and --max-disp in {sw['max_disp']}")
+        return sw["side"], sw["side"], s, sw["steps"], d
     if name not in inputs.SINGLE:
-        raise SystemExit(f"unknown workload {name}; choose from {sorted(inputs.SINGLE)}")
+        raise SystemExit(f"unknown workload {name}; choose from {sorted(inputs.SINGLE)} or sweep8192")
     w, h, s, steps, d = inputs.SINGLE[name]
     return w, h, s, steps, d
 
@@ -132,6 +148,26 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(smax) if smax else None,
                 "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# multi-rank aggregation (replicas: no data-path collective)
+# ---------------------------------------------------------------------------
+
+def max_over_ranks(pg, value, device):
+    """The largest `value` over all ranks (the slowest rank sets the job time)."""
+    if pg is None:
+        return value
+    import torch
+
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_gpx(pixel_passes_per_step, steps, world, t_max_ms):
+    """Gpixel-passes/s of the whole job: every rank's units over the max time."""
+    return pixel_passes_per_step * steps * world / (t_max_ms * 1e-3) / 1e9
 
 
 # ---------------------------------------------------------------------------
@@ -252,6 +288,7 @@ def run_ours(args):
         torch.cuda.synchronize()
 
     w, h, s, _, d = workload(args.workload)
+    wkey = args.workload if args.workload != "sweep8192" else f"sweep8192_s{s}_d{d}"
     K, W = args.steps, args.warmup
     if W < 3:
         raise SystemExit("--warmup must be >= 3")
@@ -320,18 +357,11 @@ def run_ours(args):
     t_djfa = sum(e[0].elapsed_time(e[1]) for e in ev)  # ms
     t_jfa = sum(e[2].elapsed_time(e[3]) for e in ev)
 
-    def max_over_ranks(v):
-        if pg is None:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device=f"cuda:{local}")
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        return float(t.item())
-
-    t_djfa_max = max_over_ranks(t_djfa)
-    t_jfa_max = max_over_ranks(t_jfa)
-    units = px * n_djfa * K * world
-    value = units / (t_djfa_max * 1e-3) / 1e9
-    jfa_value = px * n_jfa * K * world / (t_jfa_max * 1e-3) / 1e9
+    dev = f"cuda:{local}"
+    t_djfa_max = max_over_ranks(pg, t_djfa, dev)
+    t_jfa_max = max_over_ranks(pg, t_jfa, dev)
+    value = whole_job_gpx(px * n_djfa, K, world, t_djfa_max)
+    jfa_value = whole_job_gpx(px * n_jfa, K, world, t_jfa_max)
 
     # --- per-kernel timing for the roofline: the same trajectory replayed with
     #     events around every launch (eager launches, L2 flushed between steps)
@@ -363,7 +393,7 @@ def run_ours(args):
     tot_ms = sum(v["ms"] for v in prof.values())
     roofline = {
         "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-        "traffic": recorded_traffic(dom, args.workload),
+        "traffic": recorded_traffic(dom, wkey),
         "kernel": dom, "alg_bytes_per_launch": alg_bytes, "avg_launch_us": avg_ms * 1e3,
         "peak_source": peak_src,
         "share": {k: round(v["ms"] / tot_ms, 4) for k, v in prof.items() if tot_ms > 0},
@@ -393,9 +423,9 @@ def run_ours(args):
             ee.labels(out=pin_out)
         e1.record(stream)
         barrier()
-        te = max_over_ranks(e0.elapsed_time(e1))
+        te = max_over_ranks(pg, e0.elapsed_time(e1), dev)
         ee.close()
-        e2e = {"value": px * n_djfa * K * world / (te * 1e-3) / 1e9, "unit": UNIT,
+        e2e = {"value": whole_job_gpx(px * n_djfa, K, world, te), "unit": UNIT,
                "h2d_bytes_per_step": int(s * 2 * 4), "d2h_bytes_per_step": int(px * 4),
                "ms_per_step": te / K}
 
@@ -442,6 +472,8 @@ def run_ours(args):
 
 def main():
     args = parse_args()
+    _SWEEP["seeds"] = args.seeds
+    _SWEEP["max_disp"] = args.max_disp
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)
