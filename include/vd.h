@@ -220,6 +220,41 @@ int vd_similarity_ctx(vd_ctx* ctx, vd_ctx* ref, uint64_t* n_match);
  */
 int vd_exact(vd_ctx* ctx, int32_t* labels, int32_t* dist, int on_device, int32_t metric);
 
+/*
+ * Exact diagram for callers that cannot allocate device memory.  The paper has
+ * no counterpart to this call; it exists for code that must not call
+ * cudaMalloc: code running under another framework's memory manager (which
+ * owns the device memory and budgets every byte of it), latency-bound loops
+ * that cannot afford the synchronisation an allocation may bring, and plugin
+ * hosts that forbid allocation on their threads.  vd_exact needs a context,
+ * and a context allocates; this entry point takes everything as caller
+ * buffers and uses a fixed scratch array compiled into the library instead.
+ *
+ * Computes the same maps as vd_exact: for every pixel of a w x h grid the
+ * lowest seed index at the minimum distance (labels) and that distance
+ * (dist), dense row-major int32, either may be NULL but not both.  seeds_xy,
+ * labels and dist are DEVICE pointers of the current device (seeds_xy 8-byte
+ * aligned, n_seeds (x, y) pairs); the caller owns them.  Work runs on
+ * cuda_stream (NULL = legacy default stream); the call first synchronises
+ * that stream once to check the seeds, then queues the rest and returns.
+ *
+ * Scratch: a file-scope device array of VD_NOALLOC_SCRATCH_INTS int32 (4 MiB)
+ * that every GPU loading the library holds until the process exits.  The
+ * bucket grid needs 64 + 2 * buckets + 1 + n_seeds ints, with one to two
+ * buckets per seed: up to about 250000 seeds always fit, beyond that it
+ * depends on the grid.  Larger requests fail with VD_EINVAL and a message
+ * naming the need, as do bad sizes, a bad metric and seeds outside the
+ * grid.  No cudaMalloc, cudaFree or allocating library routine is called.
+ * The first call on a device resolves the array's device address (with that
+ * device current); make that first call before any stream capture.  All calls
+ * share the one array, which keeps the previous call's contents (the parts
+ * that must start at zero are cleared on every call): calls that overlap on
+ * the GPU, on any stream, race.
+ */
+#define VD_NOALLOC_SCRATCH_INTS (1 << 20)
+int vd_exact_noalloc(const int32_t* seeds_xy, int32_t n_seeds, int32_t grid_w, int32_t grid_h,
+                     int32_t metric, int32_t* labels, int32_t* dist, void* cuda_stream);
+
 /* Tuning and execution options (vd_set_option); values are validated. */
 #define VD_OPT_FUSE_MAX_K 1      /* largest step fused into shared-memory groups (0 = no fusion, the
                                     default; 1..16) */

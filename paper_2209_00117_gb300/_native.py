@@ -56,6 +56,7 @@ SIGNATURES = {
     "vd_launch_count": (_i64, [_p]),
     "vd_profile_read": (_int, [_p, _p, _p, _p]),
     "vd_profile_reset": (_int, [_p]),
+    "vd_exact_noalloc": (_int, [_p, _i32, _i32, _i32, _i32, _p, _p, _p]),
 }
 
 _lib = None

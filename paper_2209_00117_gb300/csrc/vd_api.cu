@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <string>
 #include <tuple>
 #include <vector>
@@ -972,4 +973,101 @@ extern "C" int vd_profile_reset(vd_ctx* c) {
   if (rc) return rc;
   c->prof.reset();
   return VD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Exact diagram without any allocation (vd_exact_noalloc)
+// ---------------------------------------------------------------------------
+
+// Scratch of vd_exact_noalloc: a u64 error flag at the front (ints 0..63 are
+// reserved for it), then the bucket counts, bucket starts and seed ids.  Every
+// GPU that loads this library holds the array until the process exits.
+static __device__ __align__(256) int g_noalloc_scratch[VD_NOALLOC_SCRATCH_INTS];
+
+namespace {
+
+constexpr int kNoallocHeaderInts = 64;
+constexpr int kNoallocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+int* g_noalloc_ptr[kNoallocMaxDevices] = {};
+
+}  // namespace
+
+extern "C" int vd_exact_noalloc(const int32_t* seeds_xy, int32_t n_seeds, int32_t w, int32_t h, int32_t metric,
+                                int32_t* labels, int32_t* dist, void* cuda_stream) {
+  if (bad_side(w) || bad_side(h)) return vd_fail(VD_EINVAL, "grid %dx%d outside [1, %d]", w, h, VD_MAX_SIDE);
+  if (n_seeds < 1) return vd_fail(VD_EINVAL, "n_seeds %d < 1", n_seeds);
+  if (!seeds_xy) return vd_fail(VD_EINVAL, "null seeds");
+  if (!labels && !dist) return vd_fail(VD_EINVAL, "no output map");
+  if (check_metric(metric)) return VD_EINVAL;
+  int cell = 1;
+  const double per = static_cast<double>(w) * h / n_seeds;
+  while (static_cast<double>(cell + 1) * (cell + 1) <= per) ++cell;
+  const int gw = (w + cell - 1) / cell, gh = (h + cell - 1) / cell;
+  const int64_t cells = static_cast<int64_t>(gw) * gh;
+  const int64_t need = kNoallocHeaderInts + cells + (cells + 1) + n_seeds;
+  if (need > VD_NOALLOC_SCRATCH_INTS)
+    return vd_fail(VD_EINVAL,
+                   "vd_exact_noalloc: %d seeds on a %dx%d grid need %lld scratch ints (%lld buckets), more than "
+                   "the static maximum of %d",
+                   n_seeds, w, h, static_cast<long long>(need), static_cast<long long>(cells),
+                   VD_NOALLOC_SCRATCH_INTS);
+
+  int dev = 0;
+  int rc = vd_cuda_check(cudaGetDevice(&dev), "cudaGetDevice");
+  if (rc) return rc;
+  if (dev < 0 || dev >= kNoallocMaxDevices) return vd_fail(VD_EINVAL, "device %d beyond %d", dev, kNoallocMaxDevices);
+  int* base = nullptr;
+  {
+    // once per device, with that device current: the host-side name of the
+    // array is only a stand-in, the kernels need its device address
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+      void* p = nullptr;
+      rc = vd_cuda_check(cudaGetSymbolAddress(&p, g_noalloc_scratch), "cudaGetSymbolAddress(scratch)");
+      if (rc) return rc;
+      g_noalloc_ptr[dev] = static_cast<int*>(p);
+    }
+    base = g_noalloc_ptr[dev];
+  }
+  unsigned long long* flag = reinterpret_cast<unsigned long long*>(base);
+  int* count = base + kNoallocHeaderInts;
+  int* start = count + cells;
+  int* ids = start + cells + 1;
+  const int2* seeds = reinterpret_cast<const int2*>(seeds_xy);
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  const int sb = (n_seeds + 255) / 256;
+
+  // seeds outside the grid would index buckets out of range: reject them first
+  rc = vd_cuda_check(cudaMemsetAsync(flag, 0, sizeof(unsigned long long), st), "memset");
+  if (rc) return rc;
+  vdk::k_check_seeds<<<sb, 256, 0, st>>>(seeds, n_seeds, w, h, flag);
+  rc = vd_cuda_check(cudaGetLastError(), "check seeds");
+  if (rc) return rc;
+  unsigned long long bad = 0;
+  rc = vd_cuda_check(cudaMemcpyAsync(&bad, flag, sizeof(bad), cudaMemcpyDeviceToHost, st), "copy flag");
+  if (!rc) rc = vd_cuda_check(cudaStreamSynchronize(st), "synchronize");
+  if (rc) return rc;
+  if (bad) return vd_fail(VD_EINVAL, "%llu seeds outside the %dx%d grid", bad, w, h);
+
+  // the array keeps the previous call's contents: the counts restart at zero
+  rc = vd_cuda_check(cudaMemsetAsync(count, 0, sizeof(int) * cells, st), "memset");
+  if (rc) return rc;
+  vdk::k_bucket_count<<<sb, 256, 0, st>>>(seeds, n_seeds, cell, gw, count);
+  vdk::k_scan<<<1, 1024, 0, st>>>(count, static_cast<int>(cells), start);
+  rc = vd_cuda_check(cudaMemsetAsync(count, 0, sizeof(int) * cells, st), "memset");
+  if (rc) return rc;
+  vdk::k_bucket_fill<<<sb, 256, 0, st>>>(seeds, n_seeds, cell, gw, start, count, ids);
+  vdk::Buckets b;
+  b.cell = cell;
+  b.gw = gw;
+  b.gh = gh;
+  b.start = start;
+  b.ids = ids;
+  dim3 block(32, 8), grid((w + 31) / 32, (h + 7) / 8);
+  if (metric == VD_METRIC_EUCLID)
+    vdk::k_exact<vdk::kEuclid><<<grid, block, 0, st>>>(b, seeds, w, h, labels, dist);
+  else
+    vdk::k_exact<vdk::kManhattan><<<grid, block, 0, st>>>(b, seeds, w, h, labels, dist);
+  return vd_cuda_check(cudaGetLastError(), "exact launch");
 }

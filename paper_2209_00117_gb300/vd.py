@@ -69,6 +69,26 @@ def djfa_schedule(w: int, h: int, n_seeds: int, d_max: int, vn_waves: int = 2, e
     return _schedule(N.lib().vd_djfa_schedule, w, h, n_seeds, d_max, vn_waves, extra)
 
 
+def exact_noalloc(seeds_xy, w: int, h: int, labels_out=None, dist_out=None, metric: int = EUCLID,
+                  stream=None):
+    """The exact diagram from caller-owned CUDA tensors, allocating no device
+    memory (the library's fixed scratch array is used instead): for callers
+    that must not call cudaMalloc.  ``seeds_xy`` is an (n, 2) int32 CUDA
+    tensor; the outputs are (h, w) int32 CUDA tensors (either may be None)."""
+    n = seeds_xy.numel() // 2
+    ps, ds = _buf(seeds_xy, 2 * n)
+    pl, dl = _buf(labels_out, w * h, writable=True)
+    pd, dd = _buf(dist_out, w * h, writable=True)
+    if not ds or (labels_out is not None and not dl) or (dist_out is not None and not dd):
+        raise ValueError("exact_noalloc takes CUDA tensors only")
+    if stream is None:
+        handle = _current_stream_handle()
+    else:
+        handle = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    N.check(N.lib().vd_exact_noalloc(ps, n, int(w), int(h), int(metric), pl, pd, ctypes.c_void_p(handle)))
+    return labels_out, dist_out
+
+
 def _current_stream_handle():
     try:
         import torch
