@@ -138,8 +138,8 @@ int vd_get_seeds(vd_ctx* ctx, int32_t* xy, int on_device);
  * SimulateParticles of Algorithm 1 under the uniform random model of
  * Section IV-A: every seed k moves to clamp(p_k + delta_k) with the clamp
  * keeping it on the grid.  If dxy is non-NULL it holds n_seeds integer
- * displacement pairs (host or device per dxy_on_device; max_disp, rng_seed,
- * stream_id and step are then ignored).  If dxy is NULL, each displacement
+ * displacement pairs (host or device per dxy_on_device, a device pointer
+ * 8-byte aligned; max_disp, rng_seed, stream_id and step are then ignored).  If dxy is NULL, each displacement
  * component is drawn on the device as u - max_disp, u uniform in
  * [0, 2 max_disp] from SplitMix64 (Steele, Lea, Flood 2014): key =
  * splitmix64(rng_seed, stream_id), draw = splitmix64(key, step * 2^33 + 2k +
@@ -254,6 +254,99 @@ int vd_exact(vd_ctx* ctx, int32_t* labels, int32_t* dist, int on_device, int32_t
 #define VD_NOALLOC_SCRATCH_INTS (1 << 20)
 int vd_exact_noalloc(const int32_t* seeds_xy, int32_t n_seeds, int32_t grid_w, int32_t grid_h,
                      int32_t metric, int32_t* labels, int32_t* dist, void* cuda_stream);
+
+/* ------------------------------------------------------------------------ */
+/* Many independent simulations (batched timestep)                          */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * A batch steps many independent simulations (each its own grid and seeds)
+ * together.  Every simulation computes exactly what a context would compute
+ * for it alone (vd_jfa, vd_move_seeds with stream_id = its index,
+ * vd_djfa_step): the same per-pixel code, the same exact-integer results.
+ * The paper runs one simulation at a time (Section V); batching is this
+ * library's way of filling a GPU with many small grids.
+ */
+typedef struct vd_batch vd_batch;
+
+/*
+ * Creates a batch of n_sims simulations with grid sizes w[i] x h[i] and
+ * n_seeds[i] seeds (host arrays; sizes as for vd_create).  All label maps
+ * start empty (-1), all seeds at (0, 0).  Seed arrays of the batch are
+ * concatenated in simulation order ("sim-major"): simulation i's seeds start
+ * at the offset vd_batch_get_shape reports.  NULL on bad sizes or OOM.
+ */
+vd_batch* vd_batch_create(int32_t n_sims, const int32_t* w, const int32_t* h, const int32_t* n_seeds);
+int vd_batch_destroy(vd_batch* batch);
+int vd_batch_set_stream(vd_batch* batch, void* cuda_stream);
+
+/* Waits for the batch's stream.  Returns VD_ETIMEOUT (once, then clears it)
+ * if a persistent step's bounded barrier wait ran out since the last check;
+ * the maps of that step are then undefined (re-run vd_batch_jfa). */
+int vd_batch_synchronize(vd_batch* batch);
+
+/* Grid size, seed count and seed offset of simulation `sim`. */
+int vd_batch_get_shape(const vd_batch* batch, int32_t sim, int32_t* w, int32_t* h, int32_t* n_seeds,
+                       int32_t* seed_offset);
+
+/* Replaces all seeds (sim-major (x, y) pairs, total = sum of n_seeds);
+ * VD_EINVAL if any lies outside its simulation's grid (nothing changes). */
+int vd_batch_set_seeds(vd_batch* batch, const int32_t* xy, int on_device);
+int vd_batch_get_seeds(vd_batch* batch, int32_t sim, int32_t* xy, int on_device);
+/* Dense w x h label map of one simulation (synchronises the batch). */
+int vd_batch_get_labels(vd_batch* batch, int32_t sim, int32_t* labels, int on_device);
+
+/* Sets the dJFA schedule of every simulation (Eq. 3-4 with its own w, h,
+ * n_seeds; parameters as vd_djfa_step).  Needed before vd_batch_step. */
+int vd_batch_configure(vd_batch* batch, int32_t d_max, int32_t vn_waves, int32_t extra_passes,
+                       int32_t metric);
+
+/* A full JFA frame (Section III) for every simulation, e.g. frame 0. */
+int vd_batch_jfa(vd_batch* batch, int32_t metric);
+
+/*
+ * One dJFA timestep of every simulation: move (given sim-major displacements
+ * dxy, or SplitMix64 draws in [-max_disp, max_disp] with stream_id = the
+ * simulation's index and step = the number of moves it has made so far, as
+ * in vd_move_seeds), stamp onto the previous map, and the configured passes.
+ * In the default mode every phase and pass round is one launch over all
+ * simulations' tiles, the whole step replayed as a CUDA graph once its plan
+ * repeats; in VD_BMODE_PERSISTENT it is one cooperative launch with a bounded
+ * grid barrier between phases (see vd_batch_synchronize).
+ */
+int vd_batch_step(vd_batch* batch, const int32_t* dxy, int dxy_on_device, int32_t max_disp,
+                  uint64_t rng_seed);
+
+/* The same timestep for a subset of simulations only (RNG moves; each listed
+ * at most once), e.g. the requests a server admitted together. */
+int vd_batch_step_subset(vd_batch* batch, const int32_t* sims, int32_t n, int32_t max_disp,
+                         uint64_t rng_seed);
+
+#define VD_BOPT_MODE 1               /* 0 = launch per phase/round (default), 1 = persistent */
+#define VD_BOPT_ROWS_PER_THREAD 2    /* rows each thread sweeps per tile: 1 (default), 2, 4 */
+#define VD_BOPT_BLOCKS_PER_SM 3      /* persistent mode: 0 = occupancy maximum (default), else cap */
+#define VD_BOPT_USE_GRAPHS 4         /* 1 (default) = replay repeating full steps as a graph */
+#define VD_BOPT_BARRIER_TIMEOUT_US 5 /* persistent mode: bounded barrier wait (default 2 s) */
+#define VD_BOPT_TEST_SKIP_ARRIVE 6   /* test only: block 0 skips its first barrier arrival so the
+                                        other blocks' wait must run out (default 0) */
+int vd_batch_set_option(vd_batch* batch, int32_t option, int64_t value);
+int vd_batch_get_option(const vd_batch* batch, int32_t option, int64_t* value);
+
+/*
+ * Autotuner: times `steps` dJFA steps (after one warm-up step) for each
+ * candidate launch shape (mode x rows per thread), restoring the batch's
+ * complete state (maps, seeds, step counters) before each candidate and at
+ * the end, so tuning leaves the simulation unchanged.  Keeps the fastest
+ * candidate; writes its index to *best and each candidate's ms per step to
+ * ms_per_step[0 .. cap).  Returns the number of candidates.
+ */
+int vd_batch_autotune(vd_batch* batch, int32_t steps, int32_t max_disp, uint64_t rng_seed,
+                      int32_t* best, double* ms_per_step, int32_t cap);
+
+/* Total pixels, pixel-passes of one configured dJFA step, total seeds. */
+int vd_batch_work(const vd_batch* batch, int64_t* pixels, int64_t* pixel_passes_per_step,
+                  int64_t* seeds);
+int64_t vd_batch_launch_count(const vd_batch* batch);
 
 /* Tuning and execution options (vd_set_option); values are validated. */
 #define VD_OPT_FUSE_MAX_K 1      /* largest step fused into shared-memory groups (0 = no fusion, the

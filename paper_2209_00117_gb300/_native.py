@@ -57,6 +57,23 @@ SIGNATURES = {
     "vd_profile_read": (_int, [_p, _p, _p, _p]),
     "vd_profile_reset": (_int, [_p]),
     "vd_exact_noalloc": (_int, [_p, _i32, _i32, _i32, _i32, _p, _p, _p]),
+    "vd_batch_create": (_p, [_i32, _p, _p, _p]),
+    "vd_batch_destroy": (_int, [_p]),
+    "vd_batch_set_stream": (_int, [_p, _p]),
+    "vd_batch_synchronize": (_int, [_p]),
+    "vd_batch_get_shape": (_int, [_p, _i32, _P32, _P32, _P32, _P32]),
+    "vd_batch_set_seeds": (_int, [_p, _p, _int]),
+    "vd_batch_get_seeds": (_int, [_p, _i32, _p, _int]),
+    "vd_batch_get_labels": (_int, [_p, _i32, _p, _int]),
+    "vd_batch_configure": (_int, [_p, _i32, _i32, _i32, _i32]),
+    "vd_batch_jfa": (_int, [_p, _i32]),
+    "vd_batch_step": (_int, [_p, _p, _int, _i32, _u64]),
+    "vd_batch_step_subset": (_int, [_p, _p, _i32, _i32, _u64]),
+    "vd_batch_set_option": (_int, [_p, _i32, _i64]),
+    "vd_batch_get_option": (_int, [_p, _i32, ctypes.POINTER(_i64)]),
+    "vd_batch_autotune": (_int, [_p, _i32, _i32, _u64, _P32, _p, _i32]),
+    "vd_batch_work": (_int, [_p, ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
+    "vd_batch_launch_count": (_i64, [_p]),
 }
 
 _lib = None

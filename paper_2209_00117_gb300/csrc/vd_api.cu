@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdarg>
+#include <cstdint>
 #include <cstdio>
 #include <cstring>
 #include <map>
@@ -590,6 +591,8 @@ extern "C" int vd_move_seeds(vd_ctx* c, const int32_t* dxy, int dxy_on_device, i
   const int2* d = nullptr;
   if (dxy) {
     if (dxy_on_device) {
+      if (reinterpret_cast<uintptr_t>(dxy) % alignof(int2) != 0)
+        return vd_fail(VD_EINVAL, "device displacements must be 8-byte aligned");
       d = reinterpret_cast<const int2*>(dxy);
     } else {
       const int rc = vd_cuda_check(cudaMemcpyAsync(c->dxy_stage, dxy, sizeof(int2) * c->n,
@@ -998,6 +1001,8 @@ extern "C" int vd_exact_noalloc(const int32_t* seeds_xy, int32_t n_seeds, int32_
   if (bad_side(w) || bad_side(h)) return vd_fail(VD_EINVAL, "grid %dx%d outside [1, %d]", w, h, VD_MAX_SIDE);
   if (n_seeds < 1) return vd_fail(VD_EINVAL, "n_seeds %d < 1", n_seeds);
   if (!seeds_xy) return vd_fail(VD_EINVAL, "null seeds");
+  if (reinterpret_cast<uintptr_t>(seeds_xy) % alignof(int2) != 0)
+    return vd_fail(VD_EINVAL, "seeds must be 8-byte aligned");
   if (!labels && !dist) return vd_fail(VD_EINVAL, "no output map");
   if (check_metric(metric)) return VD_EINVAL;
   int cell = 1;

@@ -64,18 +64,18 @@ __device__ __forceinline__ long long pack_key(int key, int c) {
   return (static_cast<long long>(key) << 32) | static_cast<unsigned int>(c);
 }
 
-template <int METRIC>
+template <int METRIC, bool COH = false>
 __device__ __forceinline__ long long cand(int c, const int2* __restrict__ table, int m2x, int m2y, int x,
                                           int y) {
-  const int2 e = __ldg(&table[c]);
+  const int2 e = COH ? __ldcg(&table[c]) : __ldg(&table[c]);
   return pack_key(table_key<METRIC>(e, c, m2x, m2y, x, y), c);
 }
 
 // Folds candidate c into the packed best b.
-template <int METRIC>
+template <int METRIC, bool COH = false>
 __device__ __forceinline__ long long fold(long long b, int c, const int2* __restrict__ table, int m2x,
                                           int m2y, int x, int y) {
-  return min(b, cand<METRIC>(c, table, m2x, m2y, x, y));
+  return min(b, cand<METRIC, COH>(c, table, m2x, m2y, x, y));
 }
 
 // Kept for the kernels that read plain int2 positions (similarity, exact).
@@ -91,8 +91,20 @@ __device__ __forceinline__ void consider(int c, const int2* __restrict__ seeds, 
   }
 }
 
-__device__ __forceinline__ int4 ld4(const int32_t* p) {
+// Label-map and seed-table loads.  Separate launches use the read-only
+// (non-coherent L1) path; a persistent launch that rewrites maps and tables
+// between grid barriers must read them at L2 (ld.global.cg): the read-only
+// path is only defined for data that no thread writes during the launch.
+template <bool COHERENT>
+__device__ __forceinline__ int4 map4(const int32_t* p) {
+  if (COHERENT) return __ldcg(reinterpret_cast<const int4*>(p));
   return __ldg(reinterpret_cast<const int4*>(p));
+}
+
+template <bool COHERENT>
+__device__ __forceinline__ int map1(const int32_t* p) {
+  if (COHERENT) return __ldcg(p);
+  return __ldg(p);
 }
 
 struct PassArgs {
@@ -122,61 +134,63 @@ __device__ __forceinline__ int4 shift_right_by(const int4& m, const int4& r, int
 
 // The four pixels (x0 .. x0+3, y) owned by one thread and their packed
 // best (key, label) so far.
-template <int METRIC>
+template <int METRIC, bool COH>
 struct Quad {
   long long b0, b1, b2, b3;
   int m2x, m2y, x0, y;
   __device__ __forceinline__ void init(const int4& L, const int2* __restrict__ table) {
-    b0 = cand<METRIC>(L.x, table, m2x, m2y, x0, y);
-    b1 = cand<METRIC>(L.y, table, m2x - 2, m2y, x0 + 1, y);
-    b2 = cand<METRIC>(L.z, table, m2x - 4, m2y, x0 + 2, y);
-    b3 = cand<METRIC>(L.w, table, m2x - 6, m2y, x0 + 3, y);
+    b0 = cand<METRIC, COH>(L.x, table, m2x, m2y, x0, y);
+    b1 = cand<METRIC, COH>(L.y, table, m2x - 2, m2y, x0 + 1, y);
+    b2 = cand<METRIC, COH>(L.z, table, m2x - 4, m2y, x0 + 2, y);
+    b3 = cand<METRIC, COH>(L.w, table, m2x - 6, m2y, x0 + 3, y);
   }
   __device__ __forceinline__ void fold4(const int4& L, const int2* __restrict__ table) {
-    b0 = fold<METRIC>(b0, L.x, table, m2x, m2y, x0, y);
-    b1 = fold<METRIC>(b1, L.y, table, m2x - 2, m2y, x0 + 1, y);
-    b2 = fold<METRIC>(b2, L.z, table, m2x - 4, m2y, x0 + 2, y);
-    b3 = fold<METRIC>(b3, L.w, table, m2x - 6, m2y, x0 + 3, y);
+    b0 = fold<METRIC, COH>(b0, L.x, table, m2x, m2y, x0, y);
+    b1 = fold<METRIC, COH>(b1, L.y, table, m2x - 2, m2y, x0 + 1, y);
+    b2 = fold<METRIC, COH>(b2, L.z, table, m2x - 4, m2y, x0 + 2, y);
+    b3 = fold<METRIC, COH>(b3, L.w, table, m2x - 6, m2y, x0 + 3, y);
   }
 };
 
 // Labels at columns x0 + dx .. x0 + dx + 3 of one row for |dx| = k, a multiple
 // of 4 (one aligned 16-byte load); columns outside [0, pitch) read as -1 and
 // the row padding [w, pitch) holds -1 already.
+template <bool COH>
 __device__ __forceinline__ int4 load_side(const int32_t* __restrict__ row, int x0, int dx, int pitch) {
   const int xs = x0 + dx;
-  return (xs >= 0 && xs < pitch) ? ld4(row + xs) : make_int4(-1, -1, -1, -1);
+  return (xs >= 0 && xs < pitch) ? map4<COH>(row + xs) : make_int4(-1, -1, -1, -1);
 }
 
+template <bool COH>
 __device__ __forceinline__ int4 load_scalar4(const int32_t* __restrict__ row, int xs, int w) {
   int v[4];
 #pragma unroll
-  for (int i = 0; i < 4; ++i) v[i] = (xs + i >= 0 && xs + i < w) ? __ldg(row + xs + i) : -1;
+  for (int i = 0; i < 4; ++i) v[i] = (xs + i >= 0 && xs + i < w) ? map1<COH>(row + xs + i) : -1;
   return make_int4(v[0], v[1], v[2], v[3]);
 }
 
 // The side candidates (x -/+ k) of one source row for the four pixels of a
 // thread; `mid` is that row's aligned vector at x0 when already loaded.
-template <int KSEL, int METRIC>
-__device__ __forceinline__ void fold_sides(Quad<METRIC>& q, const int32_t* __restrict__ row, const int4& mid,
+template <int KSEL, int METRIC, bool COH>
+__device__ __forceinline__ void fold_sides(Quad<METRIC, COH>& q, const int32_t* __restrict__ row, const int4& mid,
                                            const PassArgs& a, const int2* __restrict__ table) {
   const int x0 = q.x0;
   if (KSEL == 0) {
-    const int4 L = load_side(row, x0, -a.k, a.pitch);
-    const int4 R = load_side(row, x0, a.k, a.pitch);
+    const int4 L = load_side<COH>(row, x0, -a.k, a.pitch);
+    const int4 R = load_side<COH>(row, x0, a.k, a.pitch);
     q.fold4(L, table);
     group_fence();
     q.fold4(R, table);
   } else if (KSEL == 1 || KSEL == 2) {
     const int4 neg = make_int4(-1, -1, -1, -1);
-    const int4 lv = (x0 >= 4) ? ld4(row + x0 - 4) : neg;
-    const int4 rv = (x0 + 4 < a.pitch) ? ld4(row + x0 + 4) : neg;
+    const int4 lv = (x0 >= 4) ? map4<COH>(row + x0 - 4) : neg;
+    const int4 rv = (x0 + 4 < a.pitch) ? map4<COH>(row + x0 + 4) : neg;
     q.fold4(shift_left_by(lv, mid, KSEL), table);
     group_fence();
     q.fold4(shift_right_by(mid, rv, KSEL), table);
   } else {
-    const int4 L = load_scalar4(row, x0 - a.k, a.w);
-    const int4 R = load_scalar4(row, x0 + a.k, a.w);
+    const int4 L = load_scalar4<COH>(row, x0 - a.k, a.w);
+    const int4 R = load_scalar4<COH>(row, x0 + a.k, a.w);
     q.fold4(L, table);
     group_fence();
     q.fold4(R, table);
@@ -184,55 +198,49 @@ __device__ __forceinline__ void fold_sides(Quad<METRIC>& q, const int32_t* __res
   group_fence();
 }
 
-// One jump pass (Table I / Section IV-B) over the whole map.  Every thread
-// owns four horizontally adjacent pixels: it starts from their own labels and
+// One jump pass (Table I / Section IV-B) for the four horizontally adjacent
+// pixels (x0 .. x0+3, y) of one thread: it starts from their own labels and
 // folds in the neighbour offsets one source row at a time (16-byte label
 // loads, four seed-table gathers and four packed-key minimums per offset).
 // Candidate order does not matter: the packed minimum is a total order.
-template <int NB, int METRIC, int KSEL>
-__global__ void __launch_bounds__(256, 6) k_pass(PassArgs a) {
-  const int x0 = 4 * static_cast<int>(blockIdx.x * blockDim.x + threadIdx.x);
-  int rb = blockIdx.y;
-  if (a.band_m > 1) rb = (blockIdx.y % a.band_t) * a.band_m + blockIdx.y / a.band_t;
-  const int y = rb * static_cast<int>(blockDim.y) + static_cast<int>(threadIdx.y);
-  if (x0 >= a.pitch || y >= a.h) return;
-
+template <int NB, int METRIC, int KSEL, bool COH = false>
+__device__ __forceinline__ void pass_quad(const PassArgs& a, int x0, int y) {
   const int64_t pitch = a.pitch;
   const int2* __restrict__ table = a.table;
-  Quad<METRIC> q;
+  Quad<METRIC, COH> q;
   q.m2y = -2 * y;
   q.m2x = -2 * x0;
   q.x0 = x0;
   q.y = y;
   const int32_t* crow = a.src + y * pitch;
-  const int4 own = ld4(crow + x0);
+  const int4 own = map4<COH>(crow + x0);
   // the first up-row vector is in flight while the own labels are scored
   const bool up_ok = y - a.k >= 0;
   const bool dn_ok = y + a.k < a.h;
   const int32_t* urow = a.src + (y - a.k) * pitch;
   const int32_t* drow = a.src + (y + a.k) * pitch;
   const int4 neg = make_int4(-1, -1, -1, -1);
-  const int4 um = up_ok ? ld4(urow + x0) : neg;
+  const int4 um = up_ok ? map4<COH>(urow + x0) : neg;
   q.init(own, table);
   group_fence();
   // centre row: (-k, 0), (+k, 0)
-  fold_sides<KSEL, METRIC>(q, crow, own, a, table);
+  fold_sides<KSEL, METRIC, COH>(q, crow, own, a, table);
   // up row: (0, -k) and, for Moore, (-k, -k), (+k, -k)
   if (up_ok) {
-    const int4 dm = dn_ok ? ld4(drow + x0) : neg;
+    const int4 dm = dn_ok ? map4<COH>(drow + x0) : neg;
     q.fold4(um, table);
     group_fence();
-    if (NB == kMoore) fold_sides<KSEL, METRIC>(q, urow, um, a, table);
+    if (NB == kMoore) fold_sides<KSEL, METRIC, COH>(q, urow, um, a, table);
     if (dn_ok) {
       q.fold4(dm, table);
       group_fence();
-      if (NB == kMoore) fold_sides<KSEL, METRIC>(q, drow, dm, a, table);
+      if (NB == kMoore) fold_sides<KSEL, METRIC, COH>(q, drow, dm, a, table);
     }
   } else if (dn_ok) {
-    const int4 dm = ld4(drow + x0);
+    const int4 dm = map4<COH>(drow + x0);
     q.fold4(dm, table);
     group_fence();
-    if (NB == kMoore) fold_sides<KSEL, METRIC>(q, drow, dm, a, table);
+    if (NB == kMoore) fold_sides<KSEL, METRIC, COH>(q, drow, dm, a, table);
   }
   int4 out;
   out.x = (x0 < a.w) ? static_cast<int>(static_cast<unsigned int>(q.b0)) : -1;
@@ -240,6 +248,16 @@ __global__ void __launch_bounds__(256, 6) k_pass(PassArgs a) {
   out.z = (x0 + 2 < a.w) ? static_cast<int>(static_cast<unsigned int>(q.b2)) : -1;
   out.w = (x0 + 3 < a.w) ? static_cast<int>(static_cast<unsigned int>(q.b3)) : -1;
   *reinterpret_cast<int4*>(a.dst + y * pitch + x0) = out;
+}
+
+template <int NB, int METRIC, int KSEL>
+__global__ void __launch_bounds__(256, 6) k_pass(PassArgs a) {
+  const int x0 = 4 * static_cast<int>(blockIdx.x * blockDim.x + threadIdx.x);
+  int rb = blockIdx.y;
+  if (a.band_m > 1) rb = (blockIdx.y % a.band_t) * a.band_m + blockIdx.y / a.band_t;
+  const int y = rb * static_cast<int>(blockDim.y) + static_cast<int>(threadIdx.y);
+  if (x0 >= a.pitch || y >= a.h) return;
+  pass_quad<NB, METRIC, KSEL>(a, x0, y);
 }
 
 // ---------------------------------------------------------------------------
@@ -362,14 +380,14 @@ __device__ __forceinline__ int rng_disp(uint64_t key, uint64_t step, uint64_t k,
 }
 
 // Rebuilds the pass table (entry k + 1 for seed k; entry 0 the sentinel).
-__global__ void k_build_table(const int2* __restrict__ seeds, int n, int2* __restrict__ table) {
+static __global__ void k_build_table(const int2* __restrict__ seeds, int n, int2* __restrict__ table) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k == 0) table[0] = make_int2(0, kSentinelNorm);
   if (k < n) table[k + 1] = table_entry(seeds[k]);
 }
 
 // Flags any label outside [-1, n) (device-side input validation).
-__global__ void k_check_labels(const int32_t* __restrict__ labels, int64_t count, int n,
+static __global__ void k_check_labels(const int32_t* __restrict__ labels, int64_t count, int n,
                                unsigned long long* __restrict__ bad) {
   for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < count;
        i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
@@ -380,7 +398,7 @@ __global__ void k_check_labels(const int32_t* __restrict__ labels, int64_t count
 
 // SimulateParticles (Algorithm 1): p_k <- clamp(p_k + delta_k) on the grid;
 // also refreshes the seed's pass-table entry.
-__global__ void k_move(int2* __restrict__ seeds, int2* __restrict__ table, int n,
+static __global__ void k_move(int2* __restrict__ seeds, int2* __restrict__ table, int n,
                        const int2* __restrict__ dxy, int w, int h, int max_disp, uint64_t key,
                        uint64_t step) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -406,7 +424,7 @@ __global__ void k_move(int2* __restrict__ seeds, int2* __restrict__ table, int n
 
 // Stamp, first half: every seed pixel is overwritten with one of the indices
 // standing on it (which one does not matter), replacing any stale label.
-__global__ void k_stamp_mark(int32_t* __restrict__ labels, int pitch, const int2* __restrict__ seeds,
+static __global__ void k_stamp_mark(int32_t* __restrict__ labels, int pitch, const int2* __restrict__ seeds,
                              int n) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n) return;
@@ -416,7 +434,7 @@ __global__ void k_stamp_mark(int32_t* __restrict__ labels, int pitch, const int2
 
 // Stamp, second half: the lowest index standing on the pixel wins.  As
 // unsigned, -1 is the largest value, so this also stamps an emptied map.
-__global__ void k_stamp_min(int32_t* __restrict__ labels, int pitch, const int2* __restrict__ seeds,
+static __global__ void k_stamp_min(int32_t* __restrict__ labels, int pitch, const int2* __restrict__ seeds,
                             int n) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n) return;
@@ -425,7 +443,7 @@ __global__ void k_stamp_min(int32_t* __restrict__ labels, int pitch, const int2*
             static_cast<unsigned int>(k));
 }
 
-__global__ void k_fill(int4* __restrict__ p, int64_t n4, int v) {
+static __global__ void k_fill(int4* __restrict__ p, int64_t n4, int v) {
   const int4 val = make_int4(v, v, v, v);
   for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n4;
        i += static_cast<int64_t>(gridDim.x) * blockDim.x)
@@ -433,7 +451,7 @@ __global__ void k_fill(int4* __restrict__ p, int64_t n4, int v) {
 }
 
 // Flags any seed outside the grid (device-side input validation).
-__global__ void k_check_seeds(const int2* __restrict__ seeds, int n, int w, int h,
+static __global__ void k_check_seeds(const int2* __restrict__ seeds, int n, int w, int h,
                               unsigned long long* __restrict__ bad) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n) return;
@@ -502,7 +520,7 @@ struct Buckets {
   const int* ids;    // seed indices grouped by bucket
 };
 
-__global__ void k_bucket_count(const int2* __restrict__ seeds, int n, int cell, int gw,
+static __global__ void k_bucket_count(const int2* __restrict__ seeds, int n, int cell, int gw,
                                int* __restrict__ count) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n) return;
@@ -510,7 +528,7 @@ __global__ void k_bucket_count(const int2* __restrict__ seeds, int n, int cell, 
   atomicAdd(&count[(p.y / cell) * gw + p.x / cell], 1);
 }
 
-__global__ void k_bucket_fill(const int2* __restrict__ seeds, int n, int cell, int gw,
+static __global__ void k_bucket_fill(const int2* __restrict__ seeds, int n, int cell, int gw,
                               const int* __restrict__ start, int* __restrict__ cursor,
                               int* __restrict__ ids) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -522,7 +540,7 @@ __global__ void k_bucket_fill(const int2* __restrict__ seeds, int n, int cell, i
 
 // Exclusive scan of `count` (length m) into `start` (length m + 1), one
 // block of 1024 threads walking the array in chunks with a running carry.
-__global__ void __launch_bounds__(1024) k_scan(const int* __restrict__ count, int m,
+static __global__ void __launch_bounds__(1024) k_scan(const int* __restrict__ count, int m,
                                                int* __restrict__ start) {
   __shared__ int s[1024];
   __shared__ int carry;

@@ -261,3 +261,124 @@ class VoronoiSim:
         on_dev = dl if labels_out is not None else dd
         N.check(self._lib.vd_exact(self._h, pl, pd, on_dev, int(metric)))
         return labels_out, dist_out
+
+
+BMODE_ROUNDS, BMODE_PERSISTENT = 0, 1
+BOPT_MODE = 1
+BOPT_ROWS_PER_THREAD = 2
+BOPT_BLOCKS_PER_SM = 3
+BOPT_USE_GRAPHS = 4
+BOPT_BARRIER_TIMEOUT_US = 5
+BOPT_TEST_SKIP_ARRIVE = 6
+
+
+class VoronoiBatch:
+    """Many independent simulations stepped together on the GPU (sim-major seeds)."""
+
+    def __init__(self, shapes, stream=None):
+        """``shapes``: iterable of (w, h, n_seeds)."""
+        shapes = [tuple(int(v) for v in s) for s in shapes]
+        w = np.array([s[0] for s in shapes], np.int32)
+        h = np.array([s[1] for s in shapes], np.int32)
+        n = np.array([s[2] for s in shapes], np.int32)
+        self._lib = N.lib()
+        handle = self._lib.vd_batch_create(len(shapes), w.ctypes.data, h.ctypes.data, n.ctypes.data)
+        if not handle:
+            raise N.VDError(N.VD_EINVAL, N.last_error())
+        self._h = ctypes.c_void_p(handle)
+        self.shapes = shapes
+        self.seed_offsets = np.concatenate([[0], np.cumsum(n)[:-1]]).astype(np.int64)
+        self.total_seeds = int(n.sum())
+        self.set_stream(stream)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            self._lib.vd_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __len__(self):
+        return len(self.shapes)
+
+    def set_stream(self, stream=None):
+        if stream is None:
+            handle = _current_stream_handle()
+        elif hasattr(stream, "cuda_stream"):
+            handle = stream.cuda_stream
+        else:
+            handle = int(stream)
+        N.check(self._lib.vd_batch_set_stream(self._h, ctypes.c_void_p(handle)))
+
+    def synchronize(self):
+        N.check(self._lib.vd_batch_synchronize(self._h))
+
+    def set_option(self, option: int, value: int):
+        N.check(self._lib.vd_batch_set_option(self._h, option, int(value)))
+
+    def get_option(self, option: int) -> int:
+        v = ctypes.c_int64()
+        N.check(self._lib.vd_batch_get_option(self._h, option, ctypes.byref(v)))
+        return v.value
+
+    def set_seeds(self, xy_all):
+        ptr, dev = _buf(xy_all, 2 * self.total_seeds)
+        N.check(self._lib.vd_batch_set_seeds(self._h, ptr, dev))
+
+    def get_seeds(self, sim: int, out=None):
+        if out is None:
+            out = np.empty((self.shapes[sim][2], 2), np.int32)
+        ptr, dev = _buf(out, 2 * self.shapes[sim][2], writable=True)
+        N.check(self._lib.vd_batch_get_seeds(self._h, int(sim), ptr, dev))
+        return out
+
+    def labels(self, sim: int, out=None):
+        w, h, _ = self.shapes[sim]
+        if out is None:
+            out = np.empty((h, w), np.int32)
+        ptr, dev = _buf(out, w * h, writable=True)
+        N.check(self._lib.vd_batch_get_labels(self._h, int(sim), ptr, dev))
+        return out
+
+    def configure(self, d_max: int, vn_waves: int = 2, extra: int = 0, metric: int = EUCLID):
+        N.check(self._lib.vd_batch_configure(self._h, int(d_max), int(vn_waves), int(extra), int(metric)))
+
+    def jfa(self, metric: int = EUCLID):
+        N.check(self._lib.vd_batch_jfa(self._h, int(metric)))
+
+    def step(self, dxy_all=None, max_disp: int = 0, rng_seed: int = 0):
+        ptr, dev = _buf(dxy_all, 2 * self.total_seeds)
+        N.check(self._lib.vd_batch_step(self._h, ptr, dev, int(max_disp), int(rng_seed) & (2**64 - 1)))
+
+    def step_subset(self, sims, max_disp: int, rng_seed: int = 0):
+        a = np.ascontiguousarray(sims, np.int32)
+        N.check(self._lib.vd_batch_step_subset(self._h, a.ctypes.data, len(a), int(max_disp),
+                                               int(rng_seed) & (2**64 - 1)))
+
+    def autotune(self, steps: int, max_disp: int, rng_seed: int = 0):
+        """(best candidate index, ms per step of every candidate)."""
+        best = ctypes.c_int32(-1)
+        ms = np.zeros(16, np.float64)
+        n = N.check(self._lib.vd_batch_autotune(self._h, int(steps), int(max_disp), int(rng_seed) & (2**64 - 1),
+                                                ctypes.byref(best), ms.ctypes.data, 16))
+        return best.value, ms[:n].tolist()
+
+    def work(self):
+        """(pixels, pixel-passes of one configured dJFA step, seeds)."""
+        px, pp, sd = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        N.check(self._lib.vd_batch_work(self._h, ctypes.byref(px), ctypes.byref(pp), ctypes.byref(sd)))
+        return px.value, pp.value, sd.value
+
+    @property
+    def launches(self) -> int:
+        return int(self._lib.vd_batch_launch_count(self._h))
