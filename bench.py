@@ -57,6 +57,9 @@ def parse_args():
                     help="bounded CPU-oracle sample for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--rates", default="2000,5000,10000,20000",
+                    help="serve1000: Poisson request rates (per second)")
+    ap.add_argument("--duration", type=float, default=1.0, help="serve1000: seconds of arrivals per rate")
     return ap.parse_args()
 
 
@@ -470,8 +473,162 @@ def run_ours(args):
     return 0
 
 
+def run_batched(args):
+    """256 independent simulations (sides in {256, 512, 1024, 2048}, seeds
+    uniform in [64, side^2/64], moves in [-2, 2]) stepped as one batch per
+    timestep, against the same simulations run one by one with one launch per
+    pass (plain JFA frames, and unbatched dJFA frames)."""
+    import torch
+
+    from paper_2209_00117_gb300 import build, inputs, vd
+
+    rank, world, local = dist_env()
+    build.build()
+    torch.cuda.set_device(local)
+    K, W, D = args.steps, args.warmup, 2
+    pop = inputs.batched_population(256, seed=rank)
+    shapes = [(p.w, p.h, p.s) for p in pop]
+    xys = [inputs.uniform_seeds(w, h, s_, seed=1000 * rank + i) for i, (w, h, s_) in enumerate(shapes)]
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    b = vd.VoronoiBatch(shapes, stream=stream)
+    b.set_seeds(np.concatenate(xys))
+    b.jfa()
+    b.configure(d_max=D)
+    best, cand_ms = b.autotune(steps=3, max_disp=D, rng_seed=rank)
+    px, pp, n_seeds = b.work()
+    for _ in range(W):
+        b.step(None, max_disp=D, rng_seed=rank)
+    b.synchronize()
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    e[0].record(stream)
+    for _ in range(K):
+        b.step(None, max_disp=D, rng_seed=rank)
+    e[1].record(stream)
+    b.synchronize()
+    t_batch = e[0].elapsed_time(e[1])
+    steps_done = W + K
+
+    # the same simulations one by one, one launch per pass: JFA frames and dJFA frames
+    sims = []
+    for i, (w, h, s_) in enumerate(shapes):
+        c = vd.VoronoiSim(w, h, s_, stream=stream)
+        c.set_seeds(xys[i])
+        c.set_option(vd.OPT_USE_GRAPHS, 0)
+        sims.append(c)
+    K1 = max(1, min(K, 5))
+
+    def per_sim_steps(frame, n_steps, step0):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for t in range(n_steps):
+            for i, c in enumerate(sims):
+                c.move(None, max_disp=D, rng_seed=rank, stream_id=i, step=step0 + t)
+                frame(c)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / n_steps
+
+    # bring the contexts to the batch's frame with JFA (timing the last K1 steps)
+    for c in sims:
+        c.jfa()
+    per_sim_steps(lambda c: c.jfa(), steps_done - K1, 0)
+    t_jfa = per_sim_steps(lambda c: c.jfa(), K1, steps_done - K1)
+    # similarity of the batch's dJFA maps to same-frame JFA maps, on the GPU
+    match = 0
+    for i, (w, h, _) in enumerate(shapes):
+        lab = torch.empty((h, w), dtype=torch.int32, device=f"cuda:{local}")
+        b.labels(i, out=lab)
+        match += sims[i].similarity(ref_labels=lab)[1]
+    # unbatched dJFA, one launch per pass, from the JFA maps
+    t_djfa_alone = per_sim_steps(lambda c: c.djfa_step(d_max=D), K1, steps_done)
+    pp_jfa = sum(w * h * len(vd.jfa_schedule(w, h)) for (w, h, _) in shapes)
+    for c in sims:
+        c.close()
+    b.close()
+    if rank != 0:
+        return 0
+    line = {
+        "workload": "batched256: 256 independent simulations, sides uniform in {256, 512, 1024, 2048}, "
+                    "seeds uniform in [64, side^2/64], moves uniform in [-2, 2]",
+        "metric": METRIC, "unit": UNIT, "steps": K, "warmup": W, "dtype": "int32", "data": "synthetic",
+        "pixels": px, "seeds": n_seeds, "pixel_passes_per_step": pp,
+        "batched_djfa": {"value": pp / (t_batch / K * 1e-3) / 1e9, "ms_per_step": t_batch / K,
+                         "launch_shape": {"candidate": best, "candidate_ms": cand_ms,
+                                          "mode": "persistent" if b_mode(best) else "per round (graph)"}},
+        "unbatched_djfa_one_launch_per_pass": {"value": pp / (t_djfa_alone * 1e-3) / 1e9,
+                                               "ms_per_step": t_djfa_alone},
+        "plain_jfa_one_launch_per_pass": {"value": pp_jfa / (t_jfa * 1e-3) / 1e9, "ms_per_step": t_jfa},
+        "speedup_batched_djfa_vs_plain_jfa": t_jfa / (t_batch / K),
+        "similarity_djfa_vs_jfa_pct": round(100.0 * match / px, 4),
+        "l2": "working set (2 maps per simulation) is larger than L2",
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def b_mode(candidate):
+    """Autotuner candidates 3..5 are the persistent launch shapes."""
+    return candidate >= 3
+
+
+def run_serve(args):
+    """1000 resident simulations (sides in {512, 1024, 2048, 4096}, density as
+    the batched workload) admitted under an 80 GB HBM budget, then Poisson
+    request traces at each rate: p50 / p99 step latency and steps/s."""
+    import torch
+
+    from paper_2209_00117_gb300 import build, inputs, vd
+
+    rank, world, local = dist_env()
+    build.build()
+    torch.cuda.set_device(local)
+    D = 2
+    pop = inputs.batched_population(1000, sides=(512, 1024, 2048, 4096), seed=rank)
+    srv = vd.VoronoiServer(max_sims=1000, hbm_budget_bytes=80 * 10**9, d_max=D, max_disp=D, rng_seed=rank)
+    ids, refused = [], 0
+    from paper_2209_00117_gb300._native import VDError
+
+    t0 = time.perf_counter()
+    for i, p in enumerate(pop):
+        try:
+            ids.append(srv.add_sim(p.w, p.h, inputs.uniform_seeds(p.w, p.h, p.s, seed=i)))
+        except VDError:
+            refused += 1
+    t_admit = time.perf_counter() - t0
+    st = srv.stats()
+    out = []
+    for rate in [float(r) for r in args.rates.split(",")]:
+        n = max(1, int(rate * args.duration))
+        arr = inputs.poisson_arrivals(rate, n, seed=int(rate))
+        tgt = np.asarray(ids, np.int32)[inputs.request_targets(n, len(ids), seed=int(rate))]
+        lat = srv.run_trace(arr, tgt)
+        span = float(np.max(arr + lat))
+        out.append({"rate_per_s": rate, "requests": n, "p50_ms": 1e3 * float(np.percentile(lat, 50)),
+                    "p99_ms": 1e3 * float(np.percentile(lat, 99)), "mean_ms": 1e3 * float(lat.mean()),
+                    "steps_per_s": n / span})
+    st2 = srv.stats()
+    srv.close()
+    if rank != 0:
+        return 0
+    print(json.dumps({
+        "workload": "serve1000: 1000 resident simulations, sides uniform in {512, 1024, 2048, 4096}, seeds "
+                    "uniform in [64, side^2/64], dJFA step requests (moves in [-2, 2]) as Poisson streams",
+        "unit": "steps/s and ms", "dtype": "int32", "data": "synthetic",
+        "admitted": len(ids), "refused": refused, "hbm_used_gb": st["used_bytes"] / 1e9,
+        "hbm_budget_gb": st["budget_bytes"] / 1e9, "admit_s": t_admit,
+        "kernel_launches": st2["launches"] - st["launches"], "steps": st2["steps_done"],
+        "rates": out}))
+    return 0
+
+
 def main():
     args = parse_args()
+    if args.workload == "batched256":
+        return run_batched(args)
+    if args.workload == "serve1000":
+        return run_serve(args)
     _SWEEP["seeds"] = args.seeds
     _SWEEP["max_disp"] = args.max_disp
     if args.impl == "reference":

@@ -348,6 +348,71 @@ int vd_batch_work(const vd_batch* batch, int64_t* pixels, int64_t* pixel_passes_
                   int64_t* seeds);
 int64_t vd_batch_launch_count(const vd_batch* batch);
 
+/* ------------------------------------------------------------------------ */
+/* Serving: resident simulations, step requests, continuous batching        */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * A server keeps up to max_sims simulations resident on the device (maps,
+ * seeds and seed table in one allocation each), admitting a simulation only
+ * while the total stays within hbm_budget_bytes.  Clients submit dJFA step
+ * requests; each request moves the simulation's seeds by SplitMix64 draws in
+ * [-max_disp, max_disp] (stream_id = the simulation's id, step = the number of
+ * steps it has taken, as in vd_move_seeds) and runs one dJFA frame with the
+ * server's d_max, vn_waves and metric (as vd_djfa_step).  Requests are served
+ * in arrival order with continuous batching: two launch lanes (own stream,
+ * plan and completion event each) alternate, and a free lane takes every
+ * queued request whose simulation has no step in flight, so newly arrived
+ * requests join the next launch while the previous one still runs.  A
+ * simulation's result is the same alone or in any mix.  The paper has no
+ * serving layer; this is the library's own.  A server is not thread-safe.
+ */
+typedef struct vd_server vd_server;
+
+vd_server* vd_server_create(int32_t max_sims, int64_t hbm_budget_bytes, int32_t d_max, int32_t vn_waves,
+                            int32_t metric, int32_t max_disp, uint64_t rng_seed);
+int vd_server_destroy(vd_server* server);
+
+/*
+ * Admits a simulation (host seeds, n (x, y) pairs), runs its JFA frame 0 and
+ * returns its id (>= 0).  VD_EBUSY if it would exceed the HBM budget or all
+ * slots are live (the message gives the shortfall), VD_EINVAL for bad sizes
+ * or seeds, VD_ENOMEM if the device allocation fails.
+ */
+int32_t vd_server_add_sim(vd_server* server, int32_t w, int32_t h, int32_t n_seeds, const int32_t* xy);
+/* Frees a simulation's memory and budget (VD_EBUSY while it has work). */
+int vd_server_remove_sim(vd_server* server, int32_t sim);
+
+/* Queues one step request; t_arrive (seconds on the server clock,
+ * vd_server_now) is the time latency is measured from, or < 0 for now.
+ * Returns the request's ticket (>= 0). */
+int64_t vd_server_submit(vd_server* server, int32_t sim, double t_arrive);
+/* Reaps finished launches and admits queued requests into free lanes;
+ * returns the number of requests completed by this call.  Never blocks. */
+int vd_server_progress(vd_server* server);
+/* Runs progress until nothing is queued or in flight. */
+int vd_server_drain(vd_server* server);
+/* Moves up to cap completion records out (ticket, latency in seconds,
+ * simulation; any array may be NULL); returns how many. */
+int32_t vd_server_completions(vd_server* server, int64_t* tickets, double* latency_s, int32_t* sims,
+                              int32_t cap);
+/* Seconds since the server was created (its clock). */
+double vd_server_now(const vd_server* server);
+/*
+ * Replays a timed trace natively: request i for simulation sims[i] arrives
+ * arrival_s[i] seconds after the call starts (non-decreasing); the call
+ * submits each at its time, keeps the lanes busy, and returns when all are
+ * done with each request's latency (completion - scheduled arrival).
+ */
+int vd_server_run_trace(vd_server* server, const double* arrival_s, const int32_t* sims, int64_t n,
+                        double* latency_s);
+/* Dense label map of a simulation (waits for its in-flight step). */
+int vd_server_get_labels(vd_server* server, int32_t sim, int32_t* labels, int on_device);
+int vd_server_stats(const vd_server* server, int64_t* used_bytes, int64_t* budget_bytes, int32_t* live_sims,
+                    int64_t* pending, int64_t* steps_done, int64_t* launches);
+/* Caps the requests one launch may take (default unbounded). */
+int vd_server_set_max_batch(vd_server* server, int32_t max_batch);
+
 /* Tuning and execution options (vd_set_option); values are validated. */
 #define VD_OPT_FUSE_MAX_K 1      /* largest step fused into shared-memory groups (0 = no fusion, the
                                     default; 1..16) */

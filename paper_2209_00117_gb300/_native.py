@@ -74,6 +74,20 @@ SIGNATURES = {
     "vd_batch_autotune": (_int, [_p, _i32, _i32, _u64, _P32, _p, _i32]),
     "vd_batch_work": (_int, [_p, ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
     "vd_batch_launch_count": (_i64, [_p]),
+    "vd_server_create": (_p, [_i32, _i64, _i32, _i32, _i32, _i32, _u64]),
+    "vd_server_destroy": (_int, [_p]),
+    "vd_server_add_sim": (_i32, [_p, _i32, _i32, _i32, _p]),
+    "vd_server_remove_sim": (_int, [_p, _i32]),
+    "vd_server_submit": (_i64, [_p, _i32, ctypes.c_double]),
+    "vd_server_progress": (_int, [_p]),
+    "vd_server_drain": (_int, [_p]),
+    "vd_server_completions": (_i32, [_p, _p, _p, _p, _i32]),
+    "vd_server_now": (ctypes.c_double, [_p]),
+    "vd_server_run_trace": (_int, [_p, _p, _p, _i64, _p]),
+    "vd_server_get_labels": (_int, [_p, _i32, _p, _int]),
+    "vd_server_stats": (_int, [_p, ctypes.POINTER(_i64), ctypes.POINTER(_i64), _P32, ctypes.POINTER(_i64),
+                                ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
+    "vd_server_set_max_batch": (_int, [_p, _i32]),
 }
 
 _lib = None

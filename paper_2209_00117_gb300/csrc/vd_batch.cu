@@ -13,242 +13,8 @@
 //
 // Every simulation computes exactly what vd_djfa_step / vd_jfa compute for it
 // alone: the same kernels' per-thread code (vdk::pass_quad) on the same data.
-#include <cuda_runtime.h>
+#include "vd_batch_engine.cuh"
 
-#include <algorithm>
-#include <cstring>
-#include <vector>
-
-#include "vd.h"
-#include "vd_internal.h"
-#include "vd_kernels.cuh"
-
-namespace vdb {
-
-constexpr int kMaxPasses = 20;   // 15 (side 32768) + 2 extra, with margin
-constexpr int kThreads = 256;    // 64 quads x 4 rows per block
-constexpr int kQuadsX = 64;
-
-struct SimDesc {
-  int w, h, pitch, n;
-  int32_t* map[2];
-  int2* seeds;
-  int2* table;  // entry 0 = sentinel; the pass table is table + 1
-  int seed_off;
-  int cur;
-  long long step;      // moves drawn so far (the RNG step of the next move)
-  int n_pass[2];       // [0] dJFA schedule, [1] JFA schedule
-  int ks[2][kMaxPasses];
-  int nbs[2][kMaxPasses];
-};
-
-struct Barrier {
-  unsigned int count;
-  unsigned int gen;
-  int err;   // sticky: 1 = a bounded wait ran out
-  int pad;
-};
-
-// One planned launch.  All arrays live in device memory.
-struct BatchArgs {
-  SimDesc* sims;
-  const int* act;        // active simulations
-  int n_act;
-  const int2* sblk;      // (sim, first seed) per 256-seed block of the active simulations
-  int n_sblk;
-  const int* round_tiles;   // tiles per round
-  const int* round_off;     // entries of round r: [round_off[r], round_off[r+1])
-  const int2* entries;      // (sim, first tile of that sim in the round)
-  int rounds;
-  int sched;                // 0 = dJFA schedule, 1 = JFA schedule
-  int mark;                 // 1: overwrite seed pixels before the minimum (dJFA); 0: JFA (map pre-filled)
-  int move;                 // 1: move seeds first
-  const int2* dxy;          // given moves (concatenated, seed_off indexed) or null for RNG
-  int max_disp;
-  unsigned long long rng_seed;
-  int rows_per_thread;
-  Barrier* bar;
-  long long timeout_ns;
-  int test_skip_arrive;
-};
-
-__device__ __forceinline__ unsigned long long global_ns() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-// Grid barrier with a bounded wait.  Returns false once any block's wait has
-// run out (then every block returns at its next barrier).
-__device__ bool grid_sync(const BatchArgs& A, bool skip_arrive) {
-  __syncthreads();
-  __shared__ int s_ok;
-  if (threadIdx.x == 0) {
-    volatile int* err = &A.bar->err;
-    int ok = (*err == 0);
-    if (ok) {
-      volatile unsigned int* gen = &A.bar->gen;
-      const unsigned int g = *gen;
-      __threadfence();
-      bool released = false;
-      if (!skip_arrive) {
-        const unsigned int arrived = atomicAdd(&A.bar->count, 1u);
-        if (arrived == gridDim.x - 1) {
-          atomicExch(&A.bar->count, 0u);
-          __threadfence();
-          atomicAdd(&A.bar->gen, 1u);
-          released = true;
-        }
-      }
-      if (!released) {
-        const unsigned long long t0 = global_ns();
-        while (*gen == g && *err == 0) {
-          if (global_ns() - t0 > static_cast<unsigned long long>(A.timeout_ns)) {
-            atomicCAS(&A.bar->err, 0, 1);
-            break;
-          }
-          __nanosleep(200);
-        }
-      }
-      __threadfence();
-      ok = (*err == 0);
-    }
-    s_ok = ok;
-  }
-  __syncthreads();
-  return s_ok != 0;
-}
-
-// ---- phases ---------------------------------------------------------------
-
-__device__ __forceinline__ void move_mark_block(const BatchArgs& A, int sb) {
-  const int2 blk = A.sblk[sb];
-  SimDesc* sd = A.sims + blk.x;
-  const int k = blk.y + static_cast<int>(threadIdx.x);
-  if (k >= sd->n) return;
-  int2 p = sd->seeds[k];
-  if (A.move) {
-    long long dx, dy;
-    if (A.dxy != nullptr) {
-      const int2 d = A.dxy[sd->seed_off + k];
-      dx = d.x;
-      dy = d.y;
-    } else {
-      const uint64_t key = vdk::splitmix64(A.rng_seed, static_cast<uint64_t>(blk.x));
-      const uint64_t step = static_cast<uint64_t>(sd->step);
-      dx = vdk::rng_disp(key, step, static_cast<uint64_t>(k), 0, A.max_disp);
-      dy = vdk::rng_disp(key, step, static_cast<uint64_t>(k), 1, A.max_disp);
-    }
-    long long x = p.x + dx, y = p.y + dy;
-    x = x < 0 ? 0 : (x > sd->w - 1 ? sd->w - 1 : x);
-    y = y < 0 ? 0 : (y > sd->h - 1 ? sd->h - 1 : y);
-    p.x = static_cast<int>(x);
-    p.y = static_cast<int>(y);
-    sd->seeds[k] = p;
-    sd->table[k + 1] = vdk::table_entry(p);
-  }
-  if (A.mark) sd->map[sd->cur][static_cast<int64_t>(p.y) * sd->pitch + p.x] = k;
-}
-
-__device__ __forceinline__ void stamp_min_block(const BatchArgs& A, int sb) {
-  const int2 blk = A.sblk[sb];
-  const SimDesc* sd = A.sims + blk.x;
-  const int k = blk.y + static_cast<int>(threadIdx.x);
-  if (k >= sd->n) return;
-  const int2 p = sd->seeds[k];
-  atomicMin(reinterpret_cast<unsigned int*>(sd->map[sd->cur] + static_cast<int64_t>(p.y) * sd->pitch + p.x),
-            static_cast<unsigned int>(k));
-}
-
-template <int METRIC, bool COH>
-__device__ __forceinline__ void round_tile(const BatchArgs& A, int r, int t) {
-  // the entry holding tile t: the last one whose first tile is <= t
-  int lo = A.round_off[r], hi = A.round_off[r + 1] - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (A.entries[mid].y <= t) lo = mid;
-    else hi = mid - 1;
-  }
-  const int2 e = A.entries[lo];
-  const SimDesc* sd = A.sims + e.x;
-  const int lt = t - e.y;
-  const int tiles_x = (sd->pitch + 4 * kQuadsX - 1) / (4 * kQuadsX);
-  const int tx = lt % tiles_x, ty = lt / tiles_x;
-  const int k = sd->ks[A.sched][r];
-  const int nb = sd->nbs[A.sched][r];
-  vdk::PassArgs a;
-  a.src = sd->map[(sd->cur + r) & 1];
-  a.dst = sd->map[(sd->cur + r + 1) & 1];
-  a.table = sd->table + 1;
-  a.n_seeds = static_cast<uint32_t>(sd->n);
-  a.w = sd->w;
-  a.h = sd->h;
-  a.pitch = sd->pitch;
-  a.k = k;
-  a.band_m = 1;
-  a.band_t = 1;
-  const int x0 = 4 * (tx * kQuadsX + static_cast<int>(threadIdx.x % kQuadsX));
-  const int ksel = (k == 1) ? 1 : (k == 2 ? 2 : 0);
-  const int rows = 4 * A.rows_per_thread;
-  for (int i = 0; i < A.rows_per_thread; ++i) {
-    const int y = ty * rows + static_cast<int>(threadIdx.x / kQuadsX) + 4 * i;
-    if (x0 >= a.pitch || y >= a.h) continue;
-    switch (nb * 4 + ksel) {
-      case 0: vdk::pass_quad<vdk::kMoore, METRIC, 0, COH>(a, x0, y); break;
-      case 1: vdk::pass_quad<vdk::kMoore, METRIC, 1, COH>(a, x0, y); break;
-      case 2: vdk::pass_quad<vdk::kMoore, METRIC, 2, COH>(a, x0, y); break;
-      case 4: vdk::pass_quad<vdk::kVonNeumann, METRIC, 0, COH>(a, x0, y); break;
-      case 5: vdk::pass_quad<vdk::kVonNeumann, METRIC, 1, COH>(a, x0, y); break;
-      default: vdk::pass_quad<vdk::kVonNeumann, METRIC, 2, COH>(a, x0, y); break;
-    }
-  }
-}
-
-__device__ __forceinline__ void finish_sim(const BatchArgs& A, int i) {
-  SimDesc* sd = A.sims + A.act[i];
-  sd->cur ^= (sd->n_pass[A.sched] & 1);
-  if (A.move) sd->step += 1;
-}
-
-// ---- launch-per-phase kernels --------------------------------------------
-
-static __global__ void __launch_bounds__(kThreads) k_batch_move_mark(BatchArgs A) {
-  move_mark_block(A, blockIdx.x);
-}
-
-static __global__ void __launch_bounds__(kThreads) k_batch_min(BatchArgs A) { stamp_min_block(A, blockIdx.x); }
-
-template <int METRIC>
-__global__ void __launch_bounds__(kThreads, 6) k_batch_round(BatchArgs A, int r) {
-  round_tile<METRIC, false>(A, r, blockIdx.x);
-}
-
-static __global__ void k_batch_finish(BatchArgs A) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < A.n_act) finish_sim(A, i);
-}
-
-// ---- the persistent kernel -------------------------------------------------
-
-template <int METRIC>
-__global__ void __launch_bounds__(kThreads, 4) k_batch_persistent(BatchArgs A) {
-  if (*reinterpret_cast<volatile int*>(&A.bar->err) != 0) return;
-  if (A.move || A.mark) {
-    for (int sb = blockIdx.x; sb < A.n_sblk; sb += gridDim.x) move_mark_block(A, sb);
-    if (!grid_sync(A, A.test_skip_arrive && blockIdx.x == 0)) return;
-  }
-  for (int sb = blockIdx.x; sb < A.n_sblk; sb += gridDim.x) stamp_min_block(A, sb);
-  if (!grid_sync(A, false)) return;
-  for (int r = 0; r < A.rounds; ++r) {
-    const int nt = A.round_tiles[r];
-    // maps are rewritten between barriers of this launch: read them at L2
-    for (int t = blockIdx.x; t < nt; t += gridDim.x) round_tile<METRIC, true>(A, r, t);
-    if (!grid_sync(A, false)) return;
-  }
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < A.n_act; i += gridDim.x * blockDim.x) finish_sim(A, i);
-}
-
-}  // namespace vdb
 
 // ---------------------------------------------------------------------------
 // Host side
@@ -270,10 +36,7 @@ struct vd_batch {
   vdb::Barrier* bar = nullptr;
   int* h_err = nullptr;  // pinned mirror of bar->err
   unsigned long long* flag = nullptr;  // device counter for input validation
-  // plan buffers
-  int* d_plan = nullptr;
-  size_t plan_cap = 0;  // ints
-  int* h_plan = nullptr;
+  vdb::PlanSlot plan;
   // configuration
   bool configured = false;
   int32_t d_max = 0, vn_waves = 2, extra = 0, metric = 0;
@@ -296,105 +59,18 @@ struct vd_batch {
 
 namespace {
 
-struct HostPlan {
-  std::vector<int> act;
-  std::vector<int2> sblk;
-  std::vector<int> round_tiles, round_off;
-  std::vector<int2> entries;
-  int rounds = 0;
-  int64_t pixel_passes = 0;
-};
-
-int tiles_of(const vdb::SimDesc& s, int rpt) {
-  const int tx = (s.pitch + 4 * vdb::kQuadsX - 1) / (4 * vdb::kQuadsX);
-  const int ty = (s.h + 4 * rpt - 1) / (4 * rpt);
-  return tx * ty;
-}
-
-HostPlan make_plan(const vd_batch* b, const std::vector<int>& act, int sched) {
-  HostPlan p;
-  p.act = act;
-  for (int i : act) {
-    const vdb::SimDesc& s = b->sims[i];
-    for (int first = 0; first < s.n; first += vdb::kThreads) p.sblk.push_back(make_int2(i, first));
-    p.rounds = std::max(p.rounds, s.n_pass[sched]);
-    p.pixel_passes += static_cast<int64_t>(s.w) * s.h * s.n_pass[sched];
-  }
-  p.round_off.push_back(0);
-  for (int r = 0; r < p.rounds; ++r) {
-    int t = 0;
-    for (int i : act) {
-      const vdb::SimDesc& s = b->sims[i];
-      if (s.n_pass[sched] > r) {
-        p.entries.push_back(make_int2(i, t));
-        t += tiles_of(s, b->rows_per_thread);
-      }
-    }
-    p.round_tiles.push_back(t);
-    p.round_off.push_back(static_cast<int>(p.entries.size()));
-  }
-  return p;
-}
+using vdb::HostPlan;
 
 void drop_graph(vd_batch* b);
 
 // Uploads a plan into the batch's plan buffer.  A cached full-step graph
-// reads that buffer, so any upload invalidates it.
+// reads that buffer, so any upload invalidates it; the pinned staging buffer
+// is reused, so the previous upload must have run.
 int upload_plan(vd_batch* b, const HostPlan& p, vdb::BatchArgs* A) {
   drop_graph(b);
-  const size_t need = p.act.size() + 2 * p.sblk.size() + p.round_tiles.size() + p.round_off.size() +
-                      2 * p.entries.size() + 8;
-  if (need > b->plan_cap) {
-    // plans only grow with the batch: the first full-batch plan sizes the buffer
-    cudaStreamSynchronize(b->stream);
-    cudaFree(b->d_plan);
-    cudaFreeHost(b->h_plan);
-    b->d_plan = nullptr;
-    b->h_plan = nullptr;
-    b->plan_cap = 0;
-    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&b->d_plan), sizeof(int) * need);
-    if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&b->h_plan), sizeof(int) * need);
-    if (e != cudaSuccess) return vd_cuda_check(e, "plan buffers");
-    b->plan_cap = need;
-  } else {
-    // the pinned staging buffer is reused: the previous upload must have run
-    const int rc = vd_cuda_check(cudaStreamSynchronize(b->stream), "synchronize");
-    if (rc) return rc;
-  }
-  int* h = b->h_plan;
-  size_t o = 0;
-  auto put = [&](const int* src, size_t n) {
-    std::memcpy(h + o, src, sizeof(int) * n);
-    o += n;
-  };
-  // int2 sections are read with 8-byte loads: start them on an even int
-  auto align2 = [&]() { o = (o + 1) & ~static_cast<size_t>(1); };
-  const size_t o_act = o;
-  put(p.act.data(), p.act.size());
-  align2();
-  const size_t o_sblk = o;
-  put(reinterpret_cast<const int*>(p.sblk.data()), 2 * p.sblk.size());
-  const size_t o_rt = o;
-  put(p.round_tiles.data(), p.round_tiles.size());
-  const size_t o_ro = o;
-  put(p.round_off.data(), p.round_off.size());
-  align2();
-  const size_t o_ent = o;
-  put(reinterpret_cast<const int*>(p.entries.data()), 2 * p.entries.size());
-  if ((o_sblk | o_ent) & 1) return vd_fail(VD_ECUDA, "internal: misaligned plan section");
-  const int rc = vd_cuda_check(cudaMemcpyAsync(b->d_plan, h, sizeof(int) * o, cudaMemcpyHostToDevice, b->stream),
-                               "upload plan");
+  const int rc = vd_cuda_check(cudaStreamSynchronize(b->stream), "synchronize");
   if (rc) return rc;
-  A->sims = b->d_sims;
-  A->act = b->d_plan + o_act;
-  A->n_act = static_cast<int>(p.act.size());
-  A->sblk = reinterpret_cast<const int2*>(b->d_plan + o_sblk);
-  A->n_sblk = static_cast<int>(p.sblk.size());
-  A->round_tiles = b->d_plan + o_rt;
-  A->round_off = b->d_plan + o_ro;
-  A->entries = reinterpret_cast<const int2*>(b->d_plan + o_ent);
-  A->rounds = p.rounds;
-  return VD_OK;
+  return vdb::plan_upload(b->plan, p, b->d_sims, b->stream, A);
 }
 
 int launch_plan(vd_batch* b, const HostPlan& p, vdb::BatchArgs& A) {
@@ -417,38 +93,11 @@ int launch_plan(vd_batch* b, const HostPlan& p, vdb::BatchArgs& A) {
     ++b->launches;
     return VD_OK;
   }
-  if (A.n_sblk > 0 && (A.move || A.mark)) {
-    vdb::k_batch_move_mark<<<A.n_sblk, vdb::kThreads, 0, st>>>(A);
-    ++b->launches;
-  }
-  if (A.n_sblk > 0) {
-    vdb::k_batch_min<<<A.n_sblk, vdb::kThreads, 0, st>>>(A);
-    ++b->launches;
-  }
-  for (int r = 0; r < p.rounds; ++r) {
-    if (p.round_tiles[r] == 0) continue;
-    if (b->metric == VD_METRIC_MANHATTAN)
-      vdb::k_batch_round<vdk::kManhattan><<<p.round_tiles[r], vdb::kThreads, 0, st>>>(A, r);
-    else
-      vdb::k_batch_round<vdk::kEuclid><<<p.round_tiles[r], vdb::kThreads, 0, st>>>(A, r);
-    ++b->launches;
-  }
-  if (A.n_act > 0) {
-    vdb::k_batch_finish<<<(A.n_act + 255) / 256, 256, 0, st>>>(A);
-    ++b->launches;
-  }
-  return vd_cuda_check(cudaGetLastError(), "batch launch");
+  return vdb::launch_rounds(p, A, b->metric, st, &b->launches);
 }
 
 vdb::BatchArgs base_args(const vd_batch* b) {
-  vdb::BatchArgs A;
-  std::memset(&A, 0, sizeof(A));
-  A.rows_per_thread = b->rows_per_thread;
-  A.bar = b->bar;
-  A.timeout_ns = b->timeout_ns;
-  A.test_skip_arrive = b->test_skip_arrive;
-  A.max_disp = 0;
-  return A;
+  return vdb::make_args(b->rows_per_thread, b->bar, b->timeout_ns, b->test_skip_arrive);
 }
 
 void drop_graph(vd_batch* b) {
@@ -466,8 +115,7 @@ void batch_free(vd_batch* b) {
   cudaFree(b->dxy_stage);
   cudaFree(b->bar);
   cudaFree(b->flag);
-  cudaFree(b->d_plan);
-  cudaFreeHost(b->h_plan);
+  b->plan.release();
   cudaFreeHost(b->h_err);
 }
 
@@ -732,7 +380,7 @@ extern "C" int vd_batch_jfa(vd_batch* b, int32_t metric) {
   const int saved_metric = b->metric, saved_mode = b->mode;
   b->metric = metric;
   b->mode = 0;
-  HostPlan p = make_plan(b, all_sims(b), 1);
+  HostPlan p = vdb::make_plan(b->sims, all_sims(b), 1, b->rows_per_thread);
   vdb::BatchArgs A = base_args(b);
   A.sched = 1;
   A.mark = 0;
@@ -755,7 +403,7 @@ static int batch_step(vd_batch* b, const std::vector<int>& act, bool given, int3
   A.dxy = given ? b->dxy_stage : nullptr;
   A.max_disp = max_disp;
   A.rng_seed = rng_seed;
-  HostPlan p = make_plan(b, act, 0);
+  HostPlan p = vdb::make_plan(b->sims, act, 0, b->rows_per_thread);
   const bool graphable = full && b->use_graphs && b->mode == 0 && b->stream != nullptr;
   if (graphable && b->full_graph && b->full_graph_given == static_cast<int>(given)) {
     // the plan and the arguments baked into the graph are unchanged except the

@@ -382,3 +382,90 @@ class VoronoiBatch:
     @property
     def launches(self) -> int:
         return int(self._lib.vd_batch_launch_count(self._h))
+
+
+class VoronoiServer:
+    """Resident simulations served by step requests with continuous batching."""
+
+    def __init__(self, max_sims: int, hbm_budget_bytes: int, d_max: int, max_disp: int, vn_waves: int = 2,
+                 metric: int = EUCLID, rng_seed: int = 0):
+        self._lib = N.lib()
+        handle = self._lib.vd_server_create(int(max_sims), int(hbm_budget_bytes), int(d_max), int(vn_waves),
+                                            int(metric), int(max_disp), int(rng_seed) & (2**64 - 1))
+        if not handle:
+            raise N.VDError(N.VD_EINVAL, N.last_error())
+        self._h = ctypes.c_void_p(handle)
+        self.shapes = {}
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            self._lib.vd_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def add_sim(self, w: int, h: int, xy) -> int:
+        xy = np.ascontiguousarray(xy, np.int32).reshape(-1, 2)
+        sim = N.check(self._lib.vd_server_add_sim(self._h, int(w), int(h), len(xy), xy.ctypes.data))
+        self.shapes[sim] = (int(w), int(h), len(xy))
+        return sim
+
+    def remove_sim(self, sim: int):
+        N.check(self._lib.vd_server_remove_sim(self._h, int(sim)))
+        self.shapes.pop(sim, None)
+
+    def submit(self, sim: int, t_arrive: float = -1.0) -> int:
+        return N.check(self._lib.vd_server_submit(self._h, int(sim), float(t_arrive)))
+
+    def progress(self) -> int:
+        return N.check(self._lib.vd_server_progress(self._h))
+
+    def drain(self):
+        N.check(self._lib.vd_server_drain(self._h))
+
+    def completions(self, cap: int = 65536):
+        t = np.zeros(cap, np.int64)
+        lat = np.zeros(cap, np.float64)
+        sims = np.zeros(cap, np.int32)
+        n = N.check(self._lib.vd_server_completions(self._h, t.ctypes.data, lat.ctypes.data, sims.ctypes.data, cap))
+        return t[:n], lat[:n], sims[:n]
+
+    def now(self) -> float:
+        return float(self._lib.vd_server_now(self._h))
+
+    def run_trace(self, arrival_s, sims):
+        """Replays (arrival seconds, simulation) pairs; returns per-request latency (s)."""
+        a = np.ascontiguousarray(arrival_s, np.float64)
+        s = np.ascontiguousarray(sims, np.int32)
+        lat = np.zeros(len(a), np.float64)
+        N.check(self._lib.vd_server_run_trace(self._h, a.ctypes.data, s.ctypes.data, len(a), lat.ctypes.data))
+        return lat
+
+    def labels(self, sim: int, out=None):
+        w, h, _ = self.shapes[sim]
+        if out is None:
+            out = np.empty((h, w), np.int32)
+        ptr, dev = _buf(out, w * h, writable=True)
+        N.check(self._lib.vd_server_get_labels(self._h, int(sim), ptr, dev))
+        return out
+
+    def stats(self) -> dict:
+        u, b, p, sd, la = (ctypes.c_int64() for _ in range(5))
+        live = ctypes.c_int32()
+        N.check(self._lib.vd_server_stats(self._h, ctypes.byref(u), ctypes.byref(b), ctypes.byref(live),
+                                          ctypes.byref(p), ctypes.byref(sd), ctypes.byref(la)))
+        return {"used_bytes": u.value, "budget_bytes": b.value, "live_sims": live.value, "pending": p.value,
+                "steps_done": sd.value, "launches": la.value}
+
+    def set_max_batch(self, n: int):
+        N.check(self._lib.vd_server_set_max_batch(self._h, int(n)))
