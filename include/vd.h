@@ -329,6 +329,8 @@ int vd_batch_step_subset(vd_batch* batch, const int32_t* sims, int32_t n, int32_
 #define VD_BOPT_BARRIER_TIMEOUT_US 5 /* persistent mode: bounded barrier wait (default 2 s) */
 #define VD_BOPT_TEST_SKIP_ARRIVE 6   /* test only: block 0 skips its first barrier arrival so the
                                         other blocks' wait must run out (default 0) */
+#define VD_BOPT_CLAMPED_KEYS 7       /* as VD_OPT_CLAMPED_KEYS (-1 auto, 0 never, 1 always when usable);
+                                        applied at the next vd_batch_configure / vd_batch_jfa */
 int vd_batch_set_option(vd_batch* batch, int32_t option, int64_t value);
 int vd_batch_get_option(const vd_batch* batch, int32_t option, int64_t* value);
 
@@ -422,6 +424,10 @@ int vd_server_set_max_batch(vd_server* server, int32_t max_batch);
 #define VD_OPT_FUSE_TILE_Y 5     /* fused-group tile height in pixels (1..128) */
 #define VD_OPT_PROFILE 6         /* 1 = bracket every kernel launch with CUDA events (frames then run
                                     eagerly, never from a graph); read with vd_profile_read */
+#define VD_OPT_CLAMPED_KEYS 7    /* Euclidean passes with one 32-bit key per candidate (min(d^2, cap) *
+                                    2^lb + label, exact: quads that reach the cap are recomputed with
+                                    the 64-bit key): -1 = auto (default: dJFA passes), 0 = never,
+                                    1 = always when usable (>= 9 seeds) */
 int vd_set_option(vd_ctx* ctx, int32_t option, int64_t value);
 int vd_get_option(const vd_ctx* ctx, int32_t option, int64_t* value);
 

@@ -141,22 +141,45 @@ int ensure_smem(const void* fn, size_t bytes, size_t* done) {
   return VD_OK;
 }
 
-template <int NB, int METRIC>
+template <int NB, int METRIC, bool CLAMP>
 static void launch_pass_t(int ksel, dim3 g, dim3 b, cudaStream_t st, const vdk::PassArgs& a) {
   switch (ksel) {
-    case 0: vdk::k_pass<NB, METRIC, 0><<<g, b, 0, st>>>(a); break;
-    case 1: vdk::k_pass<NB, METRIC, 1><<<g, b, 0, st>>>(a); break;
-    case 2: vdk::k_pass<NB, METRIC, 2><<<g, b, 0, st>>>(a); break;
-    default: vdk::k_pass<NB, METRIC, 3><<<g, b, 0, st>>>(a); break;
+    case 0: vdk::k_pass<NB, METRIC, 0, CLAMP><<<g, b, 0, st>>>(a); break;
+    case 1: vdk::k_pass<NB, METRIC, 1, CLAMP><<<g, b, 0, st>>>(a); break;
+    case 2: vdk::k_pass<NB, METRIC, 2, CLAMP><<<g, b, 0, st>>>(a); break;
+    default: vdk::k_pass<NB, METRIC, 3, CLAMP><<<g, b, 0, st>>>(a); break;
   }
 }
 
+int label_bits(int32_t n) {
+  int lb = 0;
+  while ((int64_t{1} << lb) < n) ++lb;
+  return lb;
+}
+
+bool use_clamp(int clamp_option, int32_t metric, int32_t n, int32_t k, bool djfa_frame) {
+  (void)k;
+  if (clamp_option == 0 || metric != VD_METRIC_EUCLID) return false;
+  if (label_bits(n) < 4) return false;
+  if (clamp_option == 1) return true;
+  // auto: dJFA passes only.  The previous map is nearly right there, so quads
+  // almost never reach the cap; in a JFA frame the early passes still see many
+  // empty pixels, whose quads would be recomputed with the exact form.
+  return djfa_frame;
+}
+
 int launch_pass(const MapView& m, const int32_t* src, int32_t* dst, int32_t k, int32_t nb,
-                int32_t metric, int64_t band_min_k, cudaStream_t st) {
+                int32_t metric, int64_t band_min_k, bool clamp, cudaStream_t st) {
   vdk::PassArgs a;
   a.src = src;
   a.dst = dst;
   a.table = m.table;
+  a.ptable = m.ptable;
+  {
+    const int lb = label_bits(m.n);
+    a.mul = lb >= 32 ? 0u : (1u << lb);
+    a.cap = lb >= 4 ? static_cast<uint32_t>((uint64_t{1} << (32 - lb)) - 1) : 0u;
+  }
   a.n_seeds = static_cast<uint32_t>(m.n);
   a.w = m.w;
   a.h = m.h;
@@ -183,12 +206,21 @@ int launch_pass(const MapView& m, const int32_t* src, int32_t* dst, int32_t k, i
     grid.y = a.band_m * a.band_t;
   }
   const int ksel = (k % 4 == 0) ? 0 : (k == 1 ? 1 : (k == 2 ? 2 : 3));
+  if (clamp && (metric != VD_METRIC_EUCLID || a.cap == 0)) clamp = false;
   if (nb == VD_NB_MOORE) {
-    if (metric == VD_METRIC_EUCLID) launch_pass_t<vdk::kMoore, vdk::kEuclid>(ksel, grid, block, st, a);
-    else launch_pass_t<vdk::kMoore, vdk::kManhattan>(ksel, grid, block, st, a);
+    if (metric == VD_METRIC_EUCLID) {
+      if (clamp) launch_pass_t<vdk::kMoore, vdk::kEuclid, true>(ksel, grid, block, st, a);
+      else launch_pass_t<vdk::kMoore, vdk::kEuclid, false>(ksel, grid, block, st, a);
+    } else {
+      launch_pass_t<vdk::kMoore, vdk::kManhattan, false>(ksel, grid, block, st, a);
+    }
   } else {
-    if (metric == VD_METRIC_EUCLID) launch_pass_t<vdk::kVonNeumann, vdk::kEuclid>(ksel, grid, block, st, a);
-    else launch_pass_t<vdk::kVonNeumann, vdk::kManhattan>(ksel, grid, block, st, a);
+    if (metric == VD_METRIC_EUCLID) {
+      if (clamp) launch_pass_t<vdk::kVonNeumann, vdk::kEuclid, true>(ksel, grid, block, st, a);
+      else launch_pass_t<vdk::kVonNeumann, vdk::kEuclid, false>(ksel, grid, block, st, a);
+    } else {
+      launch_pass_t<vdk::kVonNeumann, vdk::kManhattan, false>(ksel, grid, block, st, a);
+    }
   }
   return vd_cuda_check(cudaGetLastError(), "jump pass launch");
 }
@@ -264,7 +296,7 @@ std::vector<Launch> plan_passes(const int32_t* ks, const int32_t* nbs, int n, in
 
 int run_passes(const MapView& m, int32_t* const buf[2], int* cur, const int32_t* ks,
                const int32_t* nbs, int n, int32_t metric, const Tuning& t, cudaStream_t st,
-               int64_t* launches, Profiler* prof) {
+               int64_t* launches, Profiler* prof, bool djfa_frame) {
   const std::vector<Launch> plan = plan_passes(ks, nbs, n, t.fuse_max_k, t.max_halo);
   const int64_t px = static_cast<int64_t>(m.w) * m.h;
   for (const Launch& l : plan) {
@@ -273,7 +305,8 @@ int run_passes(const MapView& m, int32_t* const buf[2], int* cur, const int32_t*
     int rc;
     const int pi = prof ? prof->begin(l.n == 1 ? VD_KERNEL_PASS : VD_KERNEL_FUSED, px * l.n, st) : -1;
     if (l.n == 1) {
-      rc = launch_pass(m, src, dst, ks[l.first], nbs[l.first], metric, t.band_min_k, st);
+      rc = launch_pass(m, src, dst, ks[l.first], nbs[l.first], metric, t.band_min_k,
+                       use_clamp(t.clamp, metric, m.n, ks[l.first], djfa_frame), st);
     } else {
       rc = launch_fused(m, src, dst, ks + l.first, nbs + l.first, l.n, metric, t.tile_x, t.tile_y, st);
     }
@@ -307,14 +340,14 @@ int launch_stamp(const MapView& m, int32_t* labels, bool mark, cudaStream_t st, 
   return vd_cuda_check(cudaGetLastError(), "stamp launch");
 }
 
-int launch_move(int2* seeds, int2* table, int n, const int2* dxy, int w, int h, int max_disp,
+int launch_move(int2* seeds, int2* table, int2* ptable, int n, const int2* dxy, int w, int h, int max_disp,
                 uint64_t key, uint64_t step, cudaStream_t st) {
-  vdk::k_move<<<grid1d(n, 256), 256, 0, st>>>(seeds, table, n, dxy, w, h, max_disp, key, step);
+  vdk::k_move<<<grid1d(n, 256), 256, 0, st>>>(seeds, table, ptable, n, dxy, w, h, max_disp, key, step);
   return vd_cuda_check(cudaGetLastError(), "move launch");
 }
 
-int launch_build_table(const int2* seeds, int n, int2* table, cudaStream_t st) {
-  vdk::k_build_table<<<grid1d(n, 256), 256, 0, st>>>(seeds, n, table);
+int launch_build_table(const int2* seeds, int n, int2* table, int2* ptable, cudaStream_t st) {
+  vdk::k_build_table<<<grid1d(n, 256), 256, 0, st>>>(seeds, n, table, ptable);
   return vd_cuda_check(cudaGetLastError(), "table launch");
 }
 
@@ -401,7 +434,8 @@ struct vd_ctx {
   int32_t* buf[2] = {nullptr, nullptr};
   int cur = 0;
   int2* seeds = nullptr;
-  int2* table = nullptr;  // n + 1 entries, [0] = sentinel
+  int2* table = nullptr;   // n + 1 entries, [0] = sentinel
+  int2* ptable = nullptr;  // n + 1 positions, [0] = far sentinel
   int2* dxy_stage = nullptr;
   unsigned long long* counters = nullptr;      // [0] n_exact, [1] n_match, [2] flag
   unsigned long long* host_counters = nullptr;  // pinned mirror
@@ -428,6 +462,7 @@ static vdi::MapView view(const vd_ctx* c) {
   m.n = c->n;
   m.seeds = c->seeds;
   m.table = c->table + 1;
+  m.ptable = c->ptable + 1;
   return m;
 }
 
@@ -449,6 +484,7 @@ static void ctx_free(vd_ctx* c) {
   cudaFree(c->buf[1]);
   cudaFree(c->seeds);
   cudaFree(c->table);
+  cudaFree(c->ptable);
   cudaFree(c->dxy_stage);
   cudaFree(c->counters);
   cudaFreeHost(c->host_counters);
@@ -480,6 +516,7 @@ extern "C" vd_ctx* vd_create(int32_t w, int32_t h, int32_t n) {
   rc = rc ? rc : ctx_alloc(reinterpret_cast<void**>(&c->buf[1]), map_bytes, "label map");
   rc = rc ? rc : ctx_alloc(reinterpret_cast<void**>(&c->seeds), sizeof(int2) * n, "seeds");
   rc = rc ? rc : ctx_alloc(reinterpret_cast<void**>(&c->table), sizeof(int2) * (static_cast<size_t>(n) + 1), "seed table");
+  rc = rc ? rc : ctx_alloc(reinterpret_cast<void**>(&c->ptable), sizeof(int2) * (static_cast<size_t>(n) + 1), "seed table");
   rc = rc ? rc : ctx_alloc(reinterpret_cast<void**>(&c->dxy_stage), sizeof(int2) * n, "moves");
   rc = rc ? rc : ctx_alloc(reinterpret_cast<void**>(&c->counters), 4 * sizeof(unsigned long long), "counters");
   if (!rc) {
@@ -489,7 +526,7 @@ extern "C" vd_ctx* vd_create(int32_t w, int32_t h, int32_t n) {
   if (!rc) rc = vd_cuda_check(cudaMemset(c->buf[0], 0xFF, map_bytes), "init map");
   if (!rc) rc = vd_cuda_check(cudaMemset(c->buf[1], 0xFF, map_bytes), "init map");
   if (!rc) rc = vd_cuda_check(cudaMemset(c->seeds, 0, sizeof(int2) * n), "init seeds");
-  if (!rc) rc = vdi::launch_build_table(c->seeds, n, c->table, nullptr);
+  if (!rc) rc = vdi::launch_build_table(c->seeds, n, c->table, c->ptable, nullptr);
   if (!rc) rc = vd_cuda_check(cudaDeviceSynchronize(), "create");
   if (rc) {
     ctx_free(c);
@@ -551,7 +588,7 @@ extern "C" int vd_set_seeds(vd_ctx* c, const int32_t* xy, int on_device) {
                                  "copy seeds");
     if (rc) return rc;
     ++c->launches;
-    return vdi::launch_build_table(c->seeds, c->n, c->table, c->stream);
+    return vdi::launch_build_table(c->seeds, c->n, c->table, c->ptable, c->stream);
   }
   // device input: validate in the staging buffer so that rejected seeds never
   // reach the kernels that index the map with them
@@ -572,7 +609,7 @@ extern "C" int vd_set_seeds(vd_ctx* c, const int32_t* xy, int on_device) {
                      "copy seeds");
   if (rc) return rc;
   ++c->launches;
-  return vdi::launch_build_table(c->seeds, c->n, c->table, c->stream);
+  return vdi::launch_build_table(c->seeds, c->n, c->table, c->ptable, c->stream);
 }
 
 extern "C" int vd_get_seeds(vd_ctx* c, int32_t* xy, int on_device) {
@@ -606,7 +643,7 @@ extern "C" int vd_move_seeds(vd_ctx* c, const int32_t* dxy, int dxy_on_device, i
   }
   vdi::Profiler* pr = prof_of(c);
   const int pi = pr ? pr->begin(VD_KERNEL_MOVE, c->n, c->stream) : -1;
-  const int rc = vdi::launch_move(c->seeds, c->table, c->n, d, c->w, c->h, max_disp,
+  const int rc = vdi::launch_move(c->seeds, c->table, c->ptable, c->n, d, c->w, c->h, max_disp,
                                   vdi::rng_key(rng_seed, stream_id), static_cast<uint64_t>(step), c->stream);
   if (pr) pr->end(pi, c->stream);
   ++c->launches;
@@ -679,7 +716,8 @@ extern "C" int vd_jfa(vd_ctx* c, int32_t extra, int32_t metric) {
     rc = vdi::launch_stamp(view(c), c->buf[c->cur], false, c->stream, &c->launches);
     if (pr) pr->end(pi, c->stream);
     if (rc) return rc;
-    return vdi::run_passes(view(c), c->buf, &c->cur, ks, nbs, n, metric, c->tune, c->stream, &c->launches, pr);
+    return vdi::run_passes(view(c), c->buf, &c->cur, ks, nbs, n, metric, c->tune, c->stream, &c->launches, pr,
+                           false);
   };
   return run_frame(c, std::make_tuple(0, c->cur, extra, metric, 0, 0, 0), nl + 2, cur_after, body);
 }
@@ -698,7 +736,8 @@ extern "C" int vd_djfa_step(vd_ctx* c, int32_t d_max, int32_t vn_waves, int32_t 
     const int rc = vdi::launch_stamp(view(c), c->buf[c->cur], true, c->stream, &c->launches);
     if (pr) pr->end(pi, c->stream);
     if (rc) return rc;
-    return vdi::run_passes(view(c), c->buf, &c->cur, ks, nbs, n, metric, c->tune, c->stream, &c->launches, pr);
+    return vdi::run_passes(view(c), c->buf, &c->cur, ks, nbs, n, metric, c->tune, c->stream, &c->launches, pr,
+                           true);
   };
   return run_frame(c, std::make_tuple(1, c->cur, d_max, vn_waves, extra, metric, 0), nl + 2, cur_after, body);
 }
@@ -714,7 +753,8 @@ extern "C" int vd_pass(vd_ctx* c, int32_t k, int32_t nb, int32_t metric) {
   if (k < 1) return vd_fail(VD_EINVAL, "step %d < 1", k);
   if (nb != VD_NB_MOORE && nb != VD_NB_VON_NEUMANN) return vd_fail(VD_EINVAL, "neighbourhood %d", nb);
   const int rc = vdi::launch_pass(view(c), c->buf[c->cur], c->buf[c->cur ^ 1], k, nb, metric,
-                                  c->tune.band_min_k, c->stream);
+                                  c->tune.band_min_k, vdi::use_clamp(c->tune.clamp, metric, c->n, k, false),
+                                  c->stream);
   if (rc) return rc;
   ++c->launches;
   c->cur ^= 1;
@@ -929,6 +969,10 @@ extern "C" int vd_set_option(vd_ctx* c, int32_t option, int64_t value) {
       if (value != 0 && value != 1) return vd_fail(VD_EINVAL, "profile must be 0 or 1");
       t.profile = static_cast<int>(value);
       break;
+    case VD_OPT_CLAMPED_KEYS:
+      if (value < -1 || value > 1) return vd_fail(VD_EINVAL, "clamped keys must be -1, 0 or 1");
+      t.clamp = static_cast<int>(value);
+      break;
     default:
       return vd_fail(VD_EINVAL, "unknown option %d", option);
   }
@@ -950,6 +994,7 @@ extern "C" int vd_get_option(const vd_ctx* c, int32_t option, int64_t* value) {
     case VD_OPT_FUSE_TILE_X: *value = c->tune.tile_x; break;
     case VD_OPT_FUSE_TILE_Y: *value = c->tune.tile_y; break;
     case VD_OPT_PROFILE: *value = c->tune.profile; break;
+    case VD_OPT_CLAMPED_KEYS: *value = c->tune.clamp; break;
     default: return vd_fail(VD_EINVAL, "unknown option %d", option);
   }
   return VD_OK;

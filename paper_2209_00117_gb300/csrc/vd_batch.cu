@@ -30,6 +30,7 @@ struct vd_batch {
   size_t arena_bytes = 0;
   int2* seeds = nullptr;
   int2* tables = nullptr;
+  int2* ptables = nullptr;
   int2* dxy_stage = nullptr;
   int64_t total_seeds = 0;
   int64_t total_pixels = 0;
@@ -47,6 +48,7 @@ struct vd_batch {
   int use_graphs = 1;
   long long timeout_ns = 2000000000LL;
   int test_skip_arrive = 0;
+  int clamp = -1;  // clamped 32-bit keys: -1 auto, 0 never, 1 whenever usable
   int64_t launches = 0;
   // cached full-batch dJFA plan + graph
   int full_plan_valid = 0;
@@ -112,6 +114,7 @@ void batch_free(vd_batch* b) {
   cudaFree(b->arena);
   cudaFree(b->seeds);
   cudaFree(b->tables);
+  cudaFree(b->ptables);
   cudaFree(b->dxy_stage);
   cudaFree(b->bar);
   cudaFree(b->flag);
@@ -185,6 +188,7 @@ extern "C" vd_batch* vd_batch_create(int32_t n_sims, const int32_t* w, const int
   cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&b->arena), b->arena_bytes);
   if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&b->seeds), sizeof(int2) * seeds);
   if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&b->tables), sizeof(int2) * (seeds + n_sims));
+  if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&b->ptables), sizeof(int2) * (seeds + n_sims));
   if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&b->dxy_stage), sizeof(int2) * seeds);
   if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&b->d_sims), sizeof(vdb::SimDesc) * n_sims);
   if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&b->bar), sizeof(vdb::Barrier));
@@ -210,13 +214,15 @@ extern "C" vd_batch* vd_batch_create(int32_t n_sims, const int32_t* w, const int
     off += 2 * m;
     s.seeds = b->seeds + s.seed_off;
     s.table = b->tables + toff;
+    s.ptable = b->ptables + toff;
     toff += s.n + 1;
     // JFA schedule (index 1); the dJFA one is filled by vd_batch_configure
     s.n_pass[1] = vdi::fill_schedule(vdi::jfa_first_step(s.w, s.h), 0, 0, s.ks[1], s.nbs[1], vdb::kMaxPasses);
+    vdb::set_clamp(s, 1, VD_METRIC_EUCLID, b->clamp);
   }
   int rc = upload_sims(b);
   for (int i = 0; !rc && i < n_sims; ++i)
-    rc = vdi::launch_build_table(b->sims[i].seeds, b->sims[i].n, b->sims[i].table, b->stream);
+    rc = vdi::launch_build_table(b->sims[i].seeds, b->sims[i].n, b->sims[i].table, b->sims[i].ptable, b->stream);
   if (!rc) rc = vd_cuda_check(cudaStreamSynchronize(b->stream), "create");
   if (rc) {
     batch_free(b);
@@ -306,7 +312,7 @@ extern "C" int vd_batch_set_seeds(vd_batch* b, const int32_t* xy, int on_device)
   }
   if (rc) return rc;
   for (int i = 0; !rc && i < b->n_sims; ++i) {
-    rc = vdi::launch_build_table(b->sims[i].seeds, b->sims[i].n, b->sims[i].table, b->stream);
+    rc = vdi::launch_build_table(b->sims[i].seeds, b->sims[i].n, b->sims[i].table, b->sims[i].ptable, b->stream);
     ++b->launches;
   }
   return rc;
@@ -347,9 +353,11 @@ extern "C" int vd_batch_configure(vd_batch* b, int32_t d_max, int32_t vn_waves, 
   if (d_max < 0 || vn_waves < 0 || extra < 0 || extra > 2) return vd_fail(VD_EINVAL, "bad dJFA parameters");
   int rc = pull_state(b);
   if (rc) return rc;
-  for (vdb::SimDesc& s : b->sims)
+  for (vdb::SimDesc& s : b->sims) {
     s.n_pass[0] = vdi::fill_schedule(vdi::djfa_first_step(s.w, s.h, s.n, d_max), vn_waves, extra, s.ks[0], s.nbs[0],
                                      vdb::kMaxPasses);
+    vdb::set_clamp(s, 0, metric, b->clamp);
+  }
   b->d_max = d_max;
   b->vn_waves = vn_waves;
   b->extra = extra;
@@ -370,6 +378,9 @@ extern "C" int vd_batch_jfa(vd_batch* b, int32_t metric) {
   if (metric != VD_METRIC_EUCLID && metric != VD_METRIC_MANHATTAN) return vd_fail(VD_EINVAL, "metric %d", metric);
   int rc = vd_batch_synchronize(b);
   if (!rc) rc = pull_state(b);
+  if (rc) return rc;
+  for (vdb::SimDesc& s : b->sims) vdb::set_clamp(s, 1, metric, b->clamp);
+  rc = upload_sims(b);
   if (rc) return rc;
   // frame 0 of every simulation: empty both buffers' current map, stamp, JFA passes
   for (const vdb::SimDesc& s : b->sims) {
@@ -502,6 +513,11 @@ extern "C" int vd_batch_set_option(vd_batch* b, int32_t option, int64_t value) {
       if (value != 0 && value != 1) return vd_fail(VD_EINVAL, "test flag must be 0 or 1");
       b->test_skip_arrive = static_cast<int>(value);
       break;
+    case VD_BOPT_CLAMPED_KEYS:
+      if (value < -1 || value > 1) return vd_fail(VD_EINVAL, "clamped keys must be -1, 0 or 1");
+      b->clamp = static_cast<int>(value);
+      // takes effect at the next vd_batch_configure / vd_batch_jfa
+      break;
     default:
       return vd_fail(VD_EINVAL, "unknown batch option %d", option);
   }
@@ -519,6 +535,7 @@ extern "C" int vd_batch_get_option(const vd_batch* b, int32_t option, int64_t* v
     case VD_BOPT_USE_GRAPHS: *value = b->use_graphs; break;
     case VD_BOPT_BARRIER_TIMEOUT_US: *value = b->timeout_ns / 1000; break;
     case VD_BOPT_TEST_SKIP_ARRIVE: *value = b->test_skip_arrive; break;
+    case VD_BOPT_CLAMPED_KEYS: *value = b->clamp; break;
     default: return vd_fail(VD_EINVAL, "unknown batch option %d", option);
   }
   return VD_OK;
@@ -543,6 +560,7 @@ struct Snapshot {
   int32_t* arena = nullptr;
   int2* seeds = nullptr;
   int2* tables = nullptr;
+  int2* ptables = nullptr;
   vdb::SimDesc* sims = nullptr;
   void release() {
     cudaFree(arena);
@@ -563,6 +581,9 @@ int snapshot_copy(vd_batch* b, Snapshot& sn, bool save) {
                                        sizeof(int2) * b->total_seeds, k, st), "snapshot seeds");
   if (!rc)
     rc = vd_cuda_check(cudaMemcpyAsync(save ? sn.tables : b->tables, save ? b->tables : sn.tables,
+                                       sizeof(int2) * (b->total_seeds + b->n_sims), k, st), "snapshot tables");
+  if (!rc)
+    rc = vd_cuda_check(cudaMemcpyAsync(save ? sn.ptables : b->ptables, save ? b->ptables : sn.ptables,
                                        sizeof(int2) * (b->total_seeds + b->n_sims), k, st), "snapshot tables");
   if (!rc)
     rc = vd_cuda_check(cudaMemcpyAsync(save ? sn.sims : b->d_sims, save ? b->d_sims : sn.sims,
@@ -588,6 +609,7 @@ extern "C" int vd_batch_autotune(vd_batch* b, int32_t steps, int32_t max_disp, u
   cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&sn.arena), b->arena_bytes);
   if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&sn.seeds), sizeof(int2) * b->total_seeds);
   if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&sn.tables), sizeof(int2) * (b->total_seeds + b->n_sims));
+  if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&sn.ptables), sizeof(int2) * (b->total_seeds + b->n_sims));
   if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&sn.sims), sizeof(vdb::SimDesc) * b->n_sims);
   if (e != cudaSuccess) {
     sn.release();

@@ -30,7 +30,10 @@ struct SimDesc {
   int w, h, pitch, n;
   int32_t* map[2];
   int2* seeds;
-  int2* table;  // entry 0 = sentinel; the pass table is table + 1
+  int2* table;   // entry 0 = sentinel; the pass table is table + 1
+  int2* ptable;  // positions, entry 0 = far sentinel; used as ptable + 1
+  uint32_t cap, mul;       // clamped-key parameters (cap = 0: unusable)
+  uint32_t clampmask[2];   // bit r: pass r of the schedule uses clamped keys
   int seed_off;
   int cur;
   long long step;      // moves drawn so far (the RNG step of the next move)
@@ -143,6 +146,7 @@ __device__ __forceinline__ void move_mark_block(const BatchArgs& A, int sb) {
     p.y = static_cast<int>(y);
     sd->seeds[k] = p;
     sd->table[k + 1] = vdk::table_entry(p);
+    sd->ptable[k + 1] = p;
   }
   if (A.mark) sd->map[sd->cur][static_cast<int64_t>(p.y) * sd->pitch + p.x] = k;
 }
@@ -177,6 +181,9 @@ __device__ __forceinline__ void round_tile(const BatchArgs& A, int r, int t) {
   a.src = sd->map[(sd->cur + r) & 1];
   a.dst = sd->map[(sd->cur + r + 1) & 1];
   a.table = sd->table + 1;
+  a.ptable = sd->ptable + 1;
+  a.cap = sd->cap;
+  a.mul = sd->mul;
   a.n_seeds = static_cast<uint32_t>(sd->n);
   a.w = sd->w;
   a.h = sd->h;
@@ -186,10 +193,22 @@ __device__ __forceinline__ void round_tile(const BatchArgs& A, int r, int t) {
   a.band_t = 1;
   const int x0 = 4 * (tx * kQuadsX + static_cast<int>(threadIdx.x % kQuadsX));
   const int ksel = (k == 1) ? 1 : (k == 2 ? 2 : 0);
+  const bool clamp = METRIC == vdk::kEuclid && ((sd->clampmask[A.sched] >> r) & 1u);
   const int rows = 4 * A.rows_per_thread;
   for (int i = 0; i < A.rows_per_thread; ++i) {
     const int y = ty * rows + static_cast<int>(threadIdx.x / kQuadsX) + 4 * i;
     if (x0 >= a.pitch || y >= a.h) continue;
+    if (clamp) {
+      switch (nb * 4 + ksel) {
+        case 0: vdk::pass_quad_clamped<vdk::kMoore, 0, COH>(a, x0, y); break;
+        case 1: vdk::pass_quad_clamped<vdk::kMoore, 1, COH>(a, x0, y); break;
+        case 2: vdk::pass_quad_clamped<vdk::kMoore, 2, COH>(a, x0, y); break;
+        case 4: vdk::pass_quad_clamped<vdk::kVonNeumann, 0, COH>(a, x0, y); break;
+        case 5: vdk::pass_quad_clamped<vdk::kVonNeumann, 1, COH>(a, x0, y); break;
+        default: vdk::pass_quad_clamped<vdk::kVonNeumann, 2, COH>(a, x0, y); break;
+      }
+      continue;
+    }
     switch (nb * 4 + ksel) {
       case 0: vdk::pass_quad<vdk::kMoore, METRIC, 0, COH>(a, x0, y); break;
       case 1: vdk::pass_quad<vdk::kMoore, METRIC, 1, COH>(a, x0, y); break;
@@ -289,6 +308,18 @@ inline HostPlan make_plan(const std::vector<SimDesc>& sims, const std::vector<in
   return p;
 }
 
+
+// Clamped-key parameters and per-pass choices of one simulation for one
+// schedule (sched 0 = dJFA, 1 = JFA) under `metric`.
+inline void set_clamp(SimDesc& s, int sched, int32_t metric, int clamp_option) {
+  const int lb = vdi::label_bits(s.n);
+  s.mul = lb >= 32 ? 0u : (1u << lb);
+  s.cap = lb >= 4 ? static_cast<uint32_t>((uint64_t{1} << (32 - lb)) - 1) : 0u;
+  uint32_t mask = 0;
+  for (int r = 0; r < s.n_pass[sched] && r < 32; ++r)
+    if (vdi::use_clamp(clamp_option, metric, s.n, s.ks[sched][r], sched == 0)) mask |= 1u << r;
+  s.clampmask[sched] = mask;
+}
 
 // A pinned host staging buffer and a device buffer for one plan.
 struct PlanSlot {

@@ -18,8 +18,15 @@ namespace vdi {
 struct MapView {
   int32_t w = 0, h = 0, pitch = 0, n = 0;
   const int2* seeds = nullptr;
-  const int2* table = nullptr;  // pass table, entry -1 = sentinel
+  const int2* table = nullptr;   // packed pass table, entry -1 = sentinel
+  const int2* ptable = nullptr;  // position table, entry -1 = far sentinel
 };
+
+// Bits of the largest label (ceil(log2 n_seeds)); clamped 32-bit keys need
+// lb >= 4, so that the far sentinel lies beyond the cap 2^(32 - lb) - 1.
+int label_bits(int32_t n_seeds);
+// Whether a pass with step k uses the clamped key form.
+bool use_clamp(int clamp_option, int32_t metric, int32_t n_seeds, int32_t k, bool djfa_frame);
 
 // Launch-shape choices of the jump passes.
 struct Tuning {
@@ -30,6 +37,7 @@ struct Tuning {
   int tile_x = 64;
   int tile_y = 32;
   int profile = 0;
+  int clamp = -1;  // clamped 32-bit keys: -1 auto, 0 never, 1 whenever usable
 };
 
 // Event pairs bracketing kernel launches (profiling mode).  Records are kept
@@ -69,18 +77,18 @@ int fill_schedule(int32_t first, int32_t vn_waves, int32_t extra, int32_t* ks, i
 std::vector<Launch> plan_passes(const int32_t* ks, const int32_t* nbs, int n, int fuse_max_k,
                                 int max_halo);
 int launch_pass(const MapView& m, const int32_t* src, int32_t* dst, int32_t k, int32_t nb,
-                int32_t metric, int64_t band_min_k, cudaStream_t st);
+                int32_t metric, int64_t band_min_k, bool clamp, cudaStream_t st);
 int launch_fused(const MapView& m, const int32_t* src, int32_t* dst, const int32_t* ks,
                  const int32_t* nbs, int n, int32_t metric, int tile_x, int tile_y,
                  cudaStream_t st);
 int run_passes(const MapView& m, int32_t* const buf[2], int* cur, const int32_t* ks,
                const int32_t* nbs, int n, int32_t metric, const Tuning& t, cudaStream_t st,
-               int64_t* launches, Profiler* prof);
+               int64_t* launches, Profiler* prof, bool djfa_frame);
 int launch_fill(int32_t* buf, int64_t n_elems, int32_t v, cudaStream_t st);
 int launch_stamp(const MapView& m, int32_t* labels, bool mark, cudaStream_t st, int64_t* launches);
-int launch_move(int2* seeds, int2* table, int n, const int2* dxy, int w, int h, int max_disp,
+int launch_move(int2* seeds, int2* table, int2* ptable, int n, const int2* dxy, int w, int h, int max_disp,
                 uint64_t key, uint64_t step, cudaStream_t st);
-int launch_build_table(const int2* seeds, int n, int2* table, cudaStream_t st);
+int launch_build_table(const int2* seeds, int n, int2* table, int2* ptable, cudaStream_t st);
 uint64_t rng_key(uint64_t rng_seed, uint64_t stream_id);
 int ensure_smem(const void* fn, size_t bytes, size_t* done);
 

@@ -110,7 +110,10 @@ __device__ __forceinline__ int map1(const int32_t* p) {
 struct PassArgs {
   const int32_t* __restrict__ src;
   int32_t* __restrict__ dst;
-  const int2* __restrict__ table;  // entry -1 is the sentinel
+  const int2* __restrict__ table;   // packed {x | y << 16, x^2 + y^2}; entry -1 is the sentinel
+  const int2* __restrict__ ptable;  // positions {x, y}; entry -1 is the far sentinel
+  uint32_t cap;                     // clamped-key passes: distance cap 2^(32 - lb) - 1
+  uint32_t mul;                     // and 2^lb, lb = bits of the largest label
   uint32_t n_seeds;
   int w, h, pitch, k;
   int band_m;  // > 1: visit row-blocks in k-strided bands (band_m = k / rows per block)
@@ -133,22 +136,61 @@ __device__ __forceinline__ int4 shift_right_by(const int4& m, const int4& r, int
 }
 
 // The four pixels (x0 .. x0+3, y) owned by one thread and their packed
-// best (key, label) so far.
+// best (key, label) so far: the exact 64-bit form.
 template <int METRIC, bool COH>
 struct Quad {
   long long b0, b1, b2, b3;
   int m2x, m2y, x0, y;
-  __device__ __forceinline__ void init(const int4& L, const int2* __restrict__ table) {
+  const int2* __restrict__ table;
+  __device__ __forceinline__ Quad(const PassArgs& a, int x0_, int y_)
+      : m2x(-2 * x0_), m2y(-2 * y_), x0(x0_), y(y_), table(a.table) {}
+  __device__ __forceinline__ void init(const int4& L) {
     b0 = cand<METRIC, COH>(L.x, table, m2x, m2y, x0, y);
     b1 = cand<METRIC, COH>(L.y, table, m2x - 2, m2y, x0 + 1, y);
     b2 = cand<METRIC, COH>(L.z, table, m2x - 4, m2y, x0 + 2, y);
     b3 = cand<METRIC, COH>(L.w, table, m2x - 6, m2y, x0 + 3, y);
   }
-  __device__ __forceinline__ void fold4(const int4& L, const int2* __restrict__ table) {
+  __device__ __forceinline__ void fold4(const int4& L) {
     b0 = fold<METRIC, COH>(b0, L.x, table, m2x, m2y, x0, y);
     b1 = fold<METRIC, COH>(b1, L.y, table, m2x - 2, m2y, x0 + 1, y);
     b2 = fold<METRIC, COH>(b2, L.z, table, m2x - 4, m2y, x0 + 2, y);
     b3 = fold<METRIC, COH>(b3, L.w, table, m2x - 6, m2y, x0 + 3, y);
+  }
+};
+
+// Clamped 32-bit form (Euclidean): key = min(d^2, cap) * 2^lb + label, with
+// cap = 2^(32 - lb) - 1 and every label below 2^lb.  For any pixel whose best
+// candidate lies below distance^2 cap - 1 this orders the candidates exactly
+// as the 64-bit form (distance, then lowest label), with one 32-bit minimum
+// and one clamp instead of the 64-bit compare-and-select.  An empty label
+// reads the far sentinel position, clamps to cap and (the label wrapping to
+// -1) encodes as (cap - 1, 2^lb - 1): a quad whose best reaches cap - 1 is
+// recomputed with the exact form, so the result never depends on the cap.
+template <bool COH>
+struct Quad32 {
+  uint32_t b0, b1, b2, b3;
+  int x0, y;
+  uint32_t cap, mul;
+  const int2* __restrict__ ptable;
+  __device__ __forceinline__ Quad32(const PassArgs& a, int x0_, int y_)
+      : x0(x0_), y(y_), cap(a.cap), mul(a.mul), ptable(a.ptable) {}
+  __device__ __forceinline__ uint32_t key(int c, int x) const {
+    const int2 p = COH ? __ldcg(&ptable[c]) : __ldg(&ptable[c]);
+    const int dx = p.x - x, dy = p.y - y;
+    const uint32_t d = static_cast<uint32_t>(dx * dx) + static_cast<uint32_t>(dy * dy);
+    return min(d, cap) * mul + static_cast<uint32_t>(c);
+  }
+  __device__ __forceinline__ void init(const int4& L) {
+    b0 = key(L.x, x0);
+    b1 = key(L.y, x0 + 1);
+    b2 = key(L.z, x0 + 2);
+    b3 = key(L.w, x0 + 3);
+  }
+  __device__ __forceinline__ void fold4(const int4& L) {
+    b0 = min(b0, key(L.x, x0));
+    b1 = min(b1, key(L.y, x0 + 1));
+    b2 = min(b2, key(L.z, x0 + 2));
+    b3 = min(b3, key(L.w, x0 + 3));
   }
 };
 
@@ -171,29 +213,29 @@ __device__ __forceinline__ int4 load_scalar4(const int32_t* __restrict__ row, in
 
 // The side candidates (x -/+ k) of one source row for the four pixels of a
 // thread; `mid` is that row's aligned vector at x0 when already loaded.
-template <int KSEL, int METRIC, bool COH>
-__device__ __forceinline__ void fold_sides(Quad<METRIC, COH>& q, const int32_t* __restrict__ row, const int4& mid,
-                                           const PassArgs& a, const int2* __restrict__ table) {
+template <int KSEL, bool COH, class Q>
+__device__ __forceinline__ void fold_sides(Q& q, const int32_t* __restrict__ row, const int4& mid,
+                                           const PassArgs& a) {
   const int x0 = q.x0;
   if (KSEL == 0) {
     const int4 L = load_side<COH>(row, x0, -a.k, a.pitch);
     const int4 R = load_side<COH>(row, x0, a.k, a.pitch);
-    q.fold4(L, table);
+    q.fold4(L);
     group_fence();
-    q.fold4(R, table);
+    q.fold4(R);
   } else if (KSEL == 1 || KSEL == 2) {
     const int4 neg = make_int4(-1, -1, -1, -1);
     const int4 lv = (x0 >= 4) ? map4<COH>(row + x0 - 4) : neg;
     const int4 rv = (x0 + 4 < a.pitch) ? map4<COH>(row + x0 + 4) : neg;
-    q.fold4(shift_left_by(lv, mid, KSEL), table);
+    q.fold4(shift_left_by(lv, mid, KSEL));
     group_fence();
-    q.fold4(shift_right_by(mid, rv, KSEL), table);
+    q.fold4(shift_right_by(mid, rv, KSEL));
   } else {
     const int4 L = load_scalar4<COH>(row, x0 - a.k, a.w);
     const int4 R = load_scalar4<COH>(row, x0 + a.k, a.w);
-    q.fold4(L, table);
+    q.fold4(L);
     group_fence();
-    q.fold4(R, table);
+    q.fold4(R);
   }
   group_fence();
 }
@@ -201,17 +243,11 @@ __device__ __forceinline__ void fold_sides(Quad<METRIC, COH>& q, const int32_t* 
 // One jump pass (Table I / Section IV-B) for the four horizontally adjacent
 // pixels (x0 .. x0+3, y) of one thread: it starts from their own labels and
 // folds in the neighbour offsets one source row at a time (16-byte label
-// loads, four seed-table gathers and four packed-key minimums per offset).
-// Candidate order does not matter: the packed minimum is a total order.
-template <int NB, int METRIC, int KSEL, bool COH = false>
-__device__ __forceinline__ void pass_quad(const PassArgs& a, int x0, int y) {
+// loads, four seed gathers and four minimums per offset).  Candidate order
+// does not matter: both key forms are total orders.
+template <int NB, int KSEL, bool COH, class Q>
+__device__ __forceinline__ void fold_all(Q& q, const PassArgs& a, int x0, int y) {
   const int64_t pitch = a.pitch;
-  const int2* __restrict__ table = a.table;
-  Quad<METRIC, COH> q;
-  q.m2y = -2 * y;
-  q.m2x = -2 * x0;
-  q.x0 = x0;
-  q.y = y;
   const int32_t* crow = a.src + y * pitch;
   const int4 own = map4<COH>(crow + x0);
   // the first up-row vector is in flight while the own labels are scored
@@ -221,43 +257,77 @@ __device__ __forceinline__ void pass_quad(const PassArgs& a, int x0, int y) {
   const int32_t* drow = a.src + (y + a.k) * pitch;
   const int4 neg = make_int4(-1, -1, -1, -1);
   const int4 um = up_ok ? map4<COH>(urow + x0) : neg;
-  q.init(own, table);
+  q.init(own);
   group_fence();
   // centre row: (-k, 0), (+k, 0)
-  fold_sides<KSEL, METRIC, COH>(q, crow, own, a, table);
-  // up row: (0, -k) and, for Moore, (-k, -k), (+k, -k)
+  fold_sides<KSEL, COH>(q, crow, own, a);
+  // up row: (0, -k) and, for Moore, (-k, -k), (+k, -k); then the down row
   if (up_ok) {
     const int4 dm = dn_ok ? map4<COH>(drow + x0) : neg;
-    q.fold4(um, table);
+    q.fold4(um);
     group_fence();
-    if (NB == kMoore) fold_sides<KSEL, METRIC, COH>(q, urow, um, a, table);
+    if (NB == kMoore) fold_sides<KSEL, COH>(q, urow, um, a);
     if (dn_ok) {
-      q.fold4(dm, table);
+      q.fold4(dm);
       group_fence();
-      if (NB == kMoore) fold_sides<KSEL, METRIC, COH>(q, drow, dm, a, table);
+      if (NB == kMoore) fold_sides<KSEL, COH>(q, drow, dm, a);
     }
   } else if (dn_ok) {
     const int4 dm = map4<COH>(drow + x0);
-    q.fold4(dm, table);
+    q.fold4(dm);
     group_fence();
-    if (NB == kMoore) fold_sides<KSEL, METRIC, COH>(q, drow, dm, a, table);
+    if (NB == kMoore) fold_sides<KSEL, COH>(q, drow, dm, a);
   }
-  int4 out;
-  out.x = (x0 < a.w) ? static_cast<int>(static_cast<unsigned int>(q.b0)) : -1;
-  out.y = (x0 + 1 < a.w) ? static_cast<int>(static_cast<unsigned int>(q.b1)) : -1;
-  out.z = (x0 + 2 < a.w) ? static_cast<int>(static_cast<unsigned int>(q.b2)) : -1;
-  out.w = (x0 + 3 < a.w) ? static_cast<int>(static_cast<unsigned int>(q.b3)) : -1;
-  *reinterpret_cast<int4*>(a.dst + y * pitch + x0) = out;
 }
 
-template <int NB, int METRIC, int KSEL>
-__global__ void __launch_bounds__(256, 6) k_pass(PassArgs a) {
+__device__ __forceinline__ void store_quad(const PassArgs& a, int x0, int y, int l0, int l1, int l2, int l3) {
+  int4 out;
+  out.x = (x0 < a.w) ? l0 : -1;
+  out.y = (x0 + 1 < a.w) ? l1 : -1;
+  out.z = (x0 + 2 < a.w) ? l2 : -1;
+  out.w = (x0 + 3 < a.w) ? l3 : -1;
+  *reinterpret_cast<int4*>(a.dst + static_cast<int64_t>(y) * a.pitch + x0) = out;
+}
+
+// Exact form (any metric).
+template <int NB, int METRIC, int KSEL, bool COH = false>
+__device__ __forceinline__ void pass_quad(const PassArgs& a, int x0, int y) {
+  Quad<METRIC, COH> q(a, x0, y);
+  fold_all<NB, KSEL, COH>(q, a, x0, y);
+  store_quad(a, x0, y, static_cast<int>(static_cast<unsigned int>(q.b0)),
+             static_cast<int>(static_cast<unsigned int>(q.b1)), static_cast<int>(static_cast<unsigned int>(q.b2)),
+             static_cast<int>(static_cast<unsigned int>(q.b3)));
+}
+
+// Clamped form (Euclidean), falling back to the exact form for a quad whose
+// best distance reaches the cap (or that saw only empty labels).
+template <int NB, int KSEL, bool COH = false>
+__device__ __forceinline__ void pass_quad_clamped(const PassArgs& a, int x0, int y) {
+  Quad32<COH> q(a, x0, y);
+  fold_all<NB, KSEL, COH>(q, a, x0, y);
+  const uint32_t lim = (a.cap - 1u) * a.mul;
+  if (max(max(q.b0, q.b1), max(q.b2, q.b3)) >= lim) {
+    pass_quad<NB, kEuclid, KSEL, COH>(a, x0, y);
+    return;
+  }
+  const uint32_t mask = a.mul - 1u;
+  store_quad(a, x0, y, static_cast<int>(q.b0 & mask), static_cast<int>(q.b1 & mask), static_cast<int>(q.b2 & mask),
+             static_cast<int>(q.b3 & mask));
+}
+
+#ifndef VD_PASS_MIN_BLOCKS
+#define VD_PASS_MIN_BLOCKS 6
+#endif
+
+template <int NB, int METRIC, int KSEL, bool CLAMP = false>
+__global__ void __launch_bounds__(256, VD_PASS_MIN_BLOCKS) k_pass(PassArgs a) {
   const int x0 = 4 * static_cast<int>(blockIdx.x * blockDim.x + threadIdx.x);
   int rb = blockIdx.y;
   if (a.band_m > 1) rb = (blockIdx.y % a.band_t) * a.band_m + blockIdx.y / a.band_t;
   const int y = rb * static_cast<int>(blockDim.y) + static_cast<int>(threadIdx.y);
   if (x0 >= a.pitch || y >= a.h) return;
-  pass_quad<NB, METRIC, KSEL>(a, x0, y);
+  if (CLAMP && METRIC == kEuclid) pass_quad_clamped<NB, KSEL>(a, x0, y);
+  else pass_quad<NB, METRIC, KSEL>(a, x0, y);
 }
 
 // ---------------------------------------------------------------------------
@@ -379,11 +449,24 @@ __device__ __forceinline__ int rng_disp(uint64_t key, uint64_t step, uint64_t k,
   return static_cast<int>(((draw >> 32) * m) >> 32) - max_disp;
 }
 
-// Rebuilds the pass table (entry k + 1 for seed k; entry 0 the sentinel).
-static __global__ void k_build_table(const int2* __restrict__ seeds, int n, int2* __restrict__ table) {
+// Far sentinel of the position table: from any pixel of a grid up to 32768
+// wide its squared distance lies in [2 * 13573^2, 2 * 46340^2], above every
+// clamp cap used (2^28 - 1 at most) and below 2^32.
+constexpr int kFarSentinel = -13573;
+
+// Rebuilds the pass tables (entry k + 1 for seed k; entry 0 the sentinels).
+static __global__ void k_build_table(const int2* __restrict__ seeds, int n, int2* __restrict__ table,
+                                     int2* __restrict__ ptable) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k == 0) table[0] = make_int2(0, kSentinelNorm);
-  if (k < n) table[k + 1] = table_entry(seeds[k]);
+  if (k == 0) {
+    table[0] = make_int2(0, kSentinelNorm);
+    ptable[0] = make_int2(kFarSentinel, kFarSentinel);
+  }
+  if (k < n) {
+    const int2 p = seeds[k];
+    table[k + 1] = table_entry(p);
+    ptable[k + 1] = p;
+  }
 }
 
 // Flags any label outside [-1, n) (device-side input validation).
@@ -398,9 +481,9 @@ static __global__ void k_check_labels(const int32_t* __restrict__ labels, int64_
 
 // SimulateParticles (Algorithm 1): p_k <- clamp(p_k + delta_k) on the grid;
 // also refreshes the seed's pass-table entry.
-static __global__ void k_move(int2* __restrict__ seeds, int2* __restrict__ table, int n,
-                       const int2* __restrict__ dxy, int w, int h, int max_disp, uint64_t key,
-                       uint64_t step) {
+static __global__ void k_move(int2* __restrict__ seeds, int2* __restrict__ table, int2* __restrict__ ptable,
+                              int n, const int2* __restrict__ dxy, int w, int h, int max_disp, uint64_t key,
+                              uint64_t step) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n) return;
   int2 p = seeds[k];
@@ -420,6 +503,7 @@ static __global__ void k_move(int2* __restrict__ seeds, int2* __restrict__ table
   p.y = static_cast<int>(y);
   seeds[k] = p;
   table[k + 1] = table_entry(p);
+  ptable[k + 1] = p;
 }
 
 // Stamp, first half: every seed pixel is overwritten with one of the indices

@@ -70,7 +70,7 @@ double now_s(const vd_server* s) {
 
 int64_t sim_bytes(int w, int h, int n) {
   const int64_t pitch = (w + 31) / 32 * 32;
-  return 2 * pitch * h * 4 + static_cast<int64_t>(n) * 8 + (static_cast<int64_t>(n) + 1) * 8 + 256;
+  return 2 * pitch * h * 4 + static_cast<int64_t>(n) * 8 + 2 * (static_cast<int64_t>(n) + 1) * 8 + 256;
 }
 
 void server_free(vd_server* s) {
@@ -233,14 +233,17 @@ extern "C" int32_t vd_server_add_sim(vd_server* s, int32_t w, int32_t h, int32_t
   d.map[1] = d.map[0] + map_elems;
   d.seeds = reinterpret_cast<int2*>(d.map[1] + map_elems);
   d.table = d.seeds + n;
+  d.ptable = d.table + (n + 1);
   d.cur = 0;
   d.step = 0;
   d.n_pass[0] = vdi::fill_schedule(vdi::djfa_first_step(w, h, n, s->d_max), s->vn_waves, 0, d.ks[0], d.nbs[0],
                                    vdb::kMaxPasses);
   d.n_pass[1] = vdi::fill_schedule(vdi::jfa_first_step(w, h), 0, 0, d.ks[1], d.nbs[1], vdb::kMaxPasses);
+  vdb::set_clamp(d, 0, s->metric, -1);
+  vdb::set_clamp(d, 1, s->metric, -1);
   cudaStream_t st = s->admin;
   int rc = vd_cuda_check(cudaMemcpyAsync(d.seeds, xy, sizeof(int2) * n, cudaMemcpyHostToDevice, st), "copy seeds");
-  if (!rc) rc = vdi::launch_build_table(d.seeds, n, d.table, st);
+  if (!rc) rc = vdi::launch_build_table(d.seeds, n, d.table, d.ptable, st);
   if (!rc) rc = vdi::launch_fill(d.map[0], 2 * static_cast<int64_t>(map_elems), -1, st);
   if (!rc) rc = vd_cuda_check(cudaMemcpyAsync(s->d_sims + slot, &d, sizeof(d), cudaMemcpyHostToDevice, st), "descriptor");
   // frame 0: a full JFA frame for the new simulation alone

@@ -21,6 +21,7 @@ OPT_USE_GRAPHS = 3
 OPT_FUSE_TILE_X = 4
 OPT_FUSE_TILE_Y = 5
 OPT_PROFILE = 6
+OPT_CLAMPED_KEYS = 7
 
 KERNEL_KINDS = ("pass", "fused", "stamp", "move", "fill")
 
@@ -270,6 +271,7 @@ BOPT_BLOCKS_PER_SM = 3
 BOPT_USE_GRAPHS = 4
 BOPT_BARRIER_TIMEOUT_US = 5
 BOPT_TEST_SKIP_ARRIVE = 6
+BOPT_CLAMPED_KEYS = 7
 
 
 class VoronoiBatch:

@@ -176,3 +176,20 @@ def test_batch_rejects_bad_input(vd):
     with pytest.raises(VDError):
         b.step_subset([2], max_disp=1)
     b.close()
+
+
+@pytest.mark.parametrize("clamp", [0, 1])
+def test_batch_clamped_and_exact_keys(vd, clamp):
+    D, steps, rng = 2, 2, 11
+    xys = _seeds(SHAPES, 70)
+    b = vd.VoronoiBatch(SHAPES)
+    b.set_option(vd.BOPT_CLAMPED_KEYS, clamp)
+    b.set_seeds(np.concatenate(xys))
+    b.jfa()
+    b.configure(d_max=D)
+    for _ in range(steps):
+        b.step(None, max_disp=D, rng_seed=rng)
+    for i, shape in enumerate(SHAPES):
+        want_l, _ = _alone_rng(vd, shape, xys[i], i, steps, D, rng)
+        np.testing.assert_array_equal(b.labels(i), want_l, err_msg=f"sim {i}")
+    b.close()

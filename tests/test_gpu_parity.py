@@ -275,3 +275,31 @@ def test_invalid_arguments(vd):
     with pytest.raises(VDError):
         sim.set_seeds(bad)
     sim.close()
+
+
+@pytest.mark.parametrize("clamp", [0, 1])
+@pytest.mark.parametrize("w,h,s", [(37, 29, 12), (300, 200, 500), (257, 129, 9), (640, 480, 5000), (64, 64, 8)])
+def test_clamped_and_exact_keys(vd, orc, clamp, w, h, s):
+    """Both key forms (forced) give the oracle's maps: single passes over random
+    maps with empty labels and ragged edges, JFA frames and dJFA steps."""
+    g = np.random.default_rng(s)
+    xy = inputs.uniform_seeds(w, h, s, seed=s + 1)
+    xy[-1] = xy[0]
+    sim = _sim(vd, w, h, xy, clamped_keys=clamp)
+    src = g.integers(-1, s, size=(h, w), dtype=np.int32)
+    for k in [1, 2, 4, 16, 128]:
+        for nb in [M, VN]:
+            sim.set_labels(src)
+            sim.jump_pass(k, nb)
+            np.testing.assert_array_equal(sim.labels(), orc.jump_pass(w, h, xy, src, k, nb), err_msg=f"k={k}")
+    sim.jfa()
+    lab = orc.jfa(w, h, xy)
+    np.testing.assert_array_equal(sim.labels(), lab)
+    disp = inputs.displacements(s, 3, 3, seed=s)
+    for t in range(3):
+        sim.move(disp[t])
+        xy = orc.move(w, h, xy, disp[t])
+        sim.djfa_step(d_max=3)
+        lab = orc.djfa_step(w, h, xy, lab, d_max=3)
+        np.testing.assert_array_equal(sim.labels(), lab, err_msg=f"step {t}")
+    sim.close()
