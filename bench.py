@@ -57,6 +57,9 @@ def parse_args():
                     help="bounded CPU-oracle sample for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--metric", choices=["euclid", "manhattan"], default="euclid",
+                    help="dJFA distance: euclid (dJFAe) or manhattan (dJFAm, scored against Euclidean JFA)")
+    ap.add_argument("--extra", type=int, default=0, help="extra dJFA passes after the schedule (0, 1, 2)")
     ap.add_argument("--rates", default="2000,5000,10000,20000",
                     help="serve1000: Poisson request rates (per second)")
     ap.add_argument("--duration", type=float, default=1.0, help="serve1000: seconds of arrivals per rate")
@@ -71,6 +74,7 @@ def dist_env():
 
 
 _SWEEP = {}
+_DJFA_METRIC = {}
 
 
 def workload(name):
@@ -96,6 +100,7 @@ def config_dict(name, w, h, s, d, n_jfa, n_djfa, world, l2):
                     f"[-{d},{d}] per axis, clamped; dJFA (Eq. 4) vs JFA (Eq. 2) per frame",
         "grid": [w, h], "seeds": s, "max_disp": d,
         "passes": {"jfa": n_jfa, "djfa": n_djfa, "djfa_von_neumann": 2},
+        "djfa_metric": _DJFA_METRIC.get("name", "euclid"), "djfa_extra_passes": _DJFA_METRIC.get("extra", 0),
         "l2": l2,
         "parallelism": "replicas" if world > 1 else "single",
     }
@@ -300,8 +305,9 @@ def run_ours(args):
     xy = inputs.uniform_seeds(w, h, s, seed=seed)
     disp_host = inputs.displacements(s, d, total, seed=seed)
     n_jfa = len(vd.jfa_schedule(w, h))
-    n_djfa = len(vd.djfa_schedule(w, h, s, d, vn_waves=2))
+    n_djfa = len(vd.djfa_schedule(w, h, s, d, vn_waves=2, extra=args.extra))
     px = w * h
+    metric = vd.MANHATTAN if args.metric == "manhattan" else vd.EUCLID
 
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
@@ -314,11 +320,11 @@ def run_ours(args):
     for sim in (dj, jf):
         sim.set_seeds(xy)
         sim.set_option(vd.OPT_USE_GRAPHS, 1)
-    dj.jfa()  # frame 0 of the dJFA chain
+    dj.jfa(metric=metric)  # frame 0 of the dJFA chain
 
     def djfa_step(i):
         dj.move(disp_dev[i])
-        dj.djfa_step(d_max=d, vn_waves=2)
+        dj.djfa_step(d_max=d, vn_waves=2, extra=args.extra, metric=metric)
 
     def jfa_step(i):
         jf.move(disp_dev[i])
@@ -347,10 +353,13 @@ def run_ours(args):
         jfa_step(i)
         ev[j][3].record(stream)
         if (j + 1) % 10 == 0 or j == K - 1:
-            # scored between steps, outside the step events
-            dj.exact(None, exact_dist)
-            ne_d, nm = dj.similarity(exact_dist=exact_dist, ref_labels=None)
+            # scored between steps, outside the step events; the dJFA map against
+            # the exact diagram in its own metric, the JFA map in Euclidean
+            dj.exact(None, exact_dist, metric=metric)
+            ne_d, _ = dj.similarity(exact_dist=exact_dist, metric=metric)
             nm = dj.match_count(jf)
+            if metric != vd.EUCLID:
+                dj.exact(None, exact_dist, metric=vd.EUCLID)
             ne_j, _ = jf.similarity(exact_dist=exact_dist)
             sims.append((j + 1, nm, ne_d, ne_j))
     barrier()
@@ -370,16 +379,16 @@ def run_ours(args):
     #     events around every launch (eager launches, L2 flushed between steps)
     pr = vd.VoronoiSim(w, h, s, stream=stream)
     pr.set_seeds(xy)
-    pr.jfa()
+    pr.jfa(metric=metric)
     for i in range(W):
         pr.move(disp_dev[i])
-        pr.djfa_step(d_max=d, vn_waves=2)
+        pr.djfa_step(d_max=d, vn_waves=2, extra=args.extra, metric=metric)
     pr.set_option(vd.OPT_PROFILE, 1)
     pr.profile_reset()
     for j in range(K):
         flush.zero_()
         pr.move(disp_dev[W + j])
-        pr.djfa_step(d_max=d, vn_waves=2)
+        pr.djfa_step(d_max=d, vn_waves=2, extra=args.extra, metric=metric)
     prof = pr.profile()
     pr.close()
     dom = max(prof, key=lambda k: prof[k]["ms"])
@@ -409,12 +418,12 @@ def run_ours(args):
         ee = vd.VoronoiSim(w, h, s, stream=stream)
         ee.set_seeds(xy)
         ee.set_option(vd.OPT_USE_GRAPHS, 1)
-        ee.jfa()
+        ee.jfa(metric=metric)
         pin_disp = torch.from_numpy(disp_host).pin_memory()
         pin_out = torch.empty((h, w), dtype=torch.int32).pin_memory()
         for i in range(W):
             ee.move(pin_disp[i])
-            ee.djfa_step(d_max=d, vn_waves=2)
+            ee.djfa_step(d_max=d, vn_waves=2, extra=args.extra, metric=metric)
             ee.labels(out=pin_out)
         barrier()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -422,7 +431,7 @@ def run_ours(args):
         e0.record(stream)
         for j in range(K):
             ee.move(pin_disp[W + j])
-            ee.djfa_step(d_max=d, vn_waves=2)
+            ee.djfa_step(d_max=d, vn_waves=2, extra=args.extra, metric=metric)
             ee.labels(out=pin_out)
         e1.record(stream)
         barrier()
@@ -631,6 +640,10 @@ def main():
         return run_serve(args)
     _SWEEP["seeds"] = args.seeds
     _SWEEP["max_disp"] = args.max_disp
+    _DJFA_METRIC["name"] = args.metric
+    _DJFA_METRIC["extra"] = args.extra
+    if args.extra not in (0, 1, 2):
+        raise SystemExit("--extra takes 0, 1 or 2")
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

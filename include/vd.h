@@ -424,10 +424,12 @@ int vd_server_set_max_batch(vd_server* server, int32_t max_batch);
 #define VD_OPT_FUSE_TILE_Y 5     /* fused-group tile height in pixels (1..128) */
 #define VD_OPT_PROFILE 6         /* 1 = bracket every kernel launch with CUDA events (frames then run
                                     eagerly, never from a graph); read with vd_profile_read */
-#define VD_OPT_CLAMPED_KEYS 7    /* Euclidean passes with one 32-bit key per candidate (min(d^2, cap) *
-                                    2^lb + label, exact: quads that reach the cap are recomputed with
-                                    the 64-bit key): -1 = auto (default: dJFA passes), 0 = never,
-                                    1 = always when usable (>= 9 seeds) */
+#define VD_OPT_CLAMPED_KEYS 7    /* passes with one 32-bit key per candidate, both exact:
+                                    Euclidean min(d^2, cap) * 2^lb + label (quads that reach the cap
+                                    are recomputed with the 64-bit key; usable with >= 9 seeds),
+                                    Manhattan d * 2^lb + label (no cap; usable with <= 32768 seeds).
+                                    -1 = auto (default: Euclidean dJFA passes, every Manhattan pass),
+                                    0 = never, 1 = always when usable */
 int vd_set_option(vd_ctx* ctx, int32_t option, int64_t value);
 int vd_get_option(const vd_ctx* ctx, int32_t option, int64_t* value);
 

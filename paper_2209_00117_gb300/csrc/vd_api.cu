@@ -159,12 +159,18 @@ int label_bits(int32_t n) {
 
 bool use_clamp(int clamp_option, int32_t metric, int32_t n, int32_t k, bool djfa_frame) {
   (void)k;
-  if (clamp_option == 0 || metric != VD_METRIC_EUCLID) return false;
-  if (label_bits(n) < 4) return false;
+  if (clamp_option == 0) return false;
+  const int lb = label_bits(n);
+  if (metric == VD_METRIC_MANHATTAN) {
+    // exact without a cap while d * 2^lb + label fits: every pass may use it
+    return lb <= 15;
+  }
+  if (lb < 4) return false;
   if (clamp_option == 1) return true;
-  // auto: dJFA passes only.  The previous map is nearly right there, so quads
-  // almost never reach the cap; in a JFA frame the early passes still see many
-  // empty pixels, whose quads would be recomputed with the exact form.
+  // Euclidean auto: dJFA passes only.  The previous map is nearly right
+  // there, so quads almost never reach the cap; in a JFA frame the early
+  // passes still see many empty pixels, whose quads would be recomputed with
+  // the exact form.
   return djfa_frame;
 }
 
@@ -206,20 +212,23 @@ int launch_pass(const MapView& m, const int32_t* src, int32_t* dst, int32_t k, i
     grid.y = a.band_m * a.band_t;
   }
   const int ksel = (k % 4 == 0) ? 0 : (k == 1 ? 1 : (k == 2 ? 2 : 3));
-  if (clamp && (metric != VD_METRIC_EUCLID || a.cap == 0)) clamp = false;
+  if (clamp && metric == VD_METRIC_EUCLID && a.cap == 0) clamp = false;
+  if (clamp && metric == VD_METRIC_MANHATTAN && label_bits(m.n) > 15) clamp = false;
   if (nb == VD_NB_MOORE) {
     if (metric == VD_METRIC_EUCLID) {
       if (clamp) launch_pass_t<vdk::kMoore, vdk::kEuclid, true>(ksel, grid, block, st, a);
       else launch_pass_t<vdk::kMoore, vdk::kEuclid, false>(ksel, grid, block, st, a);
     } else {
-      launch_pass_t<vdk::kMoore, vdk::kManhattan, false>(ksel, grid, block, st, a);
+      if (clamp) launch_pass_t<vdk::kMoore, vdk::kManhattan, true>(ksel, grid, block, st, a);
+      else launch_pass_t<vdk::kMoore, vdk::kManhattan, false>(ksel, grid, block, st, a);
     }
   } else {
     if (metric == VD_METRIC_EUCLID) {
       if (clamp) launch_pass_t<vdk::kVonNeumann, vdk::kEuclid, true>(ksel, grid, block, st, a);
       else launch_pass_t<vdk::kVonNeumann, vdk::kEuclid, false>(ksel, grid, block, st, a);
     } else {
-      launch_pass_t<vdk::kVonNeumann, vdk::kManhattan, false>(ksel, grid, block, st, a);
+      if (clamp) launch_pass_t<vdk::kVonNeumann, vdk::kManhattan, true>(ksel, grid, block, st, a);
+      else launch_pass_t<vdk::kVonNeumann, vdk::kManhattan, false>(ksel, grid, block, st, a);
     }
   }
   return vd_cuda_check(cudaGetLastError(), "jump pass launch");

@@ -193,19 +193,19 @@ __device__ __forceinline__ void round_tile(const BatchArgs& A, int r, int t) {
   a.band_t = 1;
   const int x0 = 4 * (tx * kQuadsX + static_cast<int>(threadIdx.x % kQuadsX));
   const int ksel = (k == 1) ? 1 : (k == 2 ? 2 : 0);
-  const bool clamp = METRIC == vdk::kEuclid && ((sd->clampmask[A.sched] >> r) & 1u);
+  const bool clamp = (sd->clampmask[A.sched] >> r) & 1u;
   const int rows = 4 * A.rows_per_thread;
   for (int i = 0; i < A.rows_per_thread; ++i) {
     const int y = ty * rows + static_cast<int>(threadIdx.x / kQuadsX) + 4 * i;
     if (x0 >= a.pitch || y >= a.h) continue;
     if (clamp) {
       switch (nb * 4 + ksel) {
-        case 0: vdk::pass_quad_clamped<vdk::kMoore, 0, COH>(a, x0, y); break;
-        case 1: vdk::pass_quad_clamped<vdk::kMoore, 1, COH>(a, x0, y); break;
-        case 2: vdk::pass_quad_clamped<vdk::kMoore, 2, COH>(a, x0, y); break;
-        case 4: vdk::pass_quad_clamped<vdk::kVonNeumann, 0, COH>(a, x0, y); break;
-        case 5: vdk::pass_quad_clamped<vdk::kVonNeumann, 1, COH>(a, x0, y); break;
-        default: vdk::pass_quad_clamped<vdk::kVonNeumann, 2, COH>(a, x0, y); break;
+        case 0: vdk::pass_quad_clamped<vdk::kMoore, 0, COH, METRIC>(a, x0, y); break;
+        case 1: vdk::pass_quad_clamped<vdk::kMoore, 1, COH, METRIC>(a, x0, y); break;
+        case 2: vdk::pass_quad_clamped<vdk::kMoore, 2, COH, METRIC>(a, x0, y); break;
+        case 4: vdk::pass_quad_clamped<vdk::kVonNeumann, 0, COH, METRIC>(a, x0, y); break;
+        case 5: vdk::pass_quad_clamped<vdk::kVonNeumann, 1, COH, METRIC>(a, x0, y); break;
+        default: vdk::pass_quad_clamped<vdk::kVonNeumann, 2, COH, METRIC>(a, x0, y); break;
       }
       continue;
     }

@@ -136,7 +136,7 @@ __device__ __forceinline__ int4 shift_right_by(const int4& m, const int4& r, int
 }
 
 // The four pixels (x0 .. x0+3, y) owned by one thread and their packed
-// best (key, label) so far: the exact 64-bit form.
+// best (key, label) so far: the exact 64-bit form (any metric).
 template <int METRIC, bool COH>
 struct Quad {
   long long b0, b1, b2, b3;
@@ -166,6 +166,41 @@ struct Quad {
 // reads the far sentinel position, clamps to cap and (the label wrapping to
 // -1) encodes as (cap - 1, 2^lb - 1): a quad whose best reaches cap - 1 is
 // recomputed with the exact form, so the result never depends on the cap.
+// Manhattan 32-bit form: distances are at most 2 * 32767 < 2^17, so with
+// every label below 2^lb, lb <= 15, key = d * 2^lb + label is exact without a
+// cap.  An empty label takes distance 2^17 - 1, above every real one (it
+// wraps to (2^17 - 2, 2^lb - 1)), and a pixel whose best is such a key has
+// no candidate at all.
+constexpr uint32_t kManhattanEmpty = (1u << 17) - 1u;
+constexpr uint32_t kManhattanMax = 2u * 32767u;
+
+template <bool COH>
+struct Quad32M {
+  uint32_t b0, b1, b2, b3;
+  int x0, y;
+  uint32_t mul;
+  const int2* __restrict__ ptable;
+  __device__ __forceinline__ Quad32M(const PassArgs& a, int x0_, int y_)
+      : x0(x0_), y(y_), mul(a.mul), ptable(a.ptable) {}
+  __device__ __forceinline__ uint32_t key(int c, int x) const {
+    const int2 p = COH ? __ldcg(&ptable[c]) : __ldg(&ptable[c]);
+    const uint32_t d = c < 0 ? kManhattanEmpty : static_cast<uint32_t>(abs(p.x - x) + abs(p.y - y));
+    return d * mul + static_cast<uint32_t>(c);
+  }
+  __device__ __forceinline__ void init(const int4& L) {
+    b0 = key(L.x, x0);
+    b1 = key(L.y, x0 + 1);
+    b2 = key(L.z, x0 + 2);
+    b3 = key(L.w, x0 + 3);
+  }
+  __device__ __forceinline__ void fold4(const int4& L) {
+    b0 = min(b0, key(L.x, x0));
+    b1 = min(b1, key(L.y, x0 + 1));
+    b2 = min(b2, key(L.z, x0 + 2));
+    b3 = min(b3, key(L.w, x0 + 3));
+  }
+};
+
 template <bool COH>
 struct Quad32 {
   uint32_t b0, b1, b2, b3;
@@ -299,10 +334,21 @@ __device__ __forceinline__ void pass_quad(const PassArgs& a, int x0, int y) {
              static_cast<int>(static_cast<unsigned int>(q.b3)));
 }
 
-// Clamped form (Euclidean), falling back to the exact form for a quad whose
-// best distance reaches the cap (or that saw only empty labels).
-template <int NB, int KSEL, bool COH = false>
+// 32-bit forms.  Euclidean: clamped, falling back to the exact form for a
+// quad whose best distance reaches the cap (or that saw only empty labels).
+// Manhattan: exact as is (lb <= 15); an all-empty pixel stays -1.
+template <int NB, int KSEL, bool COH = false, int METRIC = kEuclid>
 __device__ __forceinline__ void pass_quad_clamped(const PassArgs& a, int x0, int y) {
+  const uint32_t mask = a.mul - 1u;
+  if (METRIC == kManhattan) {
+    Quad32M<COH> q(a, x0, y);
+    fold_all<NB, KSEL, COH>(q, a, x0, y);
+    const uint32_t lim = (kManhattanMax + 1u) * a.mul;
+    store_quad(a, x0, y, q.b0 >= lim ? -1 : static_cast<int>(q.b0 & mask),
+               q.b1 >= lim ? -1 : static_cast<int>(q.b1 & mask), q.b2 >= lim ? -1 : static_cast<int>(q.b2 & mask),
+               q.b3 >= lim ? -1 : static_cast<int>(q.b3 & mask));
+    return;
+  }
   Quad32<COH> q(a, x0, y);
   fold_all<NB, KSEL, COH>(q, a, x0, y);
   const uint32_t lim = (a.cap - 1u) * a.mul;
@@ -310,7 +356,6 @@ __device__ __forceinline__ void pass_quad_clamped(const PassArgs& a, int x0, int
     pass_quad<NB, kEuclid, KSEL, COH>(a, x0, y);
     return;
   }
-  const uint32_t mask = a.mul - 1u;
   store_quad(a, x0, y, static_cast<int>(q.b0 & mask), static_cast<int>(q.b1 & mask), static_cast<int>(q.b2 & mask),
              static_cast<int>(q.b3 & mask));
 }
@@ -326,7 +371,7 @@ __global__ void __launch_bounds__(256, VD_PASS_MIN_BLOCKS) k_pass(PassArgs a) {
   if (a.band_m > 1) rb = (blockIdx.y % a.band_t) * a.band_m + blockIdx.y / a.band_t;
   const int y = rb * static_cast<int>(blockDim.y) + static_cast<int>(threadIdx.y);
   if (x0 >= a.pitch || y >= a.h) return;
-  if (CLAMP && METRIC == kEuclid) pass_quad_clamped<NB, KSEL>(a, x0, y);
+  if (CLAMP) pass_quad_clamped<NB, KSEL, false, METRIC>(a, x0, y);
   else pass_quad<NB, METRIC, KSEL>(a, x0, y);
 }
 

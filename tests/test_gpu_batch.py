@@ -178,18 +178,19 @@ def test_batch_rejects_bad_input(vd):
     b.close()
 
 
+@pytest.mark.parametrize("metric", [0, 1])
 @pytest.mark.parametrize("clamp", [0, 1])
-def test_batch_clamped_and_exact_keys(vd, clamp):
+def test_batch_clamped_and_exact_keys(vd, clamp, metric):
     D, steps, rng = 2, 2, 11
     xys = _seeds(SHAPES, 70)
     b = vd.VoronoiBatch(SHAPES)
     b.set_option(vd.BOPT_CLAMPED_KEYS, clamp)
     b.set_seeds(np.concatenate(xys))
-    b.jfa()
-    b.configure(d_max=D)
+    b.jfa(metric=metric)
+    b.configure(d_max=D, metric=metric)
     for _ in range(steps):
         b.step(None, max_disp=D, rng_seed=rng)
     for i, shape in enumerate(SHAPES):
-        want_l, _ = _alone_rng(vd, shape, xys[i], i, steps, D, rng)
+        want_l, _ = _alone_rng(vd, shape, xys[i], i, steps, D, rng, metric=metric)
         np.testing.assert_array_equal(b.labels(i), want_l, err_msg=f"sim {i}")
     b.close()

@@ -277,9 +277,11 @@ def test_invalid_arguments(vd):
     sim.close()
 
 
+@pytest.mark.parametrize("metric", [E, L1])
 @pytest.mark.parametrize("clamp", [0, 1])
-@pytest.mark.parametrize("w,h,s", [(37, 29, 12), (300, 200, 500), (257, 129, 9), (640, 480, 5000), (64, 64, 8)])
-def test_clamped_and_exact_keys(vd, orc, clamp, w, h, s):
+@pytest.mark.parametrize("w,h,s", [(37, 29, 12), (300, 200, 500), (257, 129, 9), (640, 480, 5000), (64, 64, 8),
+                                   (512, 256, 40000)])
+def test_clamped_and_exact_keys(vd, orc, clamp, metric, w, h, s):
     """Both key forms (forced) give the oracle's maps: single passes over random
     maps with empty labels and ragged edges, JFA frames and dJFA steps."""
     g = np.random.default_rng(s)
@@ -290,16 +292,42 @@ def test_clamped_and_exact_keys(vd, orc, clamp, w, h, s):
     for k in [1, 2, 4, 16, 128]:
         for nb in [M, VN]:
             sim.set_labels(src)
-            sim.jump_pass(k, nb)
-            np.testing.assert_array_equal(sim.labels(), orc.jump_pass(w, h, xy, src, k, nb), err_msg=f"k={k}")
-    sim.jfa()
-    lab = orc.jfa(w, h, xy)
+            sim.jump_pass(k, nb, metric)
+            np.testing.assert_array_equal(sim.labels(), orc.jump_pass(w, h, xy, src, k, nb, metric),
+                                          err_msg=f"k={k}")
+    sim.jfa(metric=metric)
+    lab = orc.jfa(w, h, xy, metric=metric)
     np.testing.assert_array_equal(sim.labels(), lab)
     disp = inputs.displacements(s, 3, 3, seed=s)
     for t in range(3):
         sim.move(disp[t])
         xy = orc.move(w, h, xy, disp[t])
-        sim.djfa_step(d_max=3)
-        lab = orc.djfa_step(w, h, xy, lab, d_max=3)
+        sim.djfa_step(d_max=3, metric=metric)
+        lab = orc.djfa_step(w, h, xy, lab, d_max=3, metric=metric)
         np.testing.assert_array_equal(sim.labels(), lab, err_msg=f"step {t}")
     sim.close()
+
+
+def test_checkpoint_resume_is_bit_identical(vd):
+    """State = (seeds, label map, RNG step): saving it mid-run and resuming in a
+    fresh context continues the trajectory exactly (counter-based moves)."""
+    w, h, s, D, rng = 700, 500, 3000, 3, 77
+    xy = inputs.uniform_seeds(w, h, s, seed=8)
+    a = _sim(vd, w, h, xy)
+    a.jfa()
+    for t in range(5):
+        a.move(None, max_disp=D, rng_seed=rng, stream_id=0, step=t)
+        a.djfa_step(d_max=D)
+    seeds, labels = a.get_seeds(), a.labels()
+    for t in range(5, 10):
+        a.move(None, max_disp=D, rng_seed=rng, stream_id=0, step=t)
+        a.djfa_step(d_max=D)
+    b = _sim(vd, w, h, seeds)
+    b.set_labels(labels)
+    for t in range(5, 10):
+        b.move(None, max_disp=D, rng_seed=rng, stream_id=0, step=t)
+        b.djfa_step(d_max=D)
+    np.testing.assert_array_equal(a.get_seeds(), b.get_seeds())
+    np.testing.assert_array_equal(a.labels(), b.labels())
+    a.close()
+    b.close()
