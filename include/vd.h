@@ -189,6 +189,20 @@ int vd_set_labels(vd_ctx* ctx, const int32_t* labels, int on_device);
 int vd_get_labels(vd_ctx* ctx, int32_t* labels, int on_device);
 
 /*
+ * Asynchronous read-back of the current label map into a dense w x h HOST
+ * buffer, for pipelines that overlap the copy with the next frames: the map
+ * is snapshotted on the context's stream (so later frames may rewrite it) and
+ * copied out on a copy stream of the context.  Returns at once; the copy is
+ * complete when vd_wait_labels returns.  Two copies may be outstanding; a
+ * third call first waits for the oldest.  `labels` should be page-locked for
+ * the copy to overlap, and must stay valid until the wait.  Allocates two
+ * snapshot maps on first use.
+ */
+int vd_get_labels_async(vd_ctx* ctx, int32_t* labels);
+/* Waits until every vd_get_labels_async copy of the context has landed. */
+int vd_wait_labels(vd_ctx* ctx);
+
+/*
  * Borrowed device pointer to the current label map (row pitch in elements
  * via vd_get_shape); valid until the next call on the context.
  */

@@ -455,6 +455,13 @@ struct vd_ctx {
   int* bk_start = nullptr;
   int* bk_ids = nullptr;
   int64_t bk_cells = 0;
+  // asynchronous label read-back: two snapshot slots copied out on copy_stream
+  int32_t* snap[2] = {nullptr, nullptr};
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t snap_ready[2] = {nullptr, nullptr};
+  cudaEvent_t copy_done[2] = {nullptr, nullptr};
+  bool copy_pending[2] = {false, false};
+  int snap_next = 0;
   vdi::Tuning tune;
   vdi::Profiler prof;
   int64_t launches = 0;
@@ -486,6 +493,13 @@ static int ctx_alloc(void** p, size_t bytes, const char* what) {
 }
 
 static void ctx_free(vd_ctx* c) {
+  if (c->copy_stream) cudaStreamSynchronize(c->copy_stream);
+  for (int i = 0; i < 2; ++i) {
+    cudaFree(c->snap[i]);
+    if (c->snap_ready[i]) cudaEventDestroy(c->snap_ready[i]);
+    if (c->copy_done[i]) cudaEventDestroy(c->copy_done[i]);
+  }
+  if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
   c->prof.destroy();
   for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
   c->graphs.clear();
@@ -1129,4 +1143,61 @@ extern "C" int vd_exact_noalloc(const int32_t* seeds_xy, int32_t n_seeds, int32_
   else
     vdk::k_exact<vdk::kManhattan><<<grid, block, 0, st>>>(b, seeds, w, h, labels, dist);
   return vd_cuda_check(cudaGetLastError(), "exact launch");
+}
+
+// ---------------------------------------------------------------------------
+// Asynchronous label read-back
+// ---------------------------------------------------------------------------
+
+static int ensure_async(vd_ctx* c) {
+  if (c->copy_stream) return VD_OK;
+  const size_t bytes = sizeof(int32_t) * static_cast<size_t>(c->pitch) * c->h;
+  int rc = VD_OK;
+  for (int i = 0; i < 2 && !rc; ++i) rc = ctx_alloc(reinterpret_cast<void**>(&c->snap[i]), bytes, "label snapshot");
+  for (int i = 0; i < 2 && !rc; ++i) {
+    rc = vd_cuda_check(cudaEventCreateWithFlags(&c->snap_ready[i], cudaEventDisableTiming), "event");
+    if (!rc) rc = vd_cuda_check(cudaEventCreateWithFlags(&c->copy_done[i], cudaEventDisableTiming), "event");
+  }
+  if (!rc) rc = vd_cuda_check(cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking), "copy stream");
+  return rc;
+}
+
+extern "C" int vd_get_labels_async(vd_ctx* c, int32_t* labels) {
+  VD_CHECK_CTX(c);
+  if (!labels) return vd_fail(VD_EINVAL, "null output");
+  int rc = ensure_async(c);
+  if (rc) return rc;
+  const int i = c->snap_next;
+  c->snap_next ^= 1;
+  if (c->copy_pending[i]) {
+    // the slot's previous copy must have left the snapshot before it is reused
+    rc = vd_cuda_check(cudaEventSynchronize(c->copy_done[i]), "wait for read-back");
+    if (rc) return rc;
+    c->copy_pending[i] = false;
+  }
+  const size_t bytes = sizeof(int32_t) * static_cast<size_t>(c->pitch) * c->h;
+  // snapshot the current map on the compute stream (later frames rewrite it)
+  rc = vd_cuda_check(cudaMemcpyAsync(c->snap[i], c->buf[c->cur], bytes, cudaMemcpyDeviceToDevice, c->stream),
+                     "snapshot labels");
+  if (!rc) rc = vd_cuda_check(cudaEventRecord(c->snap_ready[i], c->stream), "event");
+  if (!rc) rc = vd_cuda_check(cudaStreamWaitEvent(c->copy_stream, c->snap_ready[i], 0), "wait event");
+  if (!rc)
+    rc = vd_cuda_check(cudaMemcpy2DAsync(labels, sizeof(int32_t) * c->w, c->snap[i], sizeof(int32_t) * c->pitch,
+                                         sizeof(int32_t) * c->w, c->h, cudaMemcpyDeviceToHost, c->copy_stream),
+                       "copy labels out");
+  if (!rc) rc = vd_cuda_check(cudaEventRecord(c->copy_done[i], c->copy_stream), "event");
+  if (rc) return rc;
+  c->copy_pending[i] = true;
+  return VD_OK;
+}
+
+extern "C" int vd_wait_labels(vd_ctx* c) {
+  VD_CHECK_CTX(c);
+  for (int i = 0; i < 2; ++i) {
+    if (!c->copy_pending[i]) continue;
+    const int rc = vd_cuda_check(cudaEventSynchronize(c->copy_done[i]), "wait for read-back");
+    if (rc) return rc;
+    c->copy_pending[i] = false;
+  }
+  return VD_OK;
 }

@@ -226,6 +226,18 @@ class VoronoiSim:
         N.check(self._lib.vd_get_labels(self._h, ptr, dev))
         return out
 
+    def labels_async(self, out):
+        """Queues a copy of the current map into host array/tensor ``out``
+        (page-locked for overlap); complete after :meth:`wait_labels`."""
+        ptr, dev = _buf(out, self.w * self.h, writable=True)
+        if dev:
+            raise ValueError("labels_async copies to host memory")
+        N.check(self._lib.vd_get_labels_async(self._h, ptr))
+        return out
+
+    def wait_labels(self):
+        N.check(self._lib.vd_wait_labels(self._h))
+
     def labels_device_ptr(self) -> int:
         p = ctypes.c_void_p()
         N.check(self._lib.vd_labels_device_ptr(self._h, ctypes.byref(p)))

@@ -331,3 +331,30 @@ def test_checkpoint_resume_is_bit_identical(vd):
     np.testing.assert_array_equal(a.labels(), b.labels())
     a.close()
     b.close()
+
+
+def test_async_label_readback(vd):
+    """Pipelined read-back: every frame's map lands in its own host buffer while
+    later frames run, equal to the synchronous read of that frame."""
+    import torch
+
+    w, h, s, D = 600, 400, 2500, 2
+    xy = inputs.uniform_seeds(w, h, s, seed=12)
+    disp = inputs.displacements(s, D, 6, seed=12)
+    a = _sim(vd, w, h, xy)
+    b = _sim(vd, w, h, xy)
+    a.jfa()
+    b.jfa()
+    outs = [torch.empty((h, w), dtype=torch.int32).pin_memory() for _ in range(6)]
+    want = []
+    for t in range(6):
+        for sim in (a, b):
+            sim.move(disp[t])
+            sim.djfa_step(d_max=D)
+        a.labels_async(outs[t])  # up to two in flight; the third call waits for the oldest
+        want.append(b.labels())
+    a.wait_labels()
+    for t in range(6):
+        np.testing.assert_array_equal(outs[t].numpy(), want[t], err_msg=f"frame {t}")
+    a.close()
+    b.close()
