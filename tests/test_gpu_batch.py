@@ -194,3 +194,29 @@ def test_batch_clamped_and_exact_keys(vd, clamp, metric):
         want_l, _ = _alone_rng(vd, shape, xys[i], i, steps, D, rng, metric=metric)
         np.testing.assert_array_equal(b.labels(i), want_l, err_msg=f"sim {i}")
     b.close()
+
+
+def test_batched256_full_size_sample(vd):
+    """The 256-simulation workload at full size in the benchmarked launch shape
+    (per-round launches, graph replay, 4 rows per thread): after a few steps, a
+    sample of simulations equals the same simulations run alone."""
+    import torch
+
+    D, steps, rng = 2, 3, 0
+    pop = inputs.batched_population(256, seed=0)
+    shapes = [(p.w, p.h, p.s) for p in pop]
+    xys = [inputs.uniform_seeds(w, h, s, seed=i) for i, (w, h, s) in enumerate(shapes)]
+    stream = torch.cuda.Stream()
+    b = vd.VoronoiBatch(shapes, stream=stream)
+    b.set_option(vd.BOPT_ROWS_PER_THREAD, 4)
+    b.set_seeds(np.concatenate(xys))
+    b.jfa()
+    b.configure(d_max=D)
+    for _ in range(steps):
+        b.step(None, max_disp=D, rng_seed=rng)
+    b.synchronize()
+    sample = sorted(set(np.random.default_rng(1).choice(len(shapes), 8, replace=False).tolist()) | {0, 255})
+    for i in sample:
+        want, _ = _alone_rng(vd, shapes[i], xys[i], i, steps, D, rng)
+        np.testing.assert_array_equal(b.labels(i), want, err_msg=f"sim {i} {shapes[i]}")
+    b.close()

@@ -358,3 +358,24 @@ def test_async_label_readback(vd):
         np.testing.assert_array_equal(outs[t].numpy(), want[t], err_msg=f"frame {t}")
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("w,h", [(32768, 8), (8, 32768), (32768, 3)])
+def test_maximum_side_grids(vd, orc, w, h):
+    """Grids at the maximum side (coordinates up to 32767, squared distances up
+    to 2^30, steps up to 16384): JFA and a dJFA step in both key forms and both
+    metrics equal the oracle."""
+    s = 300
+    xy = inputs.uniform_seeds(w, h, s, seed=w + h)
+    disp = inputs.displacements(s, 5, 1, seed=1)[0]
+    for metric in [E, L1]:
+        for clamp in [0, 1]:
+            sim = _sim(vd, w, h, xy, clamped_keys=clamp)
+            sim.jfa(metric=metric)
+            lab = orc.jfa(w, h, xy, metric=metric)
+            np.testing.assert_array_equal(sim.labels(), lab)
+            sim.move(disp)
+            xy2 = orc.move(w, h, xy, disp)
+            sim.djfa_step(d_max=5, metric=metric)
+            np.testing.assert_array_equal(sim.labels(), orc.djfa_step(w, h, xy2, lab, d_max=5, metric=metric))
+            sim.close()

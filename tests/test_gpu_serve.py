@@ -95,3 +95,34 @@ def test_admission_by_budget(vd):
     srv.submit(c)
     srv.drain()
     srv.close()
+
+
+def test_serve1000_full_size_sample(vd):
+    """The 1000-simulation serving workload at full size under an 80 GB budget:
+    a 3000-request Poisson trace at 5000 req/s, then a sample of simulations
+    equals the same simulations stepped alone the same number of times."""
+    D = 2
+    pop = inputs.batched_population(1000, sides=(512, 1024, 2048, 4096), seed=0)
+    srv = vd.VoronoiServer(max_sims=1000, hbm_budget_bytes=80 * 10**9, d_max=D, max_disp=D, rng_seed=0)
+    xys = {}
+    for i, p in enumerate(pop):
+        xy = inputs.uniform_seeds(p.w, p.h, p.s, seed=i)
+        sid = srv.add_sim(p.w, p.h, xy)
+        xys[sid] = (p, xy)
+    assert srv.stats()["live_sims"] == 1000
+    n = 3000
+    arr = inputs.poisson_arrivals(5000, n, seed=5)
+    tgt = np.asarray(sorted(xys), np.int32)[inputs.request_targets(n, len(xys), seed=5)]
+    lat = srv.run_trace(arr, tgt)
+    assert (lat > 0).all()
+    for sid in sorted(set(tgt[:200].tolist()))[:6]:
+        p, xy = xys[sid]
+        sim = vd.VoronoiSim(p.w, p.h, p.s)
+        sim.set_seeds(xy)
+        sim.jfa()
+        for t in range(int((tgt == sid).sum())):
+            sim.move(None, max_disp=D, rng_seed=0, stream_id=sid, step=t)
+            sim.djfa_step(d_max=D)
+        np.testing.assert_array_equal(srv.labels(sid), sim.labels(), err_msg=f"simulation {sid}")
+        sim.close()
+    srv.close()
