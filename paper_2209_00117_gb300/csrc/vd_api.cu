@@ -349,13 +349,13 @@ int launch_stamp(const MapView& m, int32_t* labels, bool mark, cudaStream_t st, 
   return vd_cuda_check(cudaGetLastError(), "stamp launch");
 }
 
-int launch_move(int2* seeds, int2* table, int2* ptable, int n, const int2* dxy, int w, int h, int max_disp,
+int launch_move(int2* seeds, int2* table, uint32_t* ptable, int n, const int2* dxy, int w, int h, int max_disp,
                 uint64_t key, uint64_t step, cudaStream_t st) {
   vdk::k_move<<<grid1d(n, 256), 256, 0, st>>>(seeds, table, ptable, n, dxy, w, h, max_disp, key, step);
   return vd_cuda_check(cudaGetLastError(), "move launch");
 }
 
-int launch_build_table(const int2* seeds, int n, int2* table, int2* ptable, cudaStream_t st) {
+int launch_build_table(const int2* seeds, int n, int2* table, uint32_t* ptable, cudaStream_t st) {
   vdk::k_build_table<<<grid1d(n, 256), 256, 0, st>>>(seeds, n, table, ptable);
   return vd_cuda_check(cudaGetLastError(), "table launch");
 }
@@ -444,7 +444,7 @@ struct vd_ctx {
   int cur = 0;
   int2* seeds = nullptr;
   int2* table = nullptr;   // n + 1 entries, [0] = sentinel
-  int2* ptable = nullptr;  // n + 1 positions, [0] = far sentinel
+  uint32_t* ptable = nullptr;  // n + 1 packed positions, [0] = far position
   int2* dxy_stage = nullptr;
   unsigned long long* counters = nullptr;      // [0] n_exact, [1] n_match, [2] flag
   unsigned long long* host_counters = nullptr;  // pinned mirror
@@ -539,7 +539,7 @@ extern "C" vd_ctx* vd_create(int32_t w, int32_t h, int32_t n) {
   rc = rc ? rc : ctx_alloc(reinterpret_cast<void**>(&c->buf[1]), map_bytes, "label map");
   rc = rc ? rc : ctx_alloc(reinterpret_cast<void**>(&c->seeds), sizeof(int2) * n, "seeds");
   rc = rc ? rc : ctx_alloc(reinterpret_cast<void**>(&c->table), sizeof(int2) * (static_cast<size_t>(n) + 1), "seed table");
-  rc = rc ? rc : ctx_alloc(reinterpret_cast<void**>(&c->ptable), sizeof(int2) * (static_cast<size_t>(n) + 1), "seed table");
+  rc = rc ? rc : ctx_alloc(reinterpret_cast<void**>(&c->ptable), sizeof(uint32_t) * (static_cast<size_t>(n) + 1), "seed table");
   rc = rc ? rc : ctx_alloc(reinterpret_cast<void**>(&c->dxy_stage), sizeof(int2) * n, "moves");
   rc = rc ? rc : ctx_alloc(reinterpret_cast<void**>(&c->counters), 4 * sizeof(unsigned long long), "counters");
   if (!rc) {

@@ -30,7 +30,7 @@ struct vd_batch {
   size_t arena_bytes = 0;
   int2* seeds = nullptr;
   int2* tables = nullptr;
-  int2* ptables = nullptr;
+  uint32_t* ptables = nullptr;
   int2* dxy_stage = nullptr;
   int64_t total_seeds = 0;
   int64_t total_pixels = 0;
@@ -188,7 +188,7 @@ extern "C" vd_batch* vd_batch_create(int32_t n_sims, const int32_t* w, const int
   cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&b->arena), b->arena_bytes);
   if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&b->seeds), sizeof(int2) * seeds);
   if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&b->tables), sizeof(int2) * (seeds + n_sims));
-  if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&b->ptables), sizeof(int2) * (seeds + n_sims));
+  if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&b->ptables), sizeof(uint32_t) * (seeds + n_sims));
   if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&b->dxy_stage), sizeof(int2) * seeds);
   if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&b->d_sims), sizeof(vdb::SimDesc) * n_sims);
   if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&b->bar), sizeof(vdb::Barrier));
@@ -560,7 +560,7 @@ struct Snapshot {
   int32_t* arena = nullptr;
   int2* seeds = nullptr;
   int2* tables = nullptr;
-  int2* ptables = nullptr;
+  uint32_t* ptables = nullptr;
   vdb::SimDesc* sims = nullptr;
   void release() {
     cudaFree(arena);
@@ -584,7 +584,7 @@ int snapshot_copy(vd_batch* b, Snapshot& sn, bool save) {
                                        sizeof(int2) * (b->total_seeds + b->n_sims), k, st), "snapshot tables");
   if (!rc)
     rc = vd_cuda_check(cudaMemcpyAsync(save ? sn.ptables : b->ptables, save ? b->ptables : sn.ptables,
-                                       sizeof(int2) * (b->total_seeds + b->n_sims), k, st), "snapshot tables");
+                                       sizeof(uint32_t) * (b->total_seeds + b->n_sims), k, st), "snapshot positions");
   if (!rc)
     rc = vd_cuda_check(cudaMemcpyAsync(save ? sn.sims : b->d_sims, save ? b->d_sims : sn.sims,
                                        sizeof(vdb::SimDesc) * b->n_sims, k, st), "snapshot descriptors");
@@ -609,7 +609,7 @@ extern "C" int vd_batch_autotune(vd_batch* b, int32_t steps, int32_t max_disp, u
   cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&sn.arena), b->arena_bytes);
   if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&sn.seeds), sizeof(int2) * b->total_seeds);
   if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&sn.tables), sizeof(int2) * (b->total_seeds + b->n_sims));
-  if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&sn.ptables), sizeof(int2) * (b->total_seeds + b->n_sims));
+  if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&sn.ptables), sizeof(uint32_t) * (b->total_seeds + b->n_sims));
   if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&sn.sims), sizeof(vdb::SimDesc) * b->n_sims);
   if (e != cudaSuccess) {
     sn.release();

@@ -31,7 +31,7 @@ struct SimDesc {
   int32_t* map[2];
   int2* seeds;
   int2* table;   // entry 0 = sentinel; the pass table is table + 1
-  int2* ptable;  // positions, entry 0 = far sentinel; used as ptable + 1
+  uint32_t* ptable;  // packed positions, entry 0 = far position; used as ptable + 1
   uint32_t cap, mul;       // clamped-key parameters (cap = 0: unusable)
   uint32_t clampmask[2];   // bit r: pass r of the schedule uses clamped keys
   int seed_off;
@@ -146,7 +146,7 @@ __device__ __forceinline__ void move_mark_block(const BatchArgs& A, int sb) {
     p.y = static_cast<int>(y);
     sd->seeds[k] = p;
     sd->table[k + 1] = vdk::table_entry(p);
-    sd->ptable[k + 1] = p;
+    sd->ptable[k + 1] = vdk::pack_pos(p.x, p.y);
   }
   if (A.mark) sd->map[sd->cur][static_cast<int64_t>(p.y) * sd->pitch + p.x] = k;
 }

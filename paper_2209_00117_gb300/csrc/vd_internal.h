@@ -19,7 +19,7 @@ struct MapView {
   int32_t w = 0, h = 0, pitch = 0, n = 0;
   const int2* seeds = nullptr;
   const int2* table = nullptr;   // packed pass table, entry -1 = sentinel
-  const int2* ptable = nullptr;  // position table, entry -1 = far sentinel
+  const uint32_t* ptable = nullptr;  // packed positions x | y << 16, entry -1 = far position
 };
 
 // Bits of the largest label (ceil(log2 n_seeds)); clamped 32-bit keys need
@@ -86,9 +86,9 @@ int run_passes(const MapView& m, int32_t* const buf[2], int* cur, const int32_t*
                int64_t* launches, Profiler* prof, bool djfa_frame);
 int launch_fill(int32_t* buf, int64_t n_elems, int32_t v, cudaStream_t st);
 int launch_stamp(const MapView& m, int32_t* labels, bool mark, cudaStream_t st, int64_t* launches);
-int launch_move(int2* seeds, int2* table, int2* ptable, int n, const int2* dxy, int w, int h, int max_disp,
+int launch_move(int2* seeds, int2* table, uint32_t* ptable, int n, const int2* dxy, int w, int h, int max_disp,
                 uint64_t key, uint64_t step, cudaStream_t st);
-int launch_build_table(const int2* seeds, int n, int2* table, int2* ptable, cudaStream_t st);
+int launch_build_table(const int2* seeds, int n, int2* table, uint32_t* ptable, cudaStream_t st);
 uint64_t rng_key(uint64_t rng_seed, uint64_t stream_id);
 int ensure_smem(const void* fn, size_t bytes, size_t* done);
 

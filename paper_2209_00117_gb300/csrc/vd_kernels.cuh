@@ -107,13 +107,19 @@ __device__ __forceinline__ int map1(const int32_t* p) {
   return __ldg(p);
 }
 
+template <bool COHERENT>
+__device__ __forceinline__ int2 map2(const int32_t* p) {
+  if (COHERENT) return __ldcg(reinterpret_cast<const int2*>(p));
+  return __ldg(reinterpret_cast<const int2*>(p));
+}
+
 struct PassArgs {
   const int32_t* __restrict__ src;
   int32_t* __restrict__ dst;
-  const int2* __restrict__ table;   // packed {x | y << 16, x^2 + y^2}; entry -1 is the sentinel
-  const int2* __restrict__ ptable;  // positions {x, y}; entry -1 is the far sentinel
-  uint32_t cap;                     // clamped-key passes: distance cap 2^(32 - lb) - 1
-  uint32_t mul;                     // and 2^lb, lb = bits of the largest label
+  const int2* __restrict__ table;       // {x | y << 16, x^2 + y^2}; entry -1 is the sentinel
+  const uint32_t* __restrict__ ptable;  // positions x | y << 16; entry -1 is the far position
+  uint32_t cap;                         // clamped-key passes: distance cap 2^(32 - lb) - 1
+  uint32_t mul;                         // and 2^lb, lb = bits of the largest label
   uint32_t n_seeds;
   int w, h, pitch, k;
   int band_m;  // > 1: visit row-blocks in k-strided bands (band_m = k / rows per block)
@@ -125,37 +131,53 @@ struct PassArgs {
 // budget of 6 blocks/SM) and leaves latency hiding to the many resident warps.
 __device__ __forceinline__ void group_fence() { asm volatile("" ::: "memory"); }
 
-__device__ __forceinline__ int4 shift_left_by(const int4& l, const int4& m, int kk) {
-  // labels at x0 - kk + i, i = 0..3, from the vectors at x0 - 4 (l) and x0 (m)
-  return kk == 1 ? make_int4(l.w, m.x, m.y, m.z) : make_int4(l.z, l.w, m.x, m.y);
+// Packed position table of the 32-bit key forms: entry k + 1 holds seed k as
+// x | y << 16 (both below 2^15); entry 0 (label -1) holds the far position
+// (kFarX, 0).  From any pixel of a grid up to 32768 wide that position lies
+// at squared distance [2^28, 49151^2 + 32767^2]: at or above every clamp cap
+// (2^28 - 1 at most) and below 2^32.
+constexpr uint32_t kFarX = 49151;
+
+__host__ __device__ __forceinline__ uint32_t pack_pos(int x, int y) {
+  return static_cast<uint32_t>(x) | (static_cast<uint32_t>(y) << 16);
 }
 
-__device__ __forceinline__ int4 shift_right_by(const int4& m, const int4& r, int kk) {
-  // labels at x0 + kk + i from the vectors at x0 (m) and x0 + 4 (r)
-  return kk == 1 ? make_int4(m.y, m.z, m.w, r.x) : make_int4(m.z, m.w, r.x, r.y);
-}
+// The four pixels (x0 .. x0+3, y) owned by one thread and their best
+// candidate so far.  Each key form gathers a seed's table entry once per
+// label and turns it into a "prepared position" (int2) holding what the four
+// pixels of the row share -- the seed's x and its y-term -- so that a
+// gathered entry can serve every pixel of the quad it is a candidate for.
+//   pos(c)          gather + prepare label c (c = -1: the sentinel entry)
+//   set(i, p, c)    best of pixel x0 + i := candidate (p, c)
+//   fold(i, p, c)   best of pixel x0 + i := min(best, candidate (p, c))
 
-// The four pixels (x0 .. x0+3, y) owned by one thread and their packed
-// best (key, label) so far: the exact 64-bit form (any metric).
+// Exact 64-bit form (any metric): packed (key, label), table entries
+// {x | y << 16, x^2 + y^2}.
 template <int METRIC, bool COH>
 struct Quad {
-  long long b0, b1, b2, b3;
+  long long b[4];
   int m2x, m2y, x0, y;
   const int2* __restrict__ table;
   __device__ __forceinline__ Quad(const PassArgs& a, int x0_, int y_)
       : m2x(-2 * x0_), m2y(-2 * y_), x0(x0_), y(y_), table(a.table) {}
-  __device__ __forceinline__ void init(const int4& L) {
-    b0 = cand<METRIC, COH>(L.x, table, m2x, m2y, x0, y);
-    b1 = cand<METRIC, COH>(L.y, table, m2x - 2, m2y, x0 + 1, y);
-    b2 = cand<METRIC, COH>(L.z, table, m2x - 4, m2y, x0 + 2, y);
-    b3 = cand<METRIC, COH>(L.w, table, m2x - 6, m2y, x0 + 3, y);
+  __device__ __forceinline__ int2 pos(int c) const {
+    const int2 e = COH ? __ldcg(&table[c]) : __ldg(&table[c]);
+    const int sx = e.x & 0xFFFF;
+    const int sy = static_cast<int>(static_cast<unsigned int>(e.x) >> 16);
+    // the sentinel (c = -1) reads {0, INT32_MAX}: its Euclidean key is
+    // INT32_MAX, its Manhattan key 2^30 + x, both above every real key
+    if (METRIC == kManhattan) return make_int2(sx, c < 0 ? 0x40000000 : abs(sy - y));
+    return make_int2(sx, static_cast<int>(static_cast<uint32_t>(e.y) + static_cast<uint32_t>(m2y) *
+                                                                         static_cast<uint32_t>(sy)));
   }
-  __device__ __forceinline__ void fold4(const int4& L) {
-    b0 = fold<METRIC, COH>(b0, L.x, table, m2x, m2y, x0, y);
-    b1 = fold<METRIC, COH>(b1, L.y, table, m2x - 2, m2y, x0 + 1, y);
-    b2 = fold<METRIC, COH>(b2, L.z, table, m2x - 4, m2y, x0 + 2, y);
-    b3 = fold<METRIC, COH>(b3, L.w, table, m2x - 6, m2y, x0 + 3, y);
+  __device__ __forceinline__ long long key(int i, int2 p, int c) const {
+    if (METRIC == kManhattan) return pack_key(abs(p.x - (x0 + i)) + p.y, c);
+    return pack_key(static_cast<int>(static_cast<uint32_t>(p.y) +
+                                     static_cast<uint32_t>(m2x - 2 * i) * static_cast<uint32_t>(p.x)),
+                    c);
   }
+  __device__ __forceinline__ void set(int i, int2 p, int c) { b[i] = key(i, p, c); }
+  __device__ __forceinline__ void fold(int i, int2 p, int c) { b[i] = min(b[i], key(i, p, c)); }
 };
 
 // Clamped 32-bit form (Euclidean): key = min(d^2, cap) * 2^lb + label, with
@@ -163,71 +185,94 @@ struct Quad {
 // candidate lies below distance^2 cap - 1 this orders the candidates exactly
 // as the 64-bit form (distance, then lowest label), with one 32-bit minimum
 // and one clamp instead of the 64-bit compare-and-select.  An empty label
-// reads the far sentinel position, clamps to cap and (the label wrapping to
-// -1) encodes as (cap - 1, 2^lb - 1): a quad whose best reaches cap - 1 is
+// reads the far position, clamps to cap and (the label wrapping to -1)
+// encodes as (cap - 1, 2^lb - 1): a quad whose best reaches cap - 1 is
 // recomputed with the exact form, so the result never depends on the cap.
+// Prepared position: {s.x, (s.y - y)^2}.
+template <bool COH>
+struct Quad32 {
+  uint32_t b[4];
+  int x0, y;
+  uint32_t cap, mul;
+  const uint32_t* __restrict__ ptable;
+  __device__ __forceinline__ Quad32(const PassArgs& a, int x0_, int y_)
+      : x0(x0_), y(y_), cap(a.cap), mul(a.mul), ptable(a.ptable) {}
+  __device__ __forceinline__ int2 pos(int c) const {
+    const uint32_t e = COH ? __ldcg(&ptable[c]) : __ldg(&ptable[c]);
+    const uint32_t dy = static_cast<uint32_t>(static_cast<int>(e >> 16) - y);
+    return make_int2(static_cast<int>(e & 0xFFFFu), static_cast<int>(dy * dy));
+  }
+  __device__ __forceinline__ uint32_t key(int i, int2 p, int c) const {
+    const uint32_t dx = static_cast<uint32_t>(p.x - (x0 + i));
+    const uint32_t d = dx * dx + static_cast<uint32_t>(p.y);
+    return min(d, cap) * mul + static_cast<uint32_t>(c);
+  }
+  __device__ __forceinline__ void set(int i, int2 p, int c) { b[i] = key(i, p, c); }
+  __device__ __forceinline__ void fold(int i, int2 p, int c) { b[i] = min(b[i], key(i, p, c)); }
+};
+
 // Manhattan 32-bit form: distances are at most 2 * 32767 < 2^17, so with
 // every label below 2^lb, lb <= 15, key = d * 2^lb + label is exact without a
-// cap.  An empty label takes distance 2^17 - 1, above every real one (it
-// wraps to (2^17 - 2, 2^lb - 1)), and a pixel whose best is such a key has
-// no candidate at all.
-constexpr uint32_t kManhattanEmpty = (1u << 17) - 1u;
+// cap.  Prepared position: {s.x, |s.y - y|}; an empty label takes the far
+// position's x (kFarX) and the y-term kManhattanFarY, which puts it at
+// distance [81919, 114686] from every pixel: above every real distance, below
+// 2^17, and (its label wrapping to -1) at a key of at least
+// (kManhattanMax + 1) * 2^lb, so a pixel whose best is such a key has no
+// candidate at all.
 constexpr uint32_t kManhattanMax = 2u * 32767u;
+constexpr int kManhattanFarY = 65535;
 
 template <bool COH>
 struct Quad32M {
-  uint32_t b0, b1, b2, b3;
+  uint32_t b[4];
   int x0, y;
   uint32_t mul;
-  const int2* __restrict__ ptable;
+  const uint32_t* __restrict__ ptable;
   __device__ __forceinline__ Quad32M(const PassArgs& a, int x0_, int y_)
       : x0(x0_), y(y_), mul(a.mul), ptable(a.ptable) {}
-  __device__ __forceinline__ uint32_t key(int c, int x) const {
-    const int2 p = COH ? __ldcg(&ptable[c]) : __ldg(&ptable[c]);
-    const uint32_t d = c < 0 ? kManhattanEmpty : static_cast<uint32_t>(abs(p.x - x) + abs(p.y - y));
-    return d * mul + static_cast<uint32_t>(c);
+  __device__ __forceinline__ int2 pos(int c) const {
+    const uint32_t e = COH ? __ldcg(&ptable[c]) : __ldg(&ptable[c]);
+    const int ady = c < 0 ? kManhattanFarY : abs(static_cast<int>(e >> 16) - y);
+    return make_int2(static_cast<int>(e & 0xFFFFu), ady);
   }
-  __device__ __forceinline__ void init(const int4& L) {
-    b0 = key(L.x, x0);
-    b1 = key(L.y, x0 + 1);
-    b2 = key(L.z, x0 + 2);
-    b3 = key(L.w, x0 + 3);
+  __device__ __forceinline__ uint32_t key(int i, int2 p, int c) const {
+    return static_cast<uint32_t>(abs(p.x - (x0 + i)) + p.y) * mul + static_cast<uint32_t>(c);
   }
-  __device__ __forceinline__ void fold4(const int4& L) {
-    b0 = min(b0, key(L.x, x0));
-    b1 = min(b1, key(L.y, x0 + 1));
-    b2 = min(b2, key(L.z, x0 + 2));
-    b3 = min(b3, key(L.w, x0 + 3));
-  }
+  __device__ __forceinline__ void set(int i, int2 p, int c) { b[i] = key(i, p, c); }
+  __device__ __forceinline__ void fold(int i, int2 p, int c) { b[i] = min(b[i], key(i, p, c)); }
 };
 
-template <bool COH>
-struct Quad32 {
-  uint32_t b0, b1, b2, b3;
-  int x0, y;
-  uint32_t cap, mul;
-  const int2* __restrict__ ptable;
-  __device__ __forceinline__ Quad32(const PassArgs& a, int x0_, int y_)
-      : x0(x0_), y(y_), cap(a.cap), mul(a.mul), ptable(a.ptable) {}
-  __device__ __forceinline__ uint32_t key(int c, int x) const {
-    const int2 p = COH ? __ldcg(&ptable[c]) : __ldg(&ptable[c]);
-    const int dx = p.x - x, dy = p.y - y;
-    const uint32_t d = static_cast<uint32_t>(dx * dx) + static_cast<uint32_t>(dy * dy);
-    return min(d, cap) * mul + static_cast<uint32_t>(c);
-  }
-  __device__ __forceinline__ void init(const int4& L) {
-    b0 = key(L.x, x0);
-    b1 = key(L.y, x0 + 1);
-    b2 = key(L.z, x0 + 2);
-    b3 = key(L.w, x0 + 3);
-  }
-  __device__ __forceinline__ void fold4(const int4& L) {
-    b0 = min(b0, key(L.x, x0));
-    b1 = min(b1, key(L.y, x0 + 1));
-    b2 = min(b2, key(L.z, x0 + 2));
-    b3 = min(b3, key(L.w, x0 + 3));
-  }
-};
+template <class Q>
+__device__ __forceinline__ void gather4(const Q& q, const int4& L, int2 (&p)[4]) {
+  p[0] = q.pos(L.x);
+  p[1] = q.pos(L.y);
+  p[2] = q.pos(L.z);
+  p[3] = q.pos(L.w);
+}
+
+template <class Q>
+__device__ __forceinline__ void init4(Q& q, const int4& L, const int2 (&p)[4]) {
+  q.set(0, p[0], L.x);
+  q.set(1, p[1], L.y);
+  q.set(2, p[2], L.z);
+  q.set(3, p[3], L.w);
+}
+
+template <class Q>
+__device__ __forceinline__ void fold4(Q& q, const int4& L, const int2 (&p)[4]) {
+  q.fold(0, p[0], L.x);
+  q.fold(1, p[1], L.y);
+  q.fold(2, p[2], L.z);
+  q.fold(3, p[3], L.w);
+}
+
+// Pixel x0 + i takes label L_i (i = 0..3).
+template <class Q>
+__device__ __forceinline__ void fold4(Q& q, const int4& L) {
+  int2 p[4];
+  gather4(q, L, p);
+  fold4(q, L, p);
+}
 
 // Labels at columns x0 + dx .. x0 + dx + 3 of one row for |dx| = k, a multiple
 // of 4 (one aligned 16-byte load); columns outside [0, pitch) read as -1 and
@@ -247,30 +292,57 @@ __device__ __forceinline__ int4 load_scalar4(const int32_t* __restrict__ row, in
 }
 
 // The side candidates (x -/+ k) of one source row for the four pixels of a
-// thread; `mid` is that row's aligned vector at x0 when already loaded.
+// thread; `mid` is that row's vector at x0 and `mp` its prepared positions.
+// For k = 1 and k = 2 the side labels of neighbouring pixels overlap the
+// row's own vector: only the 2 (k = 1) or 4 (k = 2) labels outside it are
+// gathered, and the 8 side candidates reuse `mp` for the rest.
 template <int KSEL, bool COH, class Q>
 __device__ __forceinline__ void fold_sides(Q& q, const int32_t* __restrict__ row, const int4& mid,
-                                           const PassArgs& a) {
+                                           const int2 (&mp)[4], const PassArgs& a) {
   const int x0 = q.x0;
   if (KSEL == 0) {
     const int4 L = load_side<COH>(row, x0, -a.k, a.pitch);
     const int4 R = load_side<COH>(row, x0, a.k, a.pitch);
-    q.fold4(L);
+    fold4(q, L);
     group_fence();
-    q.fold4(R);
-  } else if (KSEL == 1 || KSEL == 2) {
-    const int4 neg = make_int4(-1, -1, -1, -1);
-    const int4 lv = (x0 >= 4) ? map4<COH>(row + x0 - 4) : neg;
-    const int4 rv = (x0 + 4 < a.pitch) ? map4<COH>(row + x0 + 4) : neg;
-    q.fold4(shift_left_by(lv, mid, KSEL));
-    group_fence();
-    q.fold4(shift_right_by(mid, rv, KSEL));
+    fold4(q, R);
+  } else if (KSEL == 1) {
+    // left of pixel i: column x0 + i - 1; right: x0 + i + 1
+    const int l = (x0 >= 4) ? map1<COH>(row + x0 - 1) : -1;
+    const int r = (x0 + 4 < a.pitch) ? map1<COH>(row + x0 + 4) : -1;
+    const int2 pl = q.pos(l);
+    const int2 pr = q.pos(r);
+    q.fold(0, pl, l);
+    q.fold(1, mp[0], mid.x);
+    q.fold(2, mp[1], mid.y);
+    q.fold(3, mp[2], mid.z);
+    q.fold(0, mp[1], mid.y);
+    q.fold(1, mp[2], mid.z);
+    q.fold(2, mp[3], mid.w);
+    q.fold(3, pr, r);
+  } else if (KSEL == 2) {
+    // left of pixel i: column x0 + i - 2; right: x0 + i + 2
+    const int2 neg = make_int2(-1, -1);
+    const int2 l = (x0 >= 4) ? map2<COH>(row + x0 - 2) : neg;
+    const int2 r = (x0 + 4 < a.pitch) ? map2<COH>(row + x0 + 4) : neg;
+    const int2 pl0 = q.pos(l.x);
+    const int2 pl1 = q.pos(l.y);
+    const int2 pr0 = q.pos(r.x);
+    const int2 pr1 = q.pos(r.y);
+    q.fold(0, pl0, l.x);
+    q.fold(1, pl1, l.y);
+    q.fold(2, mp[0], mid.x);
+    q.fold(3, mp[1], mid.y);
+    q.fold(0, mp[2], mid.z);
+    q.fold(1, mp[3], mid.w);
+    q.fold(2, pr0, r.x);
+    q.fold(3, pr1, r.y);
   } else {
     const int4 L = load_scalar4<COH>(row, x0 - a.k, a.w);
     const int4 R = load_scalar4<COH>(row, x0 + a.k, a.w);
-    q.fold4(L);
+    fold4(q, L);
     group_fence();
-    q.fold4(R);
+    fold4(q, R);
   }
   group_fence();
 }
@@ -278,8 +350,8 @@ __device__ __forceinline__ void fold_sides(Q& q, const int32_t* __restrict__ row
 // One jump pass (Table I / Section IV-B) for the four horizontally adjacent
 // pixels (x0 .. x0+3, y) of one thread: it starts from their own labels and
 // folds in the neighbour offsets one source row at a time (16-byte label
-// loads, four seed gathers and four minimums per offset).  Candidate order
-// does not matter: both key forms are total orders.
+// loads, seed gathers and minimums).  Candidate order does not matter: every
+// key form is a total order.
 template <int NB, int KSEL, bool COH, class Q>
 __device__ __forceinline__ void fold_all(Q& q, const PassArgs& a, int x0, int y) {
   const int64_t pitch = a.pitch;
@@ -292,26 +364,31 @@ __device__ __forceinline__ void fold_all(Q& q, const PassArgs& a, int x0, int y)
   const int32_t* drow = a.src + (y + a.k) * pitch;
   const int4 neg = make_int4(-1, -1, -1, -1);
   const int4 um = up_ok ? map4<COH>(urow + x0) : neg;
-  q.init(own);
+  int2 p[4];
+  gather4(q, own, p);
+  init4(q, own, p);
   group_fence();
   // centre row: (-k, 0), (+k, 0)
-  fold_sides<KSEL, COH>(q, crow, own, a);
+  fold_sides<KSEL, COH>(q, crow, own, p, a);
   // up row: (0, -k) and, for Moore, (-k, -k), (+k, -k); then the down row
   if (up_ok) {
     const int4 dm = dn_ok ? map4<COH>(drow + x0) : neg;
-    q.fold4(um);
+    gather4(q, um, p);
+    fold4(q, um, p);
     group_fence();
-    if (NB == kMoore) fold_sides<KSEL, COH>(q, urow, um, a);
+    if (NB == kMoore) fold_sides<KSEL, COH>(q, urow, um, p, a);
     if (dn_ok) {
-      q.fold4(dm);
+      gather4(q, dm, p);
+      fold4(q, dm, p);
       group_fence();
-      if (NB == kMoore) fold_sides<KSEL, COH>(q, drow, dm, a);
+      if (NB == kMoore) fold_sides<KSEL, COH>(q, drow, dm, p, a);
     }
   } else if (dn_ok) {
     const int4 dm = map4<COH>(drow + x0);
-    q.fold4(dm);
+    gather4(q, dm, p);
+    fold4(q, dm, p);
     group_fence();
-    if (NB == kMoore) fold_sides<KSEL, COH>(q, drow, dm, a);
+    if (NB == kMoore) fold_sides<KSEL, COH>(q, drow, dm, p, a);
   }
 }
 
@@ -324,14 +401,14 @@ __device__ __forceinline__ void store_quad(const PassArgs& a, int x0, int y, int
   *reinterpret_cast<int4*>(a.dst + static_cast<int64_t>(y) * a.pitch + x0) = out;
 }
 
+__device__ __forceinline__ int low_label(long long b) { return static_cast<int>(static_cast<unsigned int>(b)); }
+
 // Exact form (any metric).
 template <int NB, int METRIC, int KSEL, bool COH = false>
 __device__ __forceinline__ void pass_quad(const PassArgs& a, int x0, int y) {
   Quad<METRIC, COH> q(a, x0, y);
   fold_all<NB, KSEL, COH>(q, a, x0, y);
-  store_quad(a, x0, y, static_cast<int>(static_cast<unsigned int>(q.b0)),
-             static_cast<int>(static_cast<unsigned int>(q.b1)), static_cast<int>(static_cast<unsigned int>(q.b2)),
-             static_cast<int>(static_cast<unsigned int>(q.b3)));
+  store_quad(a, x0, y, low_label(q.b[0]), low_label(q.b[1]), low_label(q.b[2]), low_label(q.b[3]));
 }
 
 // 32-bit forms.  Euclidean: clamped, falling back to the exact form for a
@@ -344,20 +421,21 @@ __device__ __forceinline__ void pass_quad_clamped(const PassArgs& a, int x0, int
     Quad32M<COH> q(a, x0, y);
     fold_all<NB, KSEL, COH>(q, a, x0, y);
     const uint32_t lim = (kManhattanMax + 1u) * a.mul;
-    store_quad(a, x0, y, q.b0 >= lim ? -1 : static_cast<int>(q.b0 & mask),
-               q.b1 >= lim ? -1 : static_cast<int>(q.b1 & mask), q.b2 >= lim ? -1 : static_cast<int>(q.b2 & mask),
-               q.b3 >= lim ? -1 : static_cast<int>(q.b3 & mask));
+    store_quad(a, x0, y, q.b[0] >= lim ? -1 : static_cast<int>(q.b[0] & mask),
+               q.b[1] >= lim ? -1 : static_cast<int>(q.b[1] & mask),
+               q.b[2] >= lim ? -1 : static_cast<int>(q.b[2] & mask),
+               q.b[3] >= lim ? -1 : static_cast<int>(q.b[3] & mask));
     return;
   }
   Quad32<COH> q(a, x0, y);
   fold_all<NB, KSEL, COH>(q, a, x0, y);
   const uint32_t lim = (a.cap - 1u) * a.mul;
-  if (max(max(q.b0, q.b1), max(q.b2, q.b3)) >= lim) {
+  if (max(max(q.b[0], q.b[1]), max(q.b[2], q.b[3])) >= lim) {
     pass_quad<NB, kEuclid, KSEL, COH>(a, x0, y);
     return;
   }
-  store_quad(a, x0, y, static_cast<int>(q.b0 & mask), static_cast<int>(q.b1 & mask), static_cast<int>(q.b2 & mask),
-             static_cast<int>(q.b3 & mask));
+  store_quad(a, x0, y, static_cast<int>(q.b[0] & mask), static_cast<int>(q.b[1] & mask),
+             static_cast<int>(q.b[2] & mask), static_cast<int>(q.b[3] & mask));
 }
 
 #ifndef VD_PASS_MIN_BLOCKS
@@ -494,23 +572,18 @@ __device__ __forceinline__ int rng_disp(uint64_t key, uint64_t step, uint64_t k,
   return static_cast<int>(((draw >> 32) * m) >> 32) - max_disp;
 }
 
-// Far sentinel of the position table: from any pixel of a grid up to 32768
-// wide its squared distance lies in [2 * 13573^2, 2 * 46340^2], above every
-// clamp cap used (2^28 - 1 at most) and below 2^32.
-constexpr int kFarSentinel = -13573;
-
 // Rebuilds the pass tables (entry k + 1 for seed k; entry 0 the sentinels).
 static __global__ void k_build_table(const int2* __restrict__ seeds, int n, int2* __restrict__ table,
-                                     int2* __restrict__ ptable) {
+                                     uint32_t* __restrict__ ptable) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k == 0) {
     table[0] = make_int2(0, kSentinelNorm);
-    ptable[0] = make_int2(kFarSentinel, kFarSentinel);
+    ptable[0] = pack_pos(static_cast<int>(kFarX), 0);
   }
   if (k < n) {
     const int2 p = seeds[k];
     table[k + 1] = table_entry(p);
-    ptable[k + 1] = p;
+    ptable[k + 1] = pack_pos(p.x, p.y);
   }
 }
 
@@ -526,7 +599,7 @@ static __global__ void k_check_labels(const int32_t* __restrict__ labels, int64_
 
 // SimulateParticles (Algorithm 1): p_k <- clamp(p_k + delta_k) on the grid;
 // also refreshes the seed's pass-table entry.
-static __global__ void k_move(int2* __restrict__ seeds, int2* __restrict__ table, int2* __restrict__ ptable,
+static __global__ void k_move(int2* __restrict__ seeds, int2* __restrict__ table, uint32_t* __restrict__ ptable,
                               int n, const int2* __restrict__ dxy, int w, int h, int max_disp, uint64_t key,
                               uint64_t step) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -548,7 +621,7 @@ static __global__ void k_move(int2* __restrict__ seeds, int2* __restrict__ table
   p.y = static_cast<int>(y);
   seeds[k] = p;
   table[k + 1] = table_entry(p);
-  ptable[k + 1] = p;
+  ptable[k + 1] = pack_pos(p.x, p.y);
 }
 
 // Stamp, first half: every seed pixel is overwritten with one of the indices

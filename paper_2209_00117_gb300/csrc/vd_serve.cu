@@ -70,7 +70,7 @@ double now_s(const vd_server* s) {
 
 int64_t sim_bytes(int w, int h, int n) {
   const int64_t pitch = (w + 31) / 32 * 32;
-  return 2 * pitch * h * 4 + static_cast<int64_t>(n) * 8 + 2 * (static_cast<int64_t>(n) + 1) * 8 + 256;
+  return 2 * pitch * h * 4 + static_cast<int64_t>(n) * 8 + (static_cast<int64_t>(n) + 1) * (8 + 4) + 256;
 }
 
 void server_free(vd_server* s) {
@@ -233,7 +233,7 @@ extern "C" int32_t vd_server_add_sim(vd_server* s, int32_t w, int32_t h, int32_t
   d.map[1] = d.map[0] + map_elems;
   d.seeds = reinterpret_cast<int2*>(d.map[1] + map_elems);
   d.table = d.seeds + n;
-  d.ptable = d.table + (n + 1);
+  d.ptable = reinterpret_cast<uint32_t*>(d.table + (n + 1));
   d.cur = 0;
   d.step = 0;
   d.n_pass[0] = vdi::fill_schedule(vdi::djfa_first_step(w, h, n, s->d_max), s->vn_waves, 0, d.ks[0], d.nbs[0],
