@@ -444,6 +444,10 @@ int vd_server_set_max_batch(vd_server* server, int32_t max_batch);
                                     Manhattan d * 2^lb + label (no cap; usable with <= 32768 seeds).
                                     -1 = auto (default: Euclidean dJFA passes, every Manhattan pass),
                                     0 = never, 1 = always when usable */
+#define VD_OPT_PDL 8             /* 1 (default) = a frame's stamp and pass kernels are chained with
+                                    programmatic dependent launch: each may be scheduled while its
+                                    predecessor drains and waits for it on the device before touching
+                                    memory; 0 = plain stream order.  Results never depend on it */
 int vd_set_option(vd_ctx* ctx, int32_t option, int64_t value);
 int vd_get_option(const vd_ctx* ctx, int32_t option, int64_t* value);
 

@@ -141,13 +141,33 @@ int ensure_smem(const void* fn, size_t bytes, size_t* done) {
   return VD_OK;
 }
 
+// Launches `kern` on `st`.  With `pdl` the launch carries programmatic stream
+// serialization: it may be scheduled while the previous kernel on the stream
+// drains, and the kernel itself waits for that kernel (vdk::pdl_wait) before
+// touching global memory.  Only kernels that begin with pdl_wait are launched
+// this way.
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_k(void (*kern)(KArgs...), dim3 g, dim3 b, cudaStream_t st, bool pdl, Args... args) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = g;
+  cfg.blockDim = b;
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 template <int NB, int METRIC, bool CLAMP>
-static void launch_pass_t(int ksel, dim3 g, dim3 b, cudaStream_t st, const vdk::PassArgs& a) {
+static cudaError_t launch_pass_t(int ksel, dim3 g, dim3 b, cudaStream_t st, bool pdl, const vdk::PassArgs& a) {
   switch (ksel) {
-    case 0: vdk::k_pass<NB, METRIC, 0, CLAMP><<<g, b, 0, st>>>(a); break;
-    case 1: vdk::k_pass<NB, METRIC, 1, CLAMP><<<g, b, 0, st>>>(a); break;
-    case 2: vdk::k_pass<NB, METRIC, 2, CLAMP><<<g, b, 0, st>>>(a); break;
-    default: vdk::k_pass<NB, METRIC, 3, CLAMP><<<g, b, 0, st>>>(a); break;
+    case 0: return launch_k(vdk::k_pass<NB, METRIC, 0, CLAMP>, g, b, st, pdl, a);
+    case 1: return launch_k(vdk::k_pass<NB, METRIC, 1, CLAMP>, g, b, st, pdl, a);
+    case 2: return launch_k(vdk::k_pass<NB, METRIC, 2, CLAMP>, g, b, st, pdl, a);
+    default: return launch_k(vdk::k_pass<NB, METRIC, 3, CLAMP>, g, b, st, pdl, a);
   }
 }
 
@@ -175,7 +195,7 @@ bool use_clamp(int clamp_option, int32_t metric, int32_t n, int32_t k, bool djfa
 }
 
 int launch_pass(const MapView& m, const int32_t* src, int32_t* dst, int32_t k, int32_t nb,
-                int32_t metric, int64_t band_min_k, bool clamp, cudaStream_t st) {
+                int32_t metric, int64_t band_min_k, bool clamp, cudaStream_t st, bool pdl) {
   vdk::PassArgs a;
   a.src = src;
   a.dst = dst;
@@ -214,23 +234,25 @@ int launch_pass(const MapView& m, const int32_t* src, int32_t* dst, int32_t k, i
   const int ksel = (k % 4 == 0) ? 0 : (k == 1 ? 1 : (k == 2 ? 2 : 3));
   if (clamp && metric == VD_METRIC_EUCLID && a.cap == 0) clamp = false;
   if (clamp && metric == VD_METRIC_MANHATTAN && label_bits(m.n) > 15) clamp = false;
+  cudaError_t e;
   if (nb == VD_NB_MOORE) {
     if (metric == VD_METRIC_EUCLID) {
-      if (clamp) launch_pass_t<vdk::kMoore, vdk::kEuclid, true>(ksel, grid, block, st, a);
-      else launch_pass_t<vdk::kMoore, vdk::kEuclid, false>(ksel, grid, block, st, a);
+      e = clamp ? launch_pass_t<vdk::kMoore, vdk::kEuclid, true>(ksel, grid, block, st, pdl, a)
+                : launch_pass_t<vdk::kMoore, vdk::kEuclid, false>(ksel, grid, block, st, pdl, a);
     } else {
-      if (clamp) launch_pass_t<vdk::kMoore, vdk::kManhattan, true>(ksel, grid, block, st, a);
-      else launch_pass_t<vdk::kMoore, vdk::kManhattan, false>(ksel, grid, block, st, a);
+      e = clamp ? launch_pass_t<vdk::kMoore, vdk::kManhattan, true>(ksel, grid, block, st, pdl, a)
+                : launch_pass_t<vdk::kMoore, vdk::kManhattan, false>(ksel, grid, block, st, pdl, a);
     }
   } else {
     if (metric == VD_METRIC_EUCLID) {
-      if (clamp) launch_pass_t<vdk::kVonNeumann, vdk::kEuclid, true>(ksel, grid, block, st, a);
-      else launch_pass_t<vdk::kVonNeumann, vdk::kEuclid, false>(ksel, grid, block, st, a);
+      e = clamp ? launch_pass_t<vdk::kVonNeumann, vdk::kEuclid, true>(ksel, grid, block, st, pdl, a)
+                : launch_pass_t<vdk::kVonNeumann, vdk::kEuclid, false>(ksel, grid, block, st, pdl, a);
     } else {
-      if (clamp) launch_pass_t<vdk::kVonNeumann, vdk::kManhattan, true>(ksel, grid, block, st, a);
-      else launch_pass_t<vdk::kVonNeumann, vdk::kManhattan, false>(ksel, grid, block, st, a);
+      e = clamp ? launch_pass_t<vdk::kVonNeumann, vdk::kManhattan, true>(ksel, grid, block, st, pdl, a)
+                : launch_pass_t<vdk::kVonNeumann, vdk::kManhattan, false>(ksel, grid, block, st, pdl, a);
     }
   }
+  if (e != cudaSuccess) return vd_cuda_check(e, "jump pass launch");
   return vd_cuda_check(cudaGetLastError(), "jump pass launch");
 }
 
@@ -315,7 +337,7 @@ int run_passes(const MapView& m, int32_t* const buf[2], int* cur, const int32_t*
     const int pi = prof ? prof->begin(l.n == 1 ? VD_KERNEL_PASS : VD_KERNEL_FUSED, px * l.n, st) : -1;
     if (l.n == 1) {
       rc = launch_pass(m, src, dst, ks[l.first], nbs[l.first], metric, t.band_min_k,
-                       use_clamp(t.clamp, metric, m.n, ks[l.first], djfa_frame), st);
+                       use_clamp(t.clamp, metric, m.n, ks[l.first], djfa_frame), st, t.pdl != 0);
     } else {
       rc = launch_fused(m, src, dst, ks + l.first, nbs + l.first, l.n, metric, t.tile_x, t.tile_y, st);
     }
@@ -338,13 +360,16 @@ int launch_fill(int32_t* buf, int64_t n_elems, int32_t v, cudaStream_t st) {
   return vd_cuda_check(cudaGetLastError(), "fill launch");
 }
 
-int launch_stamp(const MapView& m, int32_t* labels, bool mark, cudaStream_t st, int64_t* launches) {
+int launch_stamp(const MapView& m, int32_t* labels, bool mark, cudaStream_t st, int64_t* launches, bool pdl) {
   const int blocks = grid1d(m.n, 256);
   if (mark) {
-    vdk::k_stamp_mark<<<blocks, 256, 0, st>>>(labels, m.pitch, m.seeds, m.n);
+    const cudaError_t e = launch_k(vdk::k_stamp_mark, dim3(blocks), dim3(256), st, false, labels, m.pitch, m.seeds, m.n);
+    if (e != cudaSuccess) return vd_cuda_check(e, "stamp launch");
     ++*launches;
   }
-  vdk::k_stamp_min<<<blocks, 256, 0, st>>>(labels, m.pitch, m.seeds, m.n);
+  // the minimum half follows the mark half or a fill: it may start while that drains
+  const cudaError_t e = launch_k(vdk::k_stamp_min, dim3(blocks), dim3(256), st, pdl, labels, m.pitch, m.seeds, m.n);
+  if (e != cudaSuccess) return vd_cuda_check(e, "stamp launch");
   ++*launches;
   return vd_cuda_check(cudaGetLastError(), "stamp launch");
 }
@@ -736,7 +761,7 @@ extern "C" int vd_jfa(vd_ctx* c, int32_t extra, int32_t metric) {
     ++c->launches;
     if (rc) return rc;
     pi = pr ? pr->begin(VD_KERNEL_STAMP, c->n, c->stream) : -1;
-    rc = vdi::launch_stamp(view(c), c->buf[c->cur], false, c->stream, &c->launches);
+    rc = vdi::launch_stamp(view(c), c->buf[c->cur], false, c->stream, &c->launches, c->tune.pdl != 0);
     if (pr) pr->end(pi, c->stream);
     if (rc) return rc;
     return vdi::run_passes(view(c), c->buf, &c->cur, ks, nbs, n, metric, c->tune, c->stream, &c->launches, pr,
@@ -756,7 +781,7 @@ extern "C" int vd_djfa_step(vd_ctx* c, int32_t d_max, int32_t vn_waves, int32_t 
   auto body = [&]() -> int {
     vdi::Profiler* pr = prof_of(c);
     const int pi = pr ? pr->begin(VD_KERNEL_STAMP, 2 * static_cast<int64_t>(c->n), c->stream) : -1;
-    const int rc = vdi::launch_stamp(view(c), c->buf[c->cur], true, c->stream, &c->launches);
+    const int rc = vdi::launch_stamp(view(c), c->buf[c->cur], true, c->stream, &c->launches, c->tune.pdl != 0);
     if (pr) pr->end(pi, c->stream);
     if (rc) return rc;
     return vdi::run_passes(view(c), c->buf, &c->cur, ks, nbs, n, metric, c->tune, c->stream, &c->launches, pr,
@@ -996,6 +1021,10 @@ extern "C" int vd_set_option(vd_ctx* c, int32_t option, int64_t value) {
       if (value < -1 || value > 1) return vd_fail(VD_EINVAL, "clamped keys must be -1, 0 or 1");
       t.clamp = static_cast<int>(value);
       break;
+    case VD_OPT_PDL:
+      if (value != 0 && value != 1) return vd_fail(VD_EINVAL, "pdl must be 0 or 1");
+      t.pdl = static_cast<int>(value);
+      break;
     default:
       return vd_fail(VD_EINVAL, "unknown option %d", option);
   }
@@ -1018,6 +1047,7 @@ extern "C" int vd_get_option(const vd_ctx* c, int32_t option, int64_t* value) {
     case VD_OPT_FUSE_TILE_Y: *value = c->tune.tile_y; break;
     case VD_OPT_PROFILE: *value = c->tune.profile; break;
     case VD_OPT_CLAMPED_KEYS: *value = c->tune.clamp; break;
+    case VD_OPT_PDL: *value = c->tune.pdl; break;
     default: return vd_fail(VD_EINVAL, "unknown option %d", option);
   }
   return VD_OK;

@@ -38,6 +38,7 @@ struct Tuning {
   int tile_y = 32;
   int profile = 0;
   int clamp = -1;  // clamped 32-bit keys: -1 auto, 0 never, 1 whenever usable
+  int pdl = 1;     // chain a frame's kernels with programmatic dependent launch
 };
 
 // Event pairs bracketing kernel launches (profiling mode).  Records are kept
@@ -77,7 +78,7 @@ int fill_schedule(int32_t first, int32_t vn_waves, int32_t extra, int32_t* ks, i
 std::vector<Launch> plan_passes(const int32_t* ks, const int32_t* nbs, int n, int fuse_max_k,
                                 int max_halo);
 int launch_pass(const MapView& m, const int32_t* src, int32_t* dst, int32_t k, int32_t nb,
-                int32_t metric, int64_t band_min_k, bool clamp, cudaStream_t st);
+                int32_t metric, int64_t band_min_k, bool clamp, cudaStream_t st, bool pdl = false);
 int launch_fused(const MapView& m, const int32_t* src, int32_t* dst, const int32_t* ks,
                  const int32_t* nbs, int n, int32_t metric, int tile_x, int tile_y,
                  cudaStream_t st);
@@ -85,7 +86,8 @@ int run_passes(const MapView& m, int32_t* const buf[2], int* cur, const int32_t*
                const int32_t* nbs, int n, int32_t metric, const Tuning& t, cudaStream_t st,
                int64_t* launches, Profiler* prof, bool djfa_frame);
 int launch_fill(int32_t* buf, int64_t n_elems, int32_t v, cudaStream_t st);
-int launch_stamp(const MapView& m, int32_t* labels, bool mark, cudaStream_t st, int64_t* launches);
+int launch_stamp(const MapView& m, int32_t* labels, bool mark, cudaStream_t st, int64_t* launches,
+                 bool pdl = false);
 int launch_move(int2* seeds, int2* table, uint32_t* ptable, int n, const int2* dxy, int w, int h, int max_disp,
                 uint64_t key, uint64_t step, cudaStream_t st);
 int launch_build_table(const int2* seeds, int n, int2* table, uint32_t* ptable, cudaStream_t st);

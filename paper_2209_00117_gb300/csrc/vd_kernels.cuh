@@ -131,6 +131,16 @@ struct PassArgs {
 // budget of 6 blocks/SM) and leaves latency hiding to the many resident warps.
 __device__ __forceinline__ void group_fence() { asm volatile("" ::: "memory"); }
 
+// Programmatic dependent launch.  pdl_trigger lets the next kernel on the
+// stream, when it was launched with programmatic stream serialization, be
+// scheduled onto SMs this grid frees while it drains; pdl_wait blocks until
+// the grid this one depends on has completed and its writes are visible.  A
+// kernel of such a chain calls both before its first global-memory access.
+// For a kernel launched without the attribute the wait returns at once (its
+// predecessor has completed by stream order).
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // Packed position table of the 32-bit key forms: entry k + 1 holds seed k as
 // x | y << 16 (both below 2^15); entry 0 (label -1) holds the far position
 // (kFarX, 0).  From any pixel of a grid up to 32768 wide that position lies
@@ -444,6 +454,8 @@ __device__ __forceinline__ void pass_quad_clamped(const PassArgs& a, int x0, int
 
 template <int NB, int METRIC, int KSEL, bool CLAMP = false>
 __global__ void __launch_bounds__(256, VD_PASS_MIN_BLOCKS) k_pass(PassArgs a) {
+  pdl_trigger();
+  pdl_wait();
   const int x0 = 4 * static_cast<int>(blockIdx.x * blockDim.x + threadIdx.x);
   int rb = blockIdx.y;
   if (a.band_m > 1) rb = (blockIdx.y % a.band_t) * a.band_m + blockIdx.y / a.band_t;
@@ -479,6 +491,8 @@ struct FusedArgs {
 // out-of-grid neighbours, so the result equals the unfused passes bit for bit.
 template <int METRIC>
 __global__ void __launch_bounds__(256) k_pass_fused(FusedArgs a) {
+  pdl_trigger();
+  pdl_wait();
   extern __shared__ int32_t smem[];
   const int H = a.halo;
   const int SW = a.tx + 2 * H;
@@ -628,6 +642,8 @@ static __global__ void k_move(int2* __restrict__ seeds, int2* __restrict__ table
 // standing on it (which one does not matter), replacing any stale label.
 static __global__ void k_stamp_mark(int32_t* __restrict__ labels, int pitch, const int2* __restrict__ seeds,
                              int n) {
+  pdl_trigger();
+  pdl_wait();
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n) return;
   const int2 p = seeds[k];
@@ -638,6 +654,8 @@ static __global__ void k_stamp_mark(int32_t* __restrict__ labels, int pitch, con
 // unsigned, -1 is the largest value, so this also stamps an emptied map.
 static __global__ void k_stamp_min(int32_t* __restrict__ labels, int pitch, const int2* __restrict__ seeds,
                             int n) {
+  pdl_trigger();
+  pdl_wait();
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n) return;
   const int2 p = seeds[k];
@@ -646,6 +664,8 @@ static __global__ void k_stamp_min(int32_t* __restrict__ labels, int pitch, cons
 }
 
 static __global__ void k_fill(int4* __restrict__ p, int64_t n4, int v) {
+  pdl_trigger();
+  pdl_wait();
   const int4 val = make_int4(v, v, v, v);
   for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n4;
        i += static_cast<int64_t>(gridDim.x) * blockDim.x)

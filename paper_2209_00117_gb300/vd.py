@@ -22,6 +22,7 @@ OPT_FUSE_TILE_X = 4
 OPT_FUSE_TILE_Y = 5
 OPT_PROFILE = 6
 OPT_CLAMPED_KEYS = 7
+OPT_PDL = 8
 
 KERNEL_KINDS = ("pass", "fused", "stamp", "move", "fill")
 

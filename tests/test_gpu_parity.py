@@ -379,3 +379,39 @@ def test_maximum_side_grids(vd, orc, w, h):
             sim.djfa_step(d_max=5, metric=metric)
             np.testing.assert_array_equal(sim.labels(), orc.djfa_step(w, h, xy2, lab, d_max=5, metric=metric))
             sim.close()
+
+
+@pytest.mark.parametrize("graphs", [0, 1])
+def test_dependent_launch_chain_matches_oracle(vd, orc, graphs):
+    """Frames whose stamp and pass kernels are chained with programmatic
+    dependent launch (the default) equal plain stream order and the oracle,
+    eagerly and from graphs, on a side stream, for both metrics."""
+    import torch
+
+    w, h, s, D = 2048, 1536, 9000, 3
+    xy = inputs.uniform_seeds(w, h, s, seed=77)
+    disp = inputs.displacements(s, D, 3, seed=77)
+    stream = torch.cuda.Stream()
+    on = _sim(vd, w, h, xy, use_graphs=graphs, pdl=1)
+    off = _sim(vd, w, h, xy, use_graphs=graphs, pdl=0)
+    on.set_stream(stream)
+    assert on.get_option(vd.OPT_PDL) == 1 and off.get_option(vd.OPT_PDL) == 0
+    for metric in [E, L1]:
+        on.set_seeds(xy)
+        off.set_seeds(xy)
+        on.jfa(metric=metric)
+        off.jfa(metric=metric)
+        lab = orc.jfa(w, h, xy, metric=metric)
+        np.testing.assert_array_equal(on.labels(), lab)
+        np.testing.assert_array_equal(off.labels(), lab)
+        cur = xy
+        for t in range(3):
+            cur = orc.move(w, h, cur, disp[t])
+            lab = orc.djfa_step(w, h, cur, lab, d_max=D, metric=metric)
+            for sim in (on, off):
+                sim.move(disp[t])
+                sim.djfa_step(d_max=D, metric=metric)
+            np.testing.assert_array_equal(on.labels(), lab)
+            np.testing.assert_array_equal(off.labels(), lab)
+    on.close()
+    off.close()
