@@ -448,6 +448,10 @@ int vd_server_set_max_batch(vd_server* server, int32_t max_batch);
                                     programmatic dependent launch: each may be scheduled while its
                                     predecessor drains and waits for it on the device before touching
                                     memory; 0 = plain stream order.  Results never depend on it */
+#define VD_OPT_DEDUP_GATHERS 9   /* a label equal to its left neighbour in a 4-label vector reuses that
+                                    neighbour's table gather: -1 = auto (default: dJFA passes on maps
+                                    of at most 256 pixels per seed), 0 = never, 1 = always.  Results
+                                    never depend on it */
 int vd_set_option(vd_ctx* ctx, int32_t option, int64_t value);
 int vd_get_option(const vd_ctx* ctx, int32_t option, int64_t* value);
 

@@ -162,7 +162,16 @@ static cudaError_t launch_k(void (*kern)(KArgs...), dim3 g, dim3 b, cudaStream_t
 }
 
 template <int NB, int METRIC, bool CLAMP>
-static cudaError_t launch_pass_t(int ksel, dim3 g, dim3 b, cudaStream_t st, bool pdl, const vdk::PassArgs& a) {
+static cudaError_t launch_pass_t(int ksel, bool dedup, dim3 g, dim3 b, cudaStream_t st, bool pdl,
+                                 const vdk::PassArgs& a) {
+  if (dedup) {
+    switch (ksel) {
+      case 0: return launch_k(vdk::k_pass<NB, METRIC, 0, CLAMP, true>, g, b, st, pdl, a);
+      case 1: return launch_k(vdk::k_pass<NB, METRIC, 1, CLAMP, true>, g, b, st, pdl, a);
+      case 2: return launch_k(vdk::k_pass<NB, METRIC, 2, CLAMP, true>, g, b, st, pdl, a);
+      default: break;  // any other step: scalar loads, never de-duplicated
+    }
+  }
   switch (ksel) {
     case 0: return launch_k(vdk::k_pass<NB, METRIC, 0, CLAMP>, g, b, st, pdl, a);
     case 1: return launch_k(vdk::k_pass<NB, METRIC, 1, CLAMP>, g, b, st, pdl, a);
@@ -195,7 +204,7 @@ bool use_clamp(int clamp_option, int32_t metric, int32_t n, int32_t k, bool djfa
 }
 
 int launch_pass(const MapView& m, const int32_t* src, int32_t* dst, int32_t k, int32_t nb,
-                int32_t metric, int64_t band_min_k, bool clamp, cudaStream_t st, bool pdl) {
+                int32_t metric, int64_t band_min_k, bool clamp, cudaStream_t st, bool pdl, bool dedup) {
   vdk::PassArgs a;
   a.src = src;
   a.dst = dst;
@@ -215,7 +224,7 @@ int launch_pass(const MapView& m, const int32_t* src, int32_t* dst, int32_t k, i
   a.band_t = 1;
   const int quads = m.pitch / 4;
   const int bx = quads < 64 ? quads : 64;
-  const int by = 256 / bx;
+  const int by = vdk::kPassThreads / bx;
   const int nrb = (m.h + by - 1) / by;
   dim3 block(bx, by);
   dim3 grid((quads + bx - 1) / bx, nrb);
@@ -237,19 +246,19 @@ int launch_pass(const MapView& m, const int32_t* src, int32_t* dst, int32_t k, i
   cudaError_t e;
   if (nb == VD_NB_MOORE) {
     if (metric == VD_METRIC_EUCLID) {
-      e = clamp ? launch_pass_t<vdk::kMoore, vdk::kEuclid, true>(ksel, grid, block, st, pdl, a)
-                : launch_pass_t<vdk::kMoore, vdk::kEuclid, false>(ksel, grid, block, st, pdl, a);
+      e = clamp ? launch_pass_t<vdk::kMoore, vdk::kEuclid, true>(ksel, dedup, grid, block, st, pdl, a)
+                : launch_pass_t<vdk::kMoore, vdk::kEuclid, false>(ksel, dedup, grid, block, st, pdl, a);
     } else {
-      e = clamp ? launch_pass_t<vdk::kMoore, vdk::kManhattan, true>(ksel, grid, block, st, pdl, a)
-                : launch_pass_t<vdk::kMoore, vdk::kManhattan, false>(ksel, grid, block, st, pdl, a);
+      e = clamp ? launch_pass_t<vdk::kMoore, vdk::kManhattan, true>(ksel, dedup, grid, block, st, pdl, a)
+                : launch_pass_t<vdk::kMoore, vdk::kManhattan, false>(ksel, dedup, grid, block, st, pdl, a);
     }
   } else {
     if (metric == VD_METRIC_EUCLID) {
-      e = clamp ? launch_pass_t<vdk::kVonNeumann, vdk::kEuclid, true>(ksel, grid, block, st, pdl, a)
-                : launch_pass_t<vdk::kVonNeumann, vdk::kEuclid, false>(ksel, grid, block, st, pdl, a);
+      e = clamp ? launch_pass_t<vdk::kVonNeumann, vdk::kEuclid, true>(ksel, dedup, grid, block, st, pdl, a)
+                : launch_pass_t<vdk::kVonNeumann, vdk::kEuclid, false>(ksel, dedup, grid, block, st, pdl, a);
     } else {
-      e = clamp ? launch_pass_t<vdk::kVonNeumann, vdk::kManhattan, true>(ksel, grid, block, st, pdl, a)
-                : launch_pass_t<vdk::kVonNeumann, vdk::kManhattan, false>(ksel, grid, block, st, pdl, a);
+      e = clamp ? launch_pass_t<vdk::kVonNeumann, vdk::kManhattan, true>(ksel, dedup, grid, block, st, pdl, a)
+                : launch_pass_t<vdk::kVonNeumann, vdk::kManhattan, false>(ksel, dedup, grid, block, st, pdl, a);
     }
   }
   if (e != cudaSuccess) return vd_cuda_check(e, "jump pass launch");
@@ -337,7 +346,8 @@ int run_passes(const MapView& m, int32_t* const buf[2], int* cur, const int32_t*
     const int pi = prof ? prof->begin(l.n == 1 ? VD_KERNEL_PASS : VD_KERNEL_FUSED, px * l.n, st) : -1;
     if (l.n == 1) {
       rc = launch_pass(m, src, dst, ks[l.first], nbs[l.first], metric, t.band_min_k,
-                       use_clamp(t.clamp, metric, m.n, ks[l.first], djfa_frame), st, t.pdl != 0);
+                       use_clamp(t.clamp, metric, m.n, ks[l.first], djfa_frame), st, t.pdl != 0,
+                       use_dedup(t.dedup, m.w, m.h, m.n, djfa_frame));
     } else {
       rc = launch_fused(m, src, dst, ks + l.first, nbs + l.first, l.n, metric, t.tile_x, t.tile_y, st);
     }
@@ -347,6 +357,15 @@ int run_passes(const MapView& m, int32_t* const buf[2], int* cur, const int32_t*
     *cur ^= 1;
   }
   return VD_OK;
+}
+
+bool use_dedup(int dedup_option, int32_t w, int32_t h, int32_t n, bool djfa_frame) {
+  if (dedup_option >= 0) return dedup_option == 1;
+  // auto: dJFA passes on maps of at most 256 pixels per seed.  There most
+  // quads straddle a cell boundary and the table outgrows L1, so skipping a
+  // repeated gather saves more than the compares cost; in JFA frames (many
+  // empty and changing labels) and with larger cells it loses.
+  return djfa_frame && static_cast<int64_t>(w) * h <= 256 * static_cast<int64_t>(n);
 }
 
 static int grid1d(int64_t n, int block) { return static_cast<int>((n + block - 1) / block); }
@@ -802,7 +821,7 @@ extern "C" int vd_pass(vd_ctx* c, int32_t k, int32_t nb, int32_t metric) {
   if (nb != VD_NB_MOORE && nb != VD_NB_VON_NEUMANN) return vd_fail(VD_EINVAL, "neighbourhood %d", nb);
   const int rc = vdi::launch_pass(view(c), c->buf[c->cur], c->buf[c->cur ^ 1], k, nb, metric,
                                   c->tune.band_min_k, vdi::use_clamp(c->tune.clamp, metric, c->n, k, false),
-                                  c->stream);
+                                  c->stream, false, vdi::use_dedup(c->tune.dedup, c->w, c->h, c->n, false));
   if (rc) return rc;
   ++c->launches;
   c->cur ^= 1;
@@ -1025,6 +1044,10 @@ extern "C" int vd_set_option(vd_ctx* c, int32_t option, int64_t value) {
       if (value != 0 && value != 1) return vd_fail(VD_EINVAL, "pdl must be 0 or 1");
       t.pdl = static_cast<int>(value);
       break;
+    case VD_OPT_DEDUP_GATHERS:
+      if (value < -1 || value > 1) return vd_fail(VD_EINVAL, "dedup must be -1, 0 or 1");
+      t.dedup = static_cast<int>(value);
+      break;
     default:
       return vd_fail(VD_EINVAL, "unknown option %d", option);
   }
@@ -1048,6 +1071,7 @@ extern "C" int vd_get_option(const vd_ctx* c, int32_t option, int64_t* value) {
     case VD_OPT_PROFILE: *value = c->tune.profile; break;
     case VD_OPT_CLAMPED_KEYS: *value = c->tune.clamp; break;
     case VD_OPT_PDL: *value = c->tune.pdl; break;
+    case VD_OPT_DEDUP_GATHERS: *value = c->tune.dedup; break;
     default: return vd_fail(VD_EINVAL, "unknown option %d", option);
   }
   return VD_OK;

@@ -39,6 +39,7 @@ struct Tuning {
   int profile = 0;
   int clamp = -1;  // clamped 32-bit keys: -1 auto, 0 never, 1 whenever usable
   int pdl = 1;     // chain a frame's kernels with programmatic dependent launch
+  int dedup = -1;  // skip repeated table gathers in a label vector: -1 auto, 0 never, 1 always
 };
 
 // Event pairs bracketing kernel launches (profiling mode).  Records are kept
@@ -78,7 +79,9 @@ int fill_schedule(int32_t first, int32_t vn_waves, int32_t extra, int32_t* ks, i
 std::vector<Launch> plan_passes(const int32_t* ks, const int32_t* nbs, int n, int fuse_max_k,
                                 int max_halo);
 int launch_pass(const MapView& m, const int32_t* src, int32_t* dst, int32_t k, int32_t nb,
-                int32_t metric, int64_t band_min_k, bool clamp, cudaStream_t st, bool pdl = false);
+                int32_t metric, int64_t band_min_k, bool clamp, cudaStream_t st, bool pdl = false,
+                bool dedup = false);
+bool use_dedup(int dedup_option, int32_t w, int32_t h, int32_t n, bool djfa_frame);
 int launch_fused(const MapView& m, const int32_t* src, int32_t* dst, const int32_t* ks,
                  const int32_t* nbs, int n, int32_t metric, int tile_x, int tile_y,
                  cudaStream_t st);

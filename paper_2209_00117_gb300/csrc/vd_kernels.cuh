@@ -128,7 +128,8 @@ struct PassArgs {
 
 // Stops the compiler from hoisting later loads above this point, which keeps
 // only one neighbour group's gathers in flight per thread (the register
-// budget of 6 blocks/SM) and leaves latency hiding to the many resident warps.
+// budget of the pass launch shape) and leaves latency hiding to the many
+// resident warps.
 __device__ __forceinline__ void group_fence() { asm volatile("" ::: "memory"); }
 
 // Programmatic dependent launch.  pdl_trigger lets the next kernel on the
@@ -163,8 +164,9 @@ __host__ __device__ __forceinline__ uint32_t pack_pos(int x, int y) {
 
 // Exact 64-bit form (any metric): packed (key, label), table entries
 // {x | y << 16, x^2 + y^2}.
-template <int METRIC, bool COH>
+template <int METRIC, bool COH, bool DEDUP = false>
 struct Quad {
+  static constexpr bool kDedup = DEDUP;
   long long b[4];
   int m2x, m2y, x0, y;
   const int2* __restrict__ table;
@@ -199,8 +201,9 @@ struct Quad {
 // encodes as (cap - 1, 2^lb - 1): a quad whose best reaches cap - 1 is
 // recomputed with the exact form, so the result never depends on the cap.
 // Prepared position: {s.x, (s.y - y)^2}.
-template <bool COH>
+template <bool COH, bool DEDUP = false>
 struct Quad32 {
+  static constexpr bool kDedup = DEDUP;
   uint32_t b[4];
   int x0, y;
   uint32_t cap, mul;
@@ -232,8 +235,9 @@ struct Quad32 {
 constexpr uint32_t kManhattanMax = 2u * 32767u;
 constexpr int kManhattanFarY = 65535;
 
-template <bool COH>
+template <bool COH, bool DEDUP = false>
 struct Quad32M {
+  static constexpr bool kDedup = DEDUP;
   uint32_t b[4];
   int x0, y;
   uint32_t mul;
@@ -252,12 +256,26 @@ struct Quad32M {
   __device__ __forceinline__ void fold(int i, int2 p, int c) { b[i] = min(b[i], key(i, p, c)); }
 };
 
+// Prepared positions of a label vector.  With Q::kDedup a label equal to its
+// left neighbour in the vector reuses that gather: lanes whose quads lie
+// inside one cell then issue no table load, which pays when cells are small
+// (the table falls out of L1 and most quads straddle a cell boundary) and
+// costs issue slots when cells are large.
 template <class Q>
 __device__ __forceinline__ void gather4(const Q& q, const int4& L, int2 (&p)[4]) {
   p[0] = q.pos(L.x);
-  p[1] = q.pos(L.y);
-  p[2] = q.pos(L.z);
-  p[3] = q.pos(L.w);
+  if (Q::kDedup) {
+    p[1] = p[0];
+    if (L.y != L.x) p[1] = q.pos(L.y);
+    p[2] = p[1];
+    if (L.z != L.y) p[2] = q.pos(L.z);
+    p[3] = p[2];
+    if (L.w != L.z) p[3] = q.pos(L.w);
+  } else {
+    p[1] = q.pos(L.y);
+    p[2] = q.pos(L.z);
+    p[3] = q.pos(L.w);
+  }
 }
 
 template <class Q>
@@ -414,9 +432,9 @@ __device__ __forceinline__ void store_quad(const PassArgs& a, int x0, int y, int
 __device__ __forceinline__ int low_label(long long b) { return static_cast<int>(static_cast<unsigned int>(b)); }
 
 // Exact form (any metric).
-template <int NB, int METRIC, int KSEL, bool COH = false>
+template <int NB, int METRIC, int KSEL, bool COH = false, bool DEDUP = false>
 __device__ __forceinline__ void pass_quad(const PassArgs& a, int x0, int y) {
-  Quad<METRIC, COH> q(a, x0, y);
+  Quad<METRIC, COH, DEDUP> q(a, x0, y);
   fold_all<NB, KSEL, COH>(q, a, x0, y);
   store_quad(a, x0, y, low_label(q.b[0]), low_label(q.b[1]), low_label(q.b[2]), low_label(q.b[3]));
 }
@@ -424,11 +442,11 @@ __device__ __forceinline__ void pass_quad(const PassArgs& a, int x0, int y) {
 // 32-bit forms.  Euclidean: clamped, falling back to the exact form for a
 // quad whose best distance reaches the cap (or that saw only empty labels).
 // Manhattan: exact as is (lb <= 15); an all-empty pixel stays -1.
-template <int NB, int KSEL, bool COH = false, int METRIC = kEuclid>
+template <int NB, int KSEL, bool COH = false, int METRIC = kEuclid, bool DEDUP = false>
 __device__ __forceinline__ void pass_quad_clamped(const PassArgs& a, int x0, int y) {
   const uint32_t mask = a.mul - 1u;
   if (METRIC == kManhattan) {
-    Quad32M<COH> q(a, x0, y);
+    Quad32M<COH, DEDUP> q(a, x0, y);
     fold_all<NB, KSEL, COH>(q, a, x0, y);
     const uint32_t lim = (kManhattanMax + 1u) * a.mul;
     store_quad(a, x0, y, q.b[0] >= lim ? -1 : static_cast<int>(q.b[0] & mask),
@@ -437,23 +455,28 @@ __device__ __forceinline__ void pass_quad_clamped(const PassArgs& a, int x0, int
                q.b[3] >= lim ? -1 : static_cast<int>(q.b[3] & mask));
     return;
   }
-  Quad32<COH> q(a, x0, y);
+  Quad32<COH, DEDUP> q(a, x0, y);
   fold_all<NB, KSEL, COH>(q, a, x0, y);
   const uint32_t lim = (a.cap - 1u) * a.mul;
   if (max(max(q.b[0], q.b[1]), max(q.b[2], q.b[3])) >= lim) {
-    pass_quad<NB, kEuclid, KSEL, COH>(a, x0, y);
+    pass_quad<NB, kEuclid, KSEL, COH, DEDUP>(a, x0, y);
     return;
   }
   store_quad(a, x0, y, static_cast<int>(q.b[0] & mask), static_cast<int>(q.b[1] & mask),
              static_cast<int>(q.b[2] & mask), static_cast<int>(q.b[3] & mask));
 }
 
+// Pass launch shape: 128-thread blocks (64 quads x 2 rows on wide maps), 10
+// resident per SM, which leaves 48 registers a thread: measured on the GB300
+// against 256-thread blocks at 40 and 64 registers, and 64-thread blocks, this
+// is the fastest on every map size tried (1024^2 .. 8192^2).
+constexpr int kPassThreads = 128;
 #ifndef VD_PASS_MIN_BLOCKS
-#define VD_PASS_MIN_BLOCKS 6
+#define VD_PASS_MIN_BLOCKS 10
 #endif
 
-template <int NB, int METRIC, int KSEL, bool CLAMP = false>
-__global__ void __launch_bounds__(256, VD_PASS_MIN_BLOCKS) k_pass(PassArgs a) {
+template <int NB, int METRIC, int KSEL, bool CLAMP = false, bool DEDUP = false>
+__global__ void __launch_bounds__(kPassThreads, VD_PASS_MIN_BLOCKS) k_pass(PassArgs a) {
   pdl_trigger();
   pdl_wait();
   const int x0 = 4 * static_cast<int>(blockIdx.x * blockDim.x + threadIdx.x);
@@ -461,8 +484,8 @@ __global__ void __launch_bounds__(256, VD_PASS_MIN_BLOCKS) k_pass(PassArgs a) {
   if (a.band_m > 1) rb = (blockIdx.y % a.band_t) * a.band_m + blockIdx.y / a.band_t;
   const int y = rb * static_cast<int>(blockDim.y) + static_cast<int>(threadIdx.y);
   if (x0 >= a.pitch || y >= a.h) return;
-  if (CLAMP) pass_quad_clamped<NB, KSEL, false, METRIC>(a, x0, y);
-  else pass_quad<NB, METRIC, KSEL>(a, x0, y);
+  if (CLAMP) pass_quad_clamped<NB, KSEL, false, METRIC, DEDUP>(a, x0, y);
+  else pass_quad<NB, METRIC, KSEL, false, DEDUP>(a, x0, y);
 }
 
 // ---------------------------------------------------------------------------

@@ -23,6 +23,7 @@ OPT_FUSE_TILE_Y = 5
 OPT_PROFILE = 6
 OPT_CLAMPED_KEYS = 7
 OPT_PDL = 8
+OPT_DEDUP_GATHERS = 9
 
 KERNEL_KINDS = ("pass", "fused", "stamp", "move", "fill")
 

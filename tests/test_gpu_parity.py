@@ -277,17 +277,19 @@ def test_invalid_arguments(vd):
     sim.close()
 
 
+@pytest.mark.parametrize("dedup", [0, 1])
 @pytest.mark.parametrize("metric", [E, L1])
 @pytest.mark.parametrize("clamp", [0, 1])
 @pytest.mark.parametrize("w,h,s", [(37, 29, 12), (300, 200, 500), (257, 129, 9), (640, 480, 5000), (64, 64, 8),
                                    (512, 256, 40000)])
-def test_clamped_and_exact_keys(vd, orc, clamp, metric, w, h, s):
-    """Both key forms (forced) give the oracle's maps: single passes over random
-    maps with empty labels and ragged edges, JFA frames and dJFA steps."""
+def test_clamped_and_exact_keys(vd, orc, clamp, metric, dedup, w, h, s):
+    """Both key forms (forced), with and without de-duplicated gathers, give
+    the oracle's maps: single passes over random maps with empty labels and
+    ragged edges, JFA frames and dJFA steps."""
     g = np.random.default_rng(s)
     xy = inputs.uniform_seeds(w, h, s, seed=s + 1)
     xy[-1] = xy[0]
-    sim = _sim(vd, w, h, xy, clamped_keys=clamp)
+    sim = _sim(vd, w, h, xy, clamped_keys=clamp, dedup_gathers=dedup)
     src = g.integers(-1, s, size=(h, w), dtype=np.int32)
     for k in [1, 2, 4, 16, 128]:
         for nb in [M, VN]:
