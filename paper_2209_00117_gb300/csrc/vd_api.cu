@@ -161,22 +161,22 @@ static cudaError_t launch_k(void (*kern)(KArgs...), dim3 g, dim3 b, cudaStream_t
   return cudaLaunchKernelEx(&cfg, kern, args...);
 }
 
-template <int NB, int METRIC, bool CLAMP>
+template <int NB, int METRIC, int KEY>
 static cudaError_t launch_pass_t(int ksel, bool dedup, dim3 g, dim3 b, cudaStream_t st, bool pdl,
                                  const vdk::PassArgs& a) {
   if (dedup) {
     switch (ksel) {
-      case 0: return launch_k(vdk::k_pass<NB, METRIC, 0, CLAMP, true>, g, b, st, pdl, a);
-      case 1: return launch_k(vdk::k_pass<NB, METRIC, 1, CLAMP, true>, g, b, st, pdl, a);
-      case 2: return launch_k(vdk::k_pass<NB, METRIC, 2, CLAMP, true>, g, b, st, pdl, a);
+      case 0: return launch_k(vdk::k_pass<NB, METRIC, 0, KEY, true>, g, b, st, pdl, a);
+      case 1: return launch_k(vdk::k_pass<NB, METRIC, 1, KEY, true>, g, b, st, pdl, a);
+      case 2: return launch_k(vdk::k_pass<NB, METRIC, 2, KEY, true>, g, b, st, pdl, a);
       default: break;  // any other step: scalar loads, never de-duplicated
     }
   }
   switch (ksel) {
-    case 0: return launch_k(vdk::k_pass<NB, METRIC, 0, CLAMP>, g, b, st, pdl, a);
-    case 1: return launch_k(vdk::k_pass<NB, METRIC, 1, CLAMP>, g, b, st, pdl, a);
-    case 2: return launch_k(vdk::k_pass<NB, METRIC, 2, CLAMP>, g, b, st, pdl, a);
-    default: return launch_k(vdk::k_pass<NB, METRIC, 3, CLAMP>, g, b, st, pdl, a);
+    case 0: return launch_k(vdk::k_pass<NB, METRIC, 0, KEY>, g, b, st, pdl, a);
+    case 1: return launch_k(vdk::k_pass<NB, METRIC, 1, KEY>, g, b, st, pdl, a);
+    case 2: return launch_k(vdk::k_pass<NB, METRIC, 2, KEY>, g, b, st, pdl, a);
+    default: return launch_k(vdk::k_pass<NB, METRIC, 3, KEY>, g, b, st, pdl, a);
   }
 }
 
@@ -190,16 +190,16 @@ bool use_clamp(int clamp_option, int32_t metric, int32_t n, int32_t k, bool djfa
   (void)k;
   if (clamp_option == 0) return false;
   const int lb = label_bits(n);
-  if (metric == VD_METRIC_MANHATTAN) {
+  if (metric == VD_METRIC_MANHATTAN && lb <= 15) {
     // exact without a cap while d * 2^lb + label fits: every pass may use it
-    return lb <= 15;
+    return true;
   }
   if (lb < 4) return false;
   if (clamp_option == 1) return true;
-  // Euclidean auto: dJFA passes only.  The previous map is nearly right
-  // there, so quads almost never reach the cap; in a JFA frame the early
-  // passes still see many empty pixels, whose quads would be recomputed with
-  // the exact form.
+  // Clamped keys (Euclidean; Manhattan beyond 2^15 labels), auto: dJFA
+  // passes only.  The previous map is nearly right there, so quads almost
+  // never reach the cap; in a JFA frame the early passes still see many empty
+  // pixels, whose quads would be recomputed with the exact form.
   return djfa_frame;
 }
 
@@ -241,24 +241,30 @@ int launch_pass(const MapView& m, const int32_t* src, int32_t* dst, int32_t k, i
     grid.y = a.band_m * a.band_t;
   }
   const int ksel = (k % 4 == 0) ? 0 : (k == 1 ? 1 : (k == 2 ? 2 : 3));
-  if (clamp && metric == VD_METRIC_EUCLID && a.cap == 0) clamp = false;
-  if (clamp && metric == VD_METRIC_MANHATTAN && label_bits(m.n) > 15) clamp = false;
+  // key form: 0 exact 64-bit, 1 32-bit, 2 clamped Manhattan 32-bit
+  int key = 0;
+  if (clamp) {
+    if (metric == VD_METRIC_MANHATTAN) key = label_bits(m.n) <= 15 ? 1 : 2;
+    else if (a.cap != 0) key = 1;
+  }
   cudaError_t e;
   if (nb == VD_NB_MOORE) {
     if (metric == VD_METRIC_EUCLID) {
-      e = clamp ? launch_pass_t<vdk::kMoore, vdk::kEuclid, true>(ksel, dedup, grid, block, st, pdl, a)
-                : launch_pass_t<vdk::kMoore, vdk::kEuclid, false>(ksel, dedup, grid, block, st, pdl, a);
+      e = key ? launch_pass_t<vdk::kMoore, vdk::kEuclid, 1>(ksel, dedup, grid, block, st, pdl, a)
+              : launch_pass_t<vdk::kMoore, vdk::kEuclid, 0>(ksel, dedup, grid, block, st, pdl, a);
     } else {
-      e = clamp ? launch_pass_t<vdk::kMoore, vdk::kManhattan, true>(ksel, dedup, grid, block, st, pdl, a)
-                : launch_pass_t<vdk::kMoore, vdk::kManhattan, false>(ksel, dedup, grid, block, st, pdl, a);
+      e = key == 2 ? launch_pass_t<vdk::kMoore, vdk::kManhattan, 2>(ksel, dedup, grid, block, st, pdl, a)
+          : key    ? launch_pass_t<vdk::kMoore, vdk::kManhattan, 1>(ksel, dedup, grid, block, st, pdl, a)
+                   : launch_pass_t<vdk::kMoore, vdk::kManhattan, 0>(ksel, dedup, grid, block, st, pdl, a);
     }
   } else {
     if (metric == VD_METRIC_EUCLID) {
-      e = clamp ? launch_pass_t<vdk::kVonNeumann, vdk::kEuclid, true>(ksel, dedup, grid, block, st, pdl, a)
-                : launch_pass_t<vdk::kVonNeumann, vdk::kEuclid, false>(ksel, dedup, grid, block, st, pdl, a);
+      e = key ? launch_pass_t<vdk::kVonNeumann, vdk::kEuclid, 1>(ksel, dedup, grid, block, st, pdl, a)
+              : launch_pass_t<vdk::kVonNeumann, vdk::kEuclid, 0>(ksel, dedup, grid, block, st, pdl, a);
     } else {
-      e = clamp ? launch_pass_t<vdk::kVonNeumann, vdk::kManhattan, true>(ksel, dedup, grid, block, st, pdl, a)
-                : launch_pass_t<vdk::kVonNeumann, vdk::kManhattan, false>(ksel, dedup, grid, block, st, pdl, a);
+      e = key == 2 ? launch_pass_t<vdk::kVonNeumann, vdk::kManhattan, 2>(ksel, dedup, grid, block, st, pdl, a)
+          : key    ? launch_pass_t<vdk::kVonNeumann, vdk::kManhattan, 1>(ksel, dedup, grid, block, st, pdl, a)
+                   : launch_pass_t<vdk::kVonNeumann, vdk::kManhattan, 0>(ksel, dedup, grid, block, st, pdl, a);
     }
   }
   if (e != cudaSuccess) return vd_cuda_check(e, "jump pass launch");

@@ -34,6 +34,7 @@ struct SimDesc {
   uint32_t* ptable;  // packed positions, entry 0 = far position; used as ptable + 1
   uint32_t cap, mul;       // clamped-key parameters (cap = 0: unusable)
   uint32_t clampmask[2];   // bit r: pass r of the schedule uses clamped keys
+  int dedup[2];            // 1: the schedule's passes de-duplicate repeated table gathers
   int seed_off;
   int cur;
   long long step;      // moves drawn so far (the RNG step of the next move)
@@ -161,6 +162,39 @@ __device__ __forceinline__ void stamp_min_block(const BatchArgs& A, int sb) {
             static_cast<unsigned int>(k));
 }
 
+// One quad of a pass in a 32-bit key form, dispatched on the neighbourhood and step.
+template <int METRIC, bool COH, bool DEDUP, bool MCAP>
+__device__ __forceinline__ void tile_quad32(const vdk::PassArgs& a, int x0, int y, int nb, int ksel) {
+  switch (nb * 4 + ksel) {
+    case 0: vdk::pass_quad_clamped<vdk::kMoore, 0, COH, METRIC, DEDUP, MCAP>(a, x0, y); break;
+    case 1: vdk::pass_quad_clamped<vdk::kMoore, 1, COH, METRIC, DEDUP, MCAP>(a, x0, y); break;
+    case 2: vdk::pass_quad_clamped<vdk::kMoore, 2, COH, METRIC, DEDUP, MCAP>(a, x0, y); break;
+    case 4: vdk::pass_quad_clamped<vdk::kVonNeumann, 0, COH, METRIC, DEDUP, MCAP>(a, x0, y); break;
+    case 5: vdk::pass_quad_clamped<vdk::kVonNeumann, 1, COH, METRIC, DEDUP, MCAP>(a, x0, y); break;
+    default: vdk::pass_quad_clamped<vdk::kVonNeumann, 2, COH, METRIC, DEDUP, MCAP>(a, x0, y); break;
+  }
+}
+
+// One quad of a pass, dispatched on the key form, neighbourhood and step
+// (mcap: the clamped Manhattan form, for more than 2^15 labels).
+template <int METRIC, bool COH, bool DEDUP>
+__device__ __forceinline__ void tile_quad(const vdk::PassArgs& a, int x0, int y, bool clamp, bool mcap, int nb,
+                                          int ksel) {
+  if (clamp) {
+    if (METRIC == vdk::kManhattan && mcap) tile_quad32<METRIC, COH, DEDUP, true>(a, x0, y, nb, ksel);
+    else tile_quad32<METRIC, COH, DEDUP, false>(a, x0, y, nb, ksel);
+    return;
+  }
+  switch (nb * 4 + ksel) {
+    case 0: vdk::pass_quad<vdk::kMoore, METRIC, 0, COH, DEDUP>(a, x0, y); break;
+    case 1: vdk::pass_quad<vdk::kMoore, METRIC, 1, COH, DEDUP>(a, x0, y); break;
+    case 2: vdk::pass_quad<vdk::kMoore, METRIC, 2, COH, DEDUP>(a, x0, y); break;
+    case 4: vdk::pass_quad<vdk::kVonNeumann, METRIC, 0, COH, DEDUP>(a, x0, y); break;
+    case 5: vdk::pass_quad<vdk::kVonNeumann, METRIC, 1, COH, DEDUP>(a, x0, y); break;
+    default: vdk::pass_quad<vdk::kVonNeumann, METRIC, 2, COH, DEDUP>(a, x0, y); break;
+  }
+}
+
 template <int METRIC, bool COH>
 __device__ __forceinline__ void round_tile(const BatchArgs& A, int r, int t) {
   // the entry holding tile t: the last one whose first tile is <= t
@@ -195,28 +229,13 @@ __device__ __forceinline__ void round_tile(const BatchArgs& A, int r, int t) {
   const int ksel = (k == 1) ? 1 : (k == 2 ? 2 : 0);
   const bool clamp = (sd->clampmask[A.sched] >> r) & 1u;
   const int rows = 4 * A.rows_per_thread;
+  const bool dedup = sd->dedup[A.sched] != 0;
+  const bool mcap = sd->mul > (1u << 15);
   for (int i = 0; i < A.rows_per_thread; ++i) {
     const int y = ty * rows + static_cast<int>(threadIdx.x / kQuadsX) + 4 * i;
     if (x0 >= a.pitch || y >= a.h) continue;
-    if (clamp) {
-      switch (nb * 4 + ksel) {
-        case 0: vdk::pass_quad_clamped<vdk::kMoore, 0, COH, METRIC>(a, x0, y); break;
-        case 1: vdk::pass_quad_clamped<vdk::kMoore, 1, COH, METRIC>(a, x0, y); break;
-        case 2: vdk::pass_quad_clamped<vdk::kMoore, 2, COH, METRIC>(a, x0, y); break;
-        case 4: vdk::pass_quad_clamped<vdk::kVonNeumann, 0, COH, METRIC>(a, x0, y); break;
-        case 5: vdk::pass_quad_clamped<vdk::kVonNeumann, 1, COH, METRIC>(a, x0, y); break;
-        default: vdk::pass_quad_clamped<vdk::kVonNeumann, 2, COH, METRIC>(a, x0, y); break;
-      }
-      continue;
-    }
-    switch (nb * 4 + ksel) {
-      case 0: vdk::pass_quad<vdk::kMoore, METRIC, 0, COH>(a, x0, y); break;
-      case 1: vdk::pass_quad<vdk::kMoore, METRIC, 1, COH>(a, x0, y); break;
-      case 2: vdk::pass_quad<vdk::kMoore, METRIC, 2, COH>(a, x0, y); break;
-      case 4: vdk::pass_quad<vdk::kVonNeumann, METRIC, 0, COH>(a, x0, y); break;
-      case 5: vdk::pass_quad<vdk::kVonNeumann, METRIC, 1, COH>(a, x0, y); break;
-      default: vdk::pass_quad<vdk::kVonNeumann, METRIC, 2, COH>(a, x0, y); break;
-    }
+    if (dedup) tile_quad<METRIC, COH, true>(a, x0, y, clamp, mcap, nb, ksel);
+    else tile_quad<METRIC, COH, false>(a, x0, y, clamp, mcap, nb, ksel);
   }
 }
 
@@ -235,7 +254,7 @@ static __global__ void __launch_bounds__(kThreads) k_batch_move_mark(BatchArgs A
 static __global__ void __launch_bounds__(kThreads) k_batch_min(BatchArgs A) { stamp_min_block(A, blockIdx.x); }
 
 template <int METRIC>
-__global__ void __launch_bounds__(kThreads, 6) k_batch_round(BatchArgs A, int r) {
+__global__ void __launch_bounds__(kThreads, 5) k_batch_round(BatchArgs A, int r) {
   round_tile<METRIC, false>(A, r, blockIdx.x);
 }
 
@@ -311,6 +330,8 @@ inline HostPlan make_plan(const std::vector<SimDesc>& sims, const std::vector<in
 
 // Clamped-key parameters and per-pass choices of one simulation for one
 // schedule (sched 0 = dJFA, 1 = JFA) under `metric`.
+// Per-schedule key form (clamped 32-bit or exact, per pass) and gather
+// de-duplication (the single-simulation auto rules).
 inline void set_clamp(SimDesc& s, int sched, int32_t metric, int clamp_option) {
   const int lb = vdi::label_bits(s.n);
   s.mul = lb >= 32 ? 0u : (1u << lb);
@@ -319,6 +340,7 @@ inline void set_clamp(SimDesc& s, int sched, int32_t metric, int clamp_option) {
   for (int r = 0; r < s.n_pass[sched] && r < 32; ++r)
     if (vdi::use_clamp(clamp_option, metric, s.n, s.ks[sched][r], sched == 0)) mask |= 1u << r;
   s.clampmask[sched] = mask;
+  s.dedup[sched] = vdi::use_dedup(-1, s.w, s.h, s.n, sched == 0) ? 1 : 0;
 }
 
 // A pinned host staging buffer and a device buffer for one plan.

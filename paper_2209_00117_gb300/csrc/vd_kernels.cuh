@@ -224,33 +224,36 @@ struct Quad32 {
   __device__ __forceinline__ void fold(int i, int2 p, int c) { b[i] = min(b[i], key(i, p, c)); }
 };
 
-// Manhattan 32-bit form: distances are at most 2 * 32767 < 2^17, so with
+// Manhattan 32-bit forms: distances are at most 2 * 32767 < 2^17, so with
 // every label below 2^lb, lb <= 15, key = d * 2^lb + label is exact without a
 // cap.  Prepared position: {s.x, |s.y - y|}; an empty label takes the far
 // position's x (kFarX) and the y-term kManhattanFarY, which puts it at
 // distance [81919, 114686] from every pixel: above every real distance, below
 // 2^17, and (its label wrapping to -1) at a key of at least
 // (kManhattanMax + 1) * 2^lb, so a pixel whose best is such a key has no
-// candidate at all.
+// candidate at all.  With more labels (CAP) the key is clamped like the
+// Euclidean one, min(d, cap) * 2^lb + label with cap = 2^(32 - lb) - 1 <
+// 81919, and a quad whose best reaches cap - 1 is recomputed exactly.
 constexpr uint32_t kManhattanMax = 2u * 32767u;
 constexpr int kManhattanFarY = 65535;
 
-template <bool COH, bool DEDUP = false>
+template <bool COH, bool DEDUP = false, bool CAP = false>
 struct Quad32M {
   static constexpr bool kDedup = DEDUP;
   uint32_t b[4];
   int x0, y;
-  uint32_t mul;
+  uint32_t cap, mul;
   const uint32_t* __restrict__ ptable;
   __device__ __forceinline__ Quad32M(const PassArgs& a, int x0_, int y_)
-      : x0(x0_), y(y_), mul(a.mul), ptable(a.ptable) {}
+      : x0(x0_), y(y_), cap(a.cap), mul(a.mul), ptable(a.ptable) {}
   __device__ __forceinline__ int2 pos(int c) const {
     const uint32_t e = COH ? __ldcg(&ptable[c]) : __ldg(&ptable[c]);
     const int ady = c < 0 ? kManhattanFarY : abs(static_cast<int>(e >> 16) - y);
     return make_int2(static_cast<int>(e & 0xFFFFu), ady);
   }
   __device__ __forceinline__ uint32_t key(int i, int2 p, int c) const {
-    return static_cast<uint32_t>(abs(p.x - (x0 + i)) + p.y) * mul + static_cast<uint32_t>(c);
+    const uint32_t d = static_cast<uint32_t>(abs(p.x - (x0 + i)) + p.y);
+    return (CAP ? min(d, cap) : d) * mul + static_cast<uint32_t>(c);
   }
   __device__ __forceinline__ void set(int i, int2 p, int c) { b[i] = key(i, p, c); }
   __device__ __forceinline__ void fold(int i, int2 p, int c) { b[i] = min(b[i], key(i, p, c)); }
@@ -439,12 +442,25 @@ __device__ __forceinline__ void pass_quad(const PassArgs& a, int x0, int y) {
   store_quad(a, x0, y, low_label(q.b[0]), low_label(q.b[1]), low_label(q.b[2]), low_label(q.b[3]));
 }
 
-// 32-bit forms.  Euclidean: clamped, falling back to the exact form for a
-// quad whose best distance reaches the cap (or that saw only empty labels).
-// Manhattan: exact as is (lb <= 15); an all-empty pixel stays -1.
-template <int NB, int KSEL, bool COH = false, int METRIC = kEuclid, bool DEDUP = false>
+// 32-bit forms.  Euclidean, and Manhattan with MCAP (more than 2^15 labels):
+// clamped, falling back to the exact form for a quad whose best distance
+// reaches the cap (or that saw only empty labels).  Manhattan without MCAP:
+// exact as is (lb <= 15); an all-empty pixel stays -1.
+template <int NB, int KSEL, bool COH = false, int METRIC = kEuclid, bool DEDUP = false, bool MCAP = false>
 __device__ __forceinline__ void pass_quad_clamped(const PassArgs& a, int x0, int y) {
   const uint32_t mask = a.mul - 1u;
+  if (METRIC == kManhattan && MCAP) {
+    Quad32M<COH, DEDUP, true> q(a, x0, y);
+    fold_all<NB, KSEL, COH>(q, a, x0, y);
+    const uint32_t lim = (a.cap - 1u) * a.mul;
+    if (max(max(q.b[0], q.b[1]), max(q.b[2], q.b[3])) >= lim) {
+      pass_quad<NB, kManhattan, KSEL, COH, DEDUP>(a, x0, y);
+      return;
+    }
+    store_quad(a, x0, y, static_cast<int>(q.b[0] & mask), static_cast<int>(q.b[1] & mask),
+               static_cast<int>(q.b[2] & mask), static_cast<int>(q.b[3] & mask));
+    return;
+  }
   if (METRIC == kManhattan) {
     Quad32M<COH, DEDUP> q(a, x0, y);
     fold_all<NB, KSEL, COH>(q, a, x0, y);
@@ -475,7 +491,9 @@ constexpr int kPassThreads = 128;
 #define VD_PASS_MIN_BLOCKS 10
 #endif
 
-template <int NB, int METRIC, int KSEL, bool CLAMP = false, bool DEDUP = false>
+// KEY: 0 the exact 64-bit form, 1 the 32-bit form of METRIC, 2 the clamped
+// Manhattan 32-bit form (more than 2^15 labels).
+template <int NB, int METRIC, int KSEL, int KEY = 0, bool DEDUP = false>
 __global__ void __launch_bounds__(kPassThreads, VD_PASS_MIN_BLOCKS) k_pass(PassArgs a) {
   pdl_trigger();
   pdl_wait();
@@ -484,7 +502,7 @@ __global__ void __launch_bounds__(kPassThreads, VD_PASS_MIN_BLOCKS) k_pass(PassA
   if (a.band_m > 1) rb = (blockIdx.y % a.band_t) * a.band_m + blockIdx.y / a.band_t;
   const int y = rb * static_cast<int>(blockDim.y) + static_cast<int>(threadIdx.y);
   if (x0 >= a.pitch || y >= a.h) return;
-  if (CLAMP) pass_quad_clamped<NB, KSEL, false, METRIC, DEDUP>(a, x0, y);
+  if (KEY != 0) pass_quad_clamped<NB, KSEL, false, METRIC, DEDUP, KEY == 2>(a, x0, y);
   else pass_quad<NB, METRIC, KSEL, false, DEDUP>(a, x0, y);
 }
 

@@ -220,3 +220,29 @@ def test_batched256_full_size_sample(vd):
         want, _ = _alone_rng(vd, shapes[i], xys[i], i, steps, D, rng)
         np.testing.assert_array_equal(b.labels(i), want, err_msg=f"sim {i} {shapes[i]}")
     b.close()
+
+
+@pytest.mark.parametrize("metric", [0, 1])
+def test_batch_many_labels_equal_oracle(vd, orc, metric):
+    """Simulations with more than 2^15 seeds (clamped 32-bit keys in both
+    metrics, de-duplicated gathers at a few pixels per seed) next to small ones
+    equal the oracle step by step."""
+    D, steps = 3, 3
+    shapes = [(600, 400, 40000), (512, 512, 70000), (300, 211, 700), (97, 61, 50)]
+    xys = _seeds(shapes, 90)
+    b = vd.VoronoiBatch(shapes)
+    b.set_seeds(np.concatenate(xys))
+    b.jfa(metric=metric)
+    b.configure(d_max=D, metric=metric)
+    labs = [orc.jfa(w, h, xy, metric=metric) for (w, h, _), xy in zip(shapes, xys)]
+    for i in range(len(shapes)):
+        np.testing.assert_array_equal(b.labels(i), labs[i], err_msg=f"frame 0 sim {i}")
+    for t in range(steps):
+        moves = [inputs.step_displacements(s, D, t, seed=300 + i) for i, (_, _, s) in enumerate(shapes)]
+        b.step(np.concatenate(moves))
+        for i, (w, h, _) in enumerate(shapes):
+            xys[i] = orc.move(w, h, xys[i], moves[i])
+            labs[i] = orc.djfa_step(w, h, xys[i], labs[i], d_max=D, metric=metric)
+    for i in range(len(shapes)):
+        np.testing.assert_array_equal(b.labels(i), labs[i], err_msg=f"sim {i} {shapes[i]}")
+    b.close()
