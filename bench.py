@@ -217,13 +217,21 @@ def recorded_traffic(kind, workload_name):
 # the CPU oracle (baseline leg and reference arm)
 # ---------------------------------------------------------------------------
 
-def cpu_oracle_run(name, steps, seconds, seed=0, warmup=0):
+def cpu_oracle_run(name, steps, seconds, seed=0, warmup=0, threads=None):
     """Times oracle dJFA steps on the host cores on the same trajectory; stops
-    after `steps` timed steps or `seconds` of timed work, whichever first."""
+    after `steps` timed steps or `seconds` of timed work, whichever first.
+    `threads` limits the oracle's OpenMP threads for this run (None: all)."""
     import oracle
     from paper_2209_00117_gb300 import inputs
 
     oracle.build()
+    if threads is not None:
+        prev = oracle.get_threads()
+        oracle.set_threads(threads)
+        try:
+            return cpu_oracle_run(name, steps, seconds, seed=seed, warmup=warmup)
+        finally:
+            oracle.set_threads(prev)
     w, h, s, _, d = workload(name)
     xy = inputs.uniform_seeds(w, h, s, seed=seed)
     total = warmup + steps
@@ -448,6 +456,10 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         res = cpu_oracle_run(args.workload, K, args.cpu_seconds, seed=0)
         cpu = {k: res[k] for k in ("value", "unit", "cores", "kind", "sample")}
+        cpu["ms_per_step"] = res["ms_per_step"]
+        # the same oracle on one core, a shorter bounded sample
+        one = cpu_oracle_run(args.workload, K, args.cpu_seconds / 3, seed=0, threads=1)
+        cpu["single_thread"] = {"value": one["value"], "ms_per_step": one["ms_per_step"], "steps": one["steps"]}
 
     last = sims[-1] if sims else (0, 0, 0, 0)
     similarity = {

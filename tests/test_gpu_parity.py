@@ -235,20 +235,40 @@ def test_single2048_full_size(vd, orc):
     sim.close()
 
 
-@pytest.mark.parametrize("s,D", [(1 << 14, 4), (1 << 22, 16)])
-def test_sweep8192_first_frames(vd, orc, s, D):
+@pytest.mark.parametrize("s,D,metric", [(1 << 14, 4, E), (1 << 22, 16, E), (1 << 22, 16, L1)])
+def test_sweep8192_first_frames(vd, orc, s, D, metric):
     """8192 x 8192 sweep points: JFA frame 0 and dJFA frame 1 bit-exact."""
     w = h = inputs.SWEEP8192["side"]
     xy = inputs.uniform_seeds(w, h, s, seed=1)
     disp = inputs.displacements(s, D, 1, seed=1)[0]
     sim = _sim(vd, w, h, xy)
-    sim.jfa()
-    lab = orc.jfa(w, h, xy)
+    sim.jfa(metric=metric)
+    lab = orc.jfa(w, h, xy, metric=metric)
     assert np.array_equal(sim.labels(), lab)
     sim.move(disp)
-    sim.djfa_step(d_max=D)
+    sim.djfa_step(d_max=D, metric=metric)
     xy = orc.move(w, h, xy, disp)
-    lab = orc.djfa_step(w, h, xy, lab, d_max=D)
+    lab = orc.djfa_step(w, h, xy, lab, d_max=D, metric=metric)
+    assert np.array_equal(sim.labels(), lab)
+    sim.close()
+
+
+def test_sweep8192_frame49(vd, orc):
+    """8192 x 8192, 2^18 seeds, D = 4 (de-duplicated gathers, clamped keys, 6
+    passes a frame): the dJFA chain stays bit-exact through frame 49, the last
+    frame of a 50-step sweep run, with counter-based moves on both sides."""
+    w = h = inputs.SWEEP8192["side"]
+    s, D, rng = 1 << 18, 4, 2209
+    xy = inputs.uniform_seeds(w, h, s, seed=49)
+    sim = _sim(vd, w, h, xy, use_graphs=1)
+    sim.jfa()
+    lab = orc.jfa(w, h, xy)
+    for t in range(49):
+        sim.move(None, max_disp=D, rng_seed=rng, stream_id=0, step=t)
+        sim.djfa_step(d_max=D)
+        xy = orc.move_rng(w, h, xy, D, rng, 0, t)
+        lab = orc.djfa_step(w, h, xy, lab, d_max=D)
+    np.testing.assert_array_equal(sim.get_seeds(), xy)
     assert np.array_equal(sim.labels(), lab)
     sim.close()
 
