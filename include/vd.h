@@ -438,12 +438,14 @@ int vd_server_set_max_batch(vd_server* server, int32_t max_batch);
 #define VD_OPT_FUSE_TILE_Y 5     /* fused-group tile height in pixels (1..128) */
 #define VD_OPT_PROFILE 6         /* 1 = bracket every kernel launch with CUDA events (frames then run
                                     eagerly, never from a graph); read with vd_profile_read */
-#define VD_OPT_CLAMPED_KEYS 7    /* passes with one 32-bit key per candidate, both exact:
-                                    Euclidean min(d^2, cap) * 2^lb + label (quads that reach the cap
-                                    are recomputed with the 64-bit key; usable with >= 9 seeds),
-                                    Manhattan d * 2^lb + label (no cap; usable with <= 32768 seeds).
-                                    -1 = auto (default: Euclidean dJFA passes, every Manhattan pass),
-                                    0 = never, 1 = always when usable */
+#define VD_OPT_CLAMPED_KEYS 7    /* passes with one 32-bit key per candidate, all exact:
+                                    Euclidean min(d^2, cap) * 2^lb + label and, beyond 32768 seeds,
+                                    Manhattan min(d, cap) * 2^lb + label (cap = 2^(32 - lb) - 1; quads
+                                    that reach the cap are recomputed with the 64-bit key; usable
+                                    with >= 9 seeds); up to 32768 seeds Manhattan d * 2^lb + label
+                                    (no cap).  -1 = auto (default: clamped keys for dJFA passes, the
+                                    uncapped Manhattan key for every pass), 0 = never, 1 = always
+                                    when usable */
 #define VD_OPT_PDL 8             /* 1 (default) = a frame's stamp and pass kernels are chained with
                                     programmatic dependent launch: each may be scheduled while its
                                     predecessor drains and waits for it on the device before touching
