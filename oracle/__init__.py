@@ -85,6 +85,8 @@ def _load():
             "orc_jfa": (None, [i32, i32, i64, p, c_int, c_int, p]),
             "orc_djfa_step": (None, [i32, i32, i64, p, i32, c_int, c_int, c_int, p]),
             "orc_similarity": (None, [i32, i32, p, p, p, p, c_int, p, p]),
+            "orc_update_seeds": (i64, [i32, i32, i64, p, p, p, i64, p, i64, p]),
+            "orc_repair_step": (None, [i32, i32, i64, p, c_int, c_int, p]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -226,6 +228,31 @@ def djfa_step(w: int, h: int, xy, prev_label, d_max: int, vn_waves: int = 2,
     label = _map(prev_label, w, h).copy()
     _load().orc_djfa_step(w, h, len(xy), _ptr(xy), d_max, vn_waves, extra, metric, _ptr(label))
     return label
+
+
+def update_seeds(w: int, h: int, xy, label, remove=(), add=()):
+    """Seed removal and insertion between frames (this library's rule; the
+    paper leaves it to future work): survivors keep their order, new seeds are
+    appended, the map is relabelled (a removed seed's pixels become -1).
+    Returns (new seeds, new map), or None when the update is invalid."""
+    xy = _seeds(xy)
+    label = _map(label, w, h).copy()
+    rem = np.ascontiguousarray(remove, dtype=np.int32).reshape(-1)
+    add = np.ascontiguousarray(add, dtype=np.int32).reshape(-1, 2)
+    out = np.empty((max(len(xy) + len(add), 1), 2), np.int32)
+    n = _load().orc_update_seeds(w, h, len(xy), _ptr(xy), _ptr(label), _ptr(rem), len(rem),
+                                 _ptr(add), len(add), _ptr(out))
+    if n < 0:
+        return None
+    return out[:n].copy(), label
+
+
+def repair_step(w: int, h: int, xy, label, extra: int = 0, metric=EUCLID) -> np.ndarray:
+    """The frame after a removal: stamp, then the full JFA schedule on the map."""
+    xy = _seeds(xy)
+    out = _map(label, w, h).copy()
+    _load().orc_repair_step(w, h, len(xy), _ptr(xy), extra, metric, _ptr(out))
+    return out
 
 
 def similarity(w: int, h: int, xy, label, exact_dist=None, ref_label=None, metric=EUCLID):

@@ -28,7 +28,10 @@
  *
  * Parity status: every function below is pinned by a test that does not
  * re-type its formula (brute force, library distance transforms, closed
- * forms, invariants, the worked example of Section III).
+ * forms, invariants, the worked example of Section III).  The seed update
+ * and the repair frame follow a rule of this library's own (the paper leaves
+ * insertion and removal to future work): they are pinned by invariants and
+ * by the cases that reduce to brute force, not by anything the paper prints.
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -493,6 +496,77 @@ void orc_djfa_step(int32_t w, int32_t h, int64_t s, const int32_t* xy, int32_t d
                    int vn_waves, int extra, int metric, int32_t* label) {
     int32_t ks[80], nbs[80];
     int n = orc_djfa_schedule(w, h, s, d_max, vn_waves, extra, ks, nbs, 80);
+    orc_stamp(w, h, s, xy, label);
+    orc_run_passes(w, h, xy, label, ks, nbs, n, metric);
+}
+
+/* ------------------------------------------------------------------------ */
+/* seed insertion and removal (Section V leaves it to future work; the rule   */
+/* below is this library's reading, pinned by the invariants in the tests)    */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * Seed update between frames: the seeds listed in `remove` (distinct indices
+ * in [0, s)) leave, the survivors keep their order and are renumbered
+ * 0 .. s_keep - 1, and the n_add seeds of `add` follow as s_keep, s_keep + 1,
+ * ...  The map is relabelled to match: a pixel labelled with a surviving seed
+ * takes that seed's new index, a pixel labelled with a removed seed becomes
+ * empty (-1).  Writes the new seed array to out_xy and returns its length;
+ * returns -1 (and changes nothing) when `remove` holds an index out of range
+ * or twice, an added seed lies outside the grid, or no seed would remain.
+ */
+int64_t orc_update_seeds(int32_t w, int32_t h, int64_t s, const int32_t* xy, int32_t* label,
+                         const int32_t* remove, int64_t n_remove, const int32_t* add, int64_t n_add,
+                         int32_t* out_xy) {
+    if (n_remove < 0 || n_add < 0 || s - n_remove + n_add < 1) return -1;
+    for (int64_t j = 0; j < n_add; j++) {
+        if (add[2 * j] < 0 || add[2 * j] >= w || add[2 * j + 1] < 0 || add[2 * j + 1] >= h) return -1;
+    }
+    char* gone = (char*)calloc((size_t)(s > 0 ? s : 1), 1);
+    for (int64_t j = 0; j < n_remove; j++) {
+        int32_t id = remove[j];
+        if (id < 0 || id >= s || gone[id]) {
+            free(gone);
+            return -1;
+        }
+        gone[id] = 1;
+    }
+    /* the survivors' new indices, in their old order */
+    int32_t* renum = (int32_t*)malloc(sizeof(int32_t) * (size_t)(s > 0 ? s : 1));
+    int64_t kept = 0;
+    for (int64_t k = 0; k < s; k++) {
+        if (gone[k]) {
+            renum[k] = -1;
+        } else {
+            renum[k] = (int32_t)kept;
+            out_xy[2 * kept] = xy[2 * k];
+            out_xy[2 * kept + 1] = xy[2 * k + 1];
+            kept++;
+        }
+    }
+    for (int64_t j = 0; j < n_add; j++) {
+        out_xy[2 * (kept + j)] = add[2 * j];
+        out_xy[2 * (kept + j) + 1] = add[2 * j + 1];
+    }
+    int64_t npx = (int64_t)w * h;
+    for (int64_t i = 0; i < npx; i++) {
+        if (label[i] >= 0) label[i] = renum[label[i]];
+    }
+    free(renum);
+    free(gone);
+    return kept + n_add;
+}
+
+/*
+ * The frame after a removal: the current seeds are stamped onto the
+ * relabelled map and the full JFA schedule (Eq. 2, Moore, plus `extra`
+ * passes) runs on it without clearing, so the emptied cells fill from every
+ * side whatever their size.
+ */
+void orc_repair_step(int32_t w, int32_t h, int64_t s, const int32_t* xy, int extra, int metric,
+                     int32_t* label) {
+    int32_t ks[80], nbs[80];
+    int n = orc_jfa_schedule(w, h, extra, ks, nbs, 80);
     orc_stamp(w, h, s, xy, label);
     orc_run_passes(w, h, xy, label, ks, nbs, n, metric);
 }

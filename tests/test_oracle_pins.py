@@ -385,3 +385,109 @@ def test_djfa_similarity_level_single256(orc):
         ref = orc.jfa(w, h, xy)
         _, nm = orc.similarity(w, h, xy, lab, ref_label=ref)
         assert nm >= 0.99 * w * h, (t, nm / (w * h))
+
+
+# --------------------------------------------------------------------------
+# Seed insertion and removal (future work in Section V; the library's rule)
+# --------------------------------------------------------------------------
+
+def _random_update(g, w, h, s, n_remove, n_add):
+    remove = g.choice(s, size=n_remove, replace=False).astype(np.int32)
+    add = np.stack([g.integers(0, w, n_add), g.integers(0, h, n_add)], axis=1).astype(np.int32)
+    return remove, add
+
+
+def test_update_without_changes_is_identity(orc):
+    w, h, s = 41, 29, 30
+    xy = inputs.uniform_seeds(w, h, s, seed=21)
+    lab = orc.jfa(w, h, xy)
+    new_xy, new_lab = orc.update_seeds(w, h, xy, lab)
+    np.testing.assert_array_equal(new_xy, xy)
+    np.testing.assert_array_equal(new_lab, lab)
+
+
+@pytest.mark.parametrize("trial", range(6))
+def test_update_relabels_by_position_and_order(orc, trial):
+    """Every labelled pixel keeps the same seed position (its seed survived) or
+    becomes empty (its seed left); survivors keep their relative order; new
+    seeds follow them in the order given."""
+    g = np.random.default_rng(40 + trial)
+    w, h, s = int(g.integers(5, 60)), int(g.integers(5, 60)), int(g.integers(2, 80))
+    xy = inputs.uniform_seeds(w, h, s, seed=trial)
+    lab = orc.jfa(w, h, xy)
+    remove, add = _random_update(g, w, h, s, int(g.integers(0, s)), int(g.integers(0, 20)))
+    new_xy, new_lab = orc.update_seeds(w, h, xy, lab, remove, add)
+    gone = np.zeros(s, bool)
+    gone[remove] = True
+    survivors = np.flatnonzero(~gone)
+    assert len(new_xy) == len(survivors) + len(add)
+    np.testing.assert_array_equal(new_xy[:len(survivors)], xy[survivors])
+    np.testing.assert_array_equal(new_xy[len(survivors):], add.reshape(-1, 2))
+    emptied = gone[np.maximum(lab, 0)] & (lab >= 0)
+    assert (new_lab[emptied] == -1).all()
+    kept = (lab >= 0) & ~emptied
+    np.testing.assert_array_equal(new_xy[new_lab[kept]], xy[lab[kept]])
+    # order: a survivor's new index is the number of survivors before it
+    assert (np.searchsorted(survivors, lab[kept]) == new_lab[kept]).all()
+
+
+@pytest.mark.parametrize("metric", [E, L1])
+def test_single_survivor_repair_is_brute_force(orc, metric):
+    """Remove every seed but one: the repair frame gives the one-seed diagram
+    of Eq. 1 (the survivor owns every pixel)."""
+    g = np.random.default_rng(7)
+    for w, h, s in [(1, 1, 3), (33, 17, 20), (64, 64, 90), (100, 3, 12)]:
+        xy = inputs.uniform_seeds(w, h, s, seed=w)
+        lab = orc.jfa(w, h, xy, metric=metric)
+        keep = int(g.integers(0, s))
+        remove = np.array([k for k in range(s) if k != keep], np.int32)
+        new_xy, new_lab = orc.update_seeds(w, h, xy, lab, remove)
+        assert len(new_xy) == 1
+        out = orc.repair_step(w, h, new_xy, new_lab, metric=metric)
+        want, _ = orc.exact_brute(w, h, new_xy, metric)
+        np.testing.assert_array_equal(out, want)
+
+
+@pytest.mark.parametrize("metric", [E, L1])
+def test_repair_keeps_an_exact_map(orc, metric):
+    """On a map that already is the exact diagram (Eq. 1, lowest-index ties) the
+    repair frame changes nothing: no candidate is closer than a nearest seed."""
+    for trial in range(4):
+        w, h = 30 + 7 * trial, 25 + 3 * trial
+        xy = inputs.uniform_seeds(w, h, 15 + 10 * trial, seed=trial)
+        xy[-1] = xy[0]
+        lab, _ = orc.exact_brute(w, h, xy, metric)
+        np.testing.assert_array_equal(orc.repair_step(w, h, xy, lab, metric=metric), lab)
+
+
+def test_repair_covers_every_pixel_and_seed_pixels_own_themselves(orc):
+    """After removals (up to all but one) and insertions, the repair frame leaves
+    no empty pixel and every seed pixel holds the lowest index standing on it
+    (the seed is at distance 0 from itself, Eq. 1)."""
+    g = np.random.default_rng(11)
+    for trial in range(8):
+        w, h, s = int(g.integers(10, 90)), int(g.integers(10, 90)), int(g.integers(3, 200))
+        xy = inputs.uniform_seeds(w, h, s, seed=300 + trial)
+        lab = orc.jfa(w, h, xy)
+        remove, add = _random_update(g, w, h, s, int(g.integers(1, s)), int(g.integers(0, 30)))
+        new_xy, new_lab = orc.update_seeds(w, h, xy, lab, remove, add)
+        out = orc.repair_step(w, h, new_xy, new_lab)
+        assert (out >= 0).all()
+        for k in range(len(new_xy) - 1, -1, -1):
+            x, y = new_xy[k]
+            same = np.flatnonzero((new_xy[:, 0] == x) & (new_xy[:, 1] == y))
+            assert out[y, x] == same[0]
+
+
+def test_invalid_updates_change_nothing(orc):
+    w, h, s = 20, 10, 5
+    xy = inputs.uniform_seeds(w, h, s, seed=2)
+    lab = orc.jfa(w, h, xy)
+    assert orc.update_seeds(w, h, xy, lab, remove=[1, 1]) is None
+    assert orc.update_seeds(w, h, xy, lab, remove=[5]) is None
+    assert orc.update_seeds(w, h, xy, lab, remove=[-1]) is None
+    assert orc.update_seeds(w, h, xy, lab, remove=[0, 1, 2, 3, 4]) is None
+    assert orc.update_seeds(w, h, xy, lab, add=[[20, 0]]) is None
+    assert orc.update_seeds(w, h, xy, lab, add=[[0, -1]]) is None
+    new_xy, _ = orc.update_seeds(w, h, xy, lab, remove=[0, 1, 2, 3, 4], add=[[3, 3]])
+    np.testing.assert_array_equal(new_xy, [[3, 3]])
