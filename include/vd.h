@@ -151,6 +151,29 @@ int vd_move_seeds(vd_ctx* ctx, const int32_t* dxy, int dxy_on_device, int32_t ma
                   uint64_t rng_seed, uint64_t stream_id, int64_t step);
 
 /*
+ * Seed removal and insertion between frames.  The paper leaves both to future
+ * work (Section V); the rule here is this library's own:
+ *   - the seeds whose indices are listed in remove_ids (n_remove distinct
+ *     indices in [0, n)) leave; the survivors keep their order and are
+ *     renumbered 0 .. n - n_remove - 1;
+ *   - the n_add seeds of add_xy (x, y pairs on the grid) follow them;
+ *   - the current label map is relabelled: a surviving seed's pixels take its
+ *     new index, a removed seed's pixels become empty (-1);
+ *   - after any removal, the next vd_djfa_step runs the full JFA schedule
+ *     (Eq. 2, plus its `extra` passes) on the relabelled map instead of the
+ *     dJFA schedule, so the emptied cells fill from every side whatever their
+ *     size; after insertions only, the dJFA schedule runs (a new seed is
+ *     stamped and claims its cell like a moved one).  vd_jfa clears this.
+ * The seed count may grow past the one given to vd_create (the seed buffers
+ * are reallocated, synchronously); at least one seed must remain.  Both
+ * arrays are host (on_device = 0) or device pointers; they are copied.
+ * Returns VD_EINVAL, changing nothing, for an index out of range or repeated,
+ * a new seed off the grid, or no seed left.  Synchronises the stream.
+ */
+int vd_update_seeds(vd_ctx* ctx, const int32_t* remove_ids, int32_t n_remove, const int32_t* add_xy,
+                    int32_t n_add, int on_device);
+
+/*
  * A full JFA frame (Section III): empties the map (-1), stamps the seeds
  * (each seed pixel gets the lowest index standing on it) and runs the passes
  * of vd_jfa_schedule with the Moore neighbourhood of Table I.  Each pass is

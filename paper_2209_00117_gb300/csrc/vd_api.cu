@@ -489,6 +489,8 @@ void Profiler::destroy() {
 struct vd_ctx {
   int device = 0;
   int32_t w = 0, h = 0, n = 0, pitch = 0;
+  int32_t cap = 0;       // seeds the seed-sized buffers hold (>= n)
+  bool repair = false;   // seeds were removed: the next dJFA frame runs the repair schedule
   cudaStream_t stream = nullptr;
   int32_t* buf[2] = {nullptr, nullptr};
   int cur = 0;
@@ -583,6 +585,7 @@ extern "C" vd_ctx* vd_create(int32_t w, int32_t h, int32_t n) {
   c->h = h;
   c->n = n;
   c->pitch = (w + 31) / 32 * 32;
+  c->cap = n;
   const size_t map_bytes = static_cast<size_t>(c->pitch) * h * sizeof(int32_t);
   int rc = VD_OK;
   rc = rc ? rc : ctx_alloc(reinterpret_cast<void**>(&c->buf[0]), map_bytes, "label map");
@@ -683,6 +686,135 @@ extern "C" int vd_set_seeds(vd_ctx* c, const int32_t* xy, int on_device) {
   if (rc) return rc;
   ++c->launches;
   return vdi::launch_build_table(c->seeds, c->n, c->table, c->ptable, c->stream);
+}
+
+// Seed-sized buffers for `cap` seeds (seeds, both pass tables, staging);
+// the old ones are released.  Leaves the context unchanged on failure.
+static int grow_seed_buffers(vd_ctx* c, int32_t cap, const int* keep, const int* newidx, const int2* add,
+                             int32_t n_add) {
+  int2* seeds = nullptr;
+  int2* table = nullptr;
+  uint32_t* ptable = nullptr;
+  int2* stage = nullptr;
+  int rc = ctx_alloc(reinterpret_cast<void**>(&seeds), sizeof(int2) * cap, "seeds");
+  rc = rc ? rc : ctx_alloc(reinterpret_cast<void**>(&table), sizeof(int2) * (static_cast<size_t>(cap) + 1), "seed table");
+  rc = rc ? rc : ctx_alloc(reinterpret_cast<void**>(&ptable), sizeof(uint32_t) * (static_cast<size_t>(cap) + 1), "seed table");
+  rc = rc ? rc : ctx_alloc(reinterpret_cast<void**>(&stage), sizeof(int2) * cap, "moves");
+  if (rc) {
+    cudaFree(seeds);
+    cudaFree(table);
+    cudaFree(ptable);
+    cudaFree(stage);
+    return rc;
+  }
+  const int total = c->n + n_add;
+  vdk::k_update_compact<<<(total + 255) / 256, 256, 0, c->stream>>>(c->seeds, c->n, keep, newidx, add, n_add, seeds);
+  rc = vd_cuda_check(cudaGetLastError(), "compact seeds");
+  if (!rc) rc = vd_cuda_check(cudaStreamSynchronize(c->stream), "synchronize");
+  if (rc) {
+    cudaFree(seeds);
+    cudaFree(table);
+    cudaFree(ptable);
+    cudaFree(stage);
+    return rc;
+  }
+  cudaFree(c->seeds);
+  cudaFree(c->table);
+  cudaFree(c->ptable);
+  cudaFree(c->dxy_stage);
+  cudaFree(c->bk_ids);  // sized by the seed count; reallocated on next use
+  c->bk_ids = nullptr;
+  c->seeds = seeds;
+  c->table = table;
+  c->ptable = ptable;
+  c->dxy_stage = stage;
+  c->cap = cap;
+  return VD_OK;
+}
+
+extern "C" int vd_update_seeds(vd_ctx* c, const int32_t* remove_ids, int32_t n_remove, const int32_t* add_xy,
+                               int32_t n_add, int on_device) {
+  VD_CHECK_CTX(c);
+  if (n_remove < 0 || n_add < 0) return vd_fail(VD_EINVAL, "negative counts (%d removed, %d added)", n_remove, n_add);
+  if ((n_remove > 0 && !remove_ids) || (n_add > 0 && !add_xy)) return vd_fail(VD_EINVAL, "null input");
+  if (n_remove > c->n) return vd_fail(VD_EINVAL, "%d removals of %d seeds", n_remove, c->n);
+  const int64_t n_new = static_cast<int64_t>(c->n) - n_remove + n_add;
+  if (n_new < 1) return vd_fail(VD_EINVAL, "no seed would remain");
+  if (n_new > (int64_t{1} << 30)) return vd_fail(VD_EINVAL, "%lld seeds exceed 2^30", static_cast<long long>(n_new));
+  cudaStream_t st = c->stream;
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  // stream-ordered scratch: keep flags, new indices (+ the survivor count), the inputs
+  int* keep = nullptr;
+  int* newidx = nullptr;
+  int* rem = nullptr;
+  int2* add = nullptr;
+  auto release = [&]() {
+    if (keep) cudaFreeAsync(keep, st);
+    if (newidx) cudaFreeAsync(newidx, st);
+    if (rem) cudaFreeAsync(rem, st);
+    if (add) cudaFreeAsync(add, st);
+  };
+  int rc = vd_cuda_check(cudaMallocAsync(reinterpret_cast<void**>(&keep), sizeof(int) * c->n, st), "update scratch");
+  if (!rc) rc = vd_cuda_check(cudaMallocAsync(reinterpret_cast<void**>(&newidx), sizeof(int) * (c->n + 1), st), "update scratch");
+  if (!rc && n_remove > 0) rc = vd_cuda_check(cudaMallocAsync(reinterpret_cast<void**>(&rem), sizeof(int) * n_remove, st), "update scratch");
+  if (!rc && n_add > 0) rc = vd_cuda_check(cudaMallocAsync(reinterpret_cast<void**>(&add), sizeof(int2) * n_add, st), "update scratch");
+  if (!rc && n_remove > 0) rc = vd_cuda_check(cudaMemcpyAsync(rem, remove_ids, sizeof(int) * n_remove, kind, st), "copy removals");
+  if (!rc && n_add > 0) rc = vd_cuda_check(cudaMemcpyAsync(add, add_xy, sizeof(int2) * n_add, kind, st), "copy new seeds");
+  if (!rc) rc = vd_cuda_check(cudaMemsetAsync(c->counters + 2, 0, sizeof(unsigned long long), st), "memset");
+  if (rc) {
+    release();
+    return rc;
+  }
+  // validate first: nothing of the context changes unless every removal
+  // names a distinct seed and every new seed lies on the grid
+  vdk::k_fill_i32<<<std::min((c->n + 255) / 256, 152 * 8), 256, 0, st>>>(keep, c->n, 1);
+  if (n_remove > 0)
+    vdk::k_update_remove<<<(n_remove + 255) / 256, 256, 0, st>>>(rem, n_remove, c->n, keep, c->counters + 2);
+  if (n_add > 0) vdk::k_check_seeds<<<(n_add + 255) / 256, 256, 0, st>>>(add, n_add, c->w, c->h, c->counters + 2);
+  c->launches += 1 + (n_remove > 0) + (n_add > 0);
+  rc = vd_cuda_check(cudaGetLastError(), "validate update");
+  if (!rc) rc = vd_cuda_check(cudaMemcpyAsync(c->host_counters + 2, c->counters + 2, sizeof(unsigned long long),
+                                              cudaMemcpyDeviceToHost, st), "copy flag");
+  if (!rc) rc = vd_cuda_check(cudaStreamSynchronize(st), "synchronize");
+  if (!rc && c->host_counters[2] != 0)
+    rc = vd_fail(VD_EINVAL, "%llu invalid entries (a removal out of range or repeated, or a new seed off the grid)",
+                 c->host_counters[2]);
+  if (rc) {
+    release();
+    return rc;
+  }
+  vdk::k_scan<<<1, 1024, 0, st>>>(keep, c->n, newidx);
+  ++c->launches;
+  rc = vd_cuda_check(cudaGetLastError(), "scan");
+  // the new seed array, then the map relabelled (it still holds old indices)
+  if (!rc && n_new > c->cap) {
+    rc = grow_seed_buffers(c, static_cast<int32_t>(n_new), keep, newidx, add, n_add);
+  } else if (!rc) {
+    const int total = c->n + n_add;
+    vdk::k_update_compact<<<(total + 255) / 256, 256, 0, st>>>(c->seeds, c->n, keep, newidx, add, n_add, c->dxy_stage);
+    rc = vd_cuda_check(cudaGetLastError(), "compact seeds");
+    if (!rc) rc = vd_cuda_check(cudaMemcpyAsync(c->seeds, c->dxy_stage, sizeof(int2) * n_new, cudaMemcpyDeviceToDevice, st),
+                                "copy seeds");
+  }
+  ++c->launches;
+  if (rc) {
+    release();
+    return rc;
+  }
+  const int64_t count = static_cast<int64_t>(c->pitch) * c->h;
+  vdk::k_update_relabel<<<static_cast<int>(std::min<int64_t>((count + 255) / 256, 152 * 16)), 256, 0, st>>>(
+      c->buf[c->cur], count, keep, newidx);
+  ++c->launches;
+  rc = vd_cuda_check(cudaGetLastError(), "relabel");
+  release();
+  if (rc) return rc;
+  c->n = static_cast<int32_t>(n_new);
+  if (n_remove > 0) c->repair = true;
+  // captured frames hold the old seed count and buffers
+  for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
+  c->graphs.clear();
+  ++c->launches;
+  return vdi::launch_build_table(c->seeds, c->n, c->table, c->ptable, st);
 }
 
 extern "C" int vd_get_seeds(vd_ctx* c, int32_t* xy, int on_device) {
@@ -792,15 +924,24 @@ extern "C" int vd_jfa(vd_ctx* c, int32_t extra, int32_t metric) {
     return vdi::run_passes(view(c), c->buf, &c->cur, ks, nbs, n, metric, c->tune, c->stream, &c->launches, pr,
                            false);
   };
-  return run_frame(c, std::make_tuple(0, c->cur, extra, metric, 0, 0, 0), nl + 2, cur_after, body);
+  const int rc = run_frame(c, std::make_tuple(0, c->cur, extra, metric, 0, 0, 0), nl + 2, cur_after, body);
+  if (!rc) c->repair = false;  // a full frame covers every pixel
+  return rc;
 }
 
 extern "C" int vd_djfa_step(vd_ctx* c, int32_t d_max, int32_t vn_waves, int32_t extra, int32_t metric) {
   VD_CHECK_CTX(c);
   if (check_metric(metric)) return VD_EINVAL;
   int32_t ks[VD_MAX_PASSES], nbs[VD_MAX_PASSES];
-  const int n = vd_djfa_schedule(c->w, c->h, c->n, d_max, vn_waves, extra, ks, nbs, VD_MAX_PASSES);
+  int n = vd_djfa_schedule(c->w, c->h, c->n, d_max, vn_waves, extra, ks, nbs, VD_MAX_PASSES);
   if (n < 0) return n;
+  // after a removal: the full JFA schedule on the relabelled map, so that the
+  // emptied cells fill from every side whatever their size
+  const bool repair = c->repair;
+  if (repair) {
+    n = vd_jfa_schedule(c->w, c->h, extra, ks, nbs, VD_MAX_PASSES);
+    if (n < 0) return n;
+  }
   const int nl = count_launches(ks, nbs, n, c->tune);
   const int cur_after = c->cur ^ (nl & 1);
   auto body = [&]() -> int {
@@ -810,9 +951,12 @@ extern "C" int vd_djfa_step(vd_ctx* c, int32_t d_max, int32_t vn_waves, int32_t 
     if (pr) pr->end(pi, c->stream);
     if (rc) return rc;
     return vdi::run_passes(view(c), c->buf, &c->cur, ks, nbs, n, metric, c->tune, c->stream, &c->launches, pr,
-                           true);
+                           !repair);
   };
-  return run_frame(c, std::make_tuple(1, c->cur, d_max, vn_waves, extra, metric, 0), nl + 2, cur_after, body);
+  const int rc = run_frame(c, std::make_tuple(1, c->cur, d_max, vn_waves, extra, metric, repair ? 1 : 0), nl + 2,
+                           cur_after, body);
+  if (!rc) c->repair = false;
+  return rc;
 }
 
 extern "C" int vd_stamp(vd_ctx* c) {
@@ -968,7 +1112,7 @@ extern "C" int vd_exact(vd_ctx* c, int32_t* labels, int32_t* dist, int on_device
     if (rc) return rc;
     c->bk_cells = cells;
   }
-  if (!c->bk_ids) rc = ctx_alloc(reinterpret_cast<void**>(&c->bk_ids), sizeof(int) * c->n, "bucket ids");
+  if (!c->bk_ids) rc = ctx_alloc(reinterpret_cast<void**>(&c->bk_ids), sizeof(int) * c->cap, "bucket ids");
   if (rc) return rc;
   int32_t* dl = labels;
   int32_t* dd = dist;

@@ -723,6 +723,54 @@ static __global__ void k_check_seeds(const int2* __restrict__ seeds, int n, int 
 }
 
 // ---------------------------------------------------------------------------
+// Seed insertion and removal between frames (the paper leaves both to future
+// work, Section V; the rule is this library's: survivors keep their order and
+// are renumbered, new seeds follow, a removed seed's pixels become empty)
+// ---------------------------------------------------------------------------
+
+static __global__ void k_fill_i32(int* __restrict__ p, int n, int v) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) p[i] = v;
+}
+
+// keep[id] = 0 for every removed index; an index out of range or listed twice
+// is counted in *bad.
+static __global__ void k_update_remove(const int* __restrict__ remove, int n_remove, int n, int* __restrict__ keep,
+                                       unsigned long long* __restrict__ bad) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n_remove) return;
+  const int id = remove[j];
+  if (id < 0 || id >= n) {
+    atomicAdd(bad, 1ULL);
+    return;
+  }
+  if (atomicExch(&keep[id], 0) == 0) atomicAdd(bad, 1ULL);
+}
+
+// The new seed array: each survivor at its new index (the exclusive prefix
+// sum of keep, newidx[n] = survivors), then the added seeds.
+static __global__ void k_update_compact(const int2* __restrict__ seeds, int n, const int* __restrict__ keep,
+                                        const int* __restrict__ newidx, const int2* __restrict__ add, int n_add,
+                                        int2* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    if (keep[i]) out[newidx[i]] = seeds[i];
+  } else if (i < n + n_add) {
+    out[newidx[n] + (i - n)] = add[i - n];
+  }
+}
+
+// Relabels a map in place: a surviving seed's label becomes its new index, a
+// removed seed's -1; empty pixels and the row padding stay -1.
+static __global__ void k_update_relabel(int32_t* __restrict__ labels, int64_t count, const int* __restrict__ keep,
+                                        const int* __restrict__ newidx) {
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < count;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int l = labels[i];
+    if (l >= 0) labels[i] = keep[l] ? newidx[l] : -1;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Similarity counts (Section V-A)
 // ---------------------------------------------------------------------------
 

@@ -202,6 +202,29 @@ class VoronoiSim:
         N.check(self._lib.vd_move_seeds(self._h, ptr, dev, int(max_disp), int(rng_seed) & (2**64 - 1),
                                         int(stream_id) & (2**64 - 1), int(step)))
 
+    def update_seeds(self, remove=None, add=None):
+        """Removes the seeds with the given indices and appends new (x, y)
+        seeds; survivors are renumbered in order and the map is relabelled
+        (see vd_update_seeds).  Both host arrays or both CUDA int32 tensors."""
+        rem = remove if remove is not None else np.zeros(0, np.int32)
+        new = add if add is not None else np.zeros((0, 2), np.int32)
+        if not _is_torch(rem):
+            rem = np.ascontiguousarray(rem, dtype=np.int32).reshape(-1)
+        if not _is_torch(new):
+            new = np.ascontiguousarray(new, dtype=np.int32).reshape(-1)
+        nr = int(rem.numel() if _is_torch(rem) else rem.size)
+        na = int(new.numel() if _is_torch(new) else new.size) // 2
+        pr, dr = _buf(rem) if nr else (None, None)
+        pa, da = _buf(new) if na else (None, None)
+        kinds = {d for d in (dr, da) if d is not None}
+        if len(kinds) > 1:
+            raise ValueError("removals and new seeds must both be host arrays or both CUDA tensors")
+        on_device = kinds.pop() if kinds else 0
+        N.check(self._lib.vd_update_seeds(self._h, pr, nr, pa, na, on_device))
+        n = ctypes.c_int32()
+        N.check(self._lib.vd_get_shape(self._h, None, None, ctypes.byref(n), None))
+        self.n_seeds = n.value
+
     # -- frames ---------------------------------------------------------
     def jfa(self, extra: int = 0, metric: int = EUCLID):
         N.check(self._lib.vd_jfa(self._h, int(extra), int(metric)))
