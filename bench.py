@@ -8,7 +8,7 @@ selects a point of the 8192 x 8192 sweep instead): the seed
 move (Algorithm 1's SimulateParticles), the stamp and the dJFA passes of Eq. 4
 (6 passes, the first two Von Neumann).  The same trajectory is also run with a
 full JFA frame per step (11 passes, Eq. 2) for the speedup, and every 10th frame
-both are scored against each other (the paper's similarity, Section V-A) and
+both are scored against each other (the paper's similarity, Section VI-A) and
 against the exact diagram (distance-correct pixels).
 
 Printed: one JSON line (rank 0).  ``value`` is whole-job dJFA throughput in

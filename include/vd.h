@@ -79,12 +79,12 @@ int vd_jfa_schedule(int32_t w, int32_t h, int32_t extra_passes, int32_t* ks, int
                     int32_t cap);
 
 /*
- * dJFA step lengths, Eq. 3-4 (Section IV-A): delta_1 = 2^ceil(log2(max(
+ * dJFA step lengths, Eq. 3-4 (Section V-A): delta_1 = 2^ceil(log2(max(
  * 2 L_avg, d_max))) with L_avg = sqrt(w h / s), decided in exact integers
  * (the least P = 2^e with P^2 s >= 4 w h and P >= d_max), capped at JFA's
  * k_1 (Algorithm 1's k_m).  Passes delta_1, ..., 1 (log2(delta_1) + 1), the
  * first `vn_waves` with the Von Neumann neighbourhood and the rest Moore
- * (Section IV-B), then `extra_passes` as in vd_jfa_schedule (the optional
+ * (Section V-B), then `extra_passes` as in vd_jfa_schedule (the optional
  * extra step after Eq. 4).  Same output and errors as vd_jfa_schedule;
  * vn_waves must be >= 0.
  */
@@ -136,7 +136,7 @@ int vd_get_seeds(vd_ctx* ctx, int32_t* xy, int on_device);
 
 /*
  * SimulateParticles of Algorithm 1 under the uniform random model of
- * Section IV-A: every seed k moves to clamp(p_k + delta_k) with the clamp
+ * Section V-A: every seed k moves to clamp(p_k + delta_k) with the clamp
  * keeping it on the grid.  If dxy is non-NULL it holds n_seeds integer
  * displacement pairs (host or device per dxy_on_device, a device pointer
  * 8-byte aligned; max_disp, rng_seed, stream_id and step are then ignored).  If dxy is NULL, each displacement
@@ -152,7 +152,7 @@ int vd_move_seeds(vd_ctx* ctx, const int32_t* dxy, int dxy_on_device, int32_t ma
 
 /*
  * Seed removal and insertion between frames.  The paper leaves both to future
- * work (Section V); the rule here is this library's own:
+ * work (Section VII); the rule here is this library's own:
  *   - the seeds whose indices are listed in remove_ids (n_remove distinct
  *     indices in [0, n)) leave; the survivors keep their order and are
  *     renumbered 0 .. n - n_remove - 1;
@@ -185,10 +185,10 @@ int vd_update_seeds(vd_ctx* ctx, const int32_t* remove_ids, int32_t n_remove, co
 int vd_jfa(vd_ctx* ctx, int32_t extra_passes, int32_t metric);
 
 /*
- * One dJFA frame (Section IV, Algorithm 1 after SimulateParticles): stamps
+ * One dJFA frame (Section V, Algorithm 1 after SimulateParticles): stamps
  * the current seeds onto the previous frame's map without clearing it, then
  * runs the passes of vd_djfa_schedule(w, h, n_seeds, d_max, vn_waves,
- * extra_passes).  d_max is the per-step move bound of Section IV-A (the
+ * extra_passes).  d_max is the per-step move bound of Section V-A (the
  * Chebyshev bound of the moves, e.g. max_disp).  VD_EINVAL for d_max < 0,
  * vn_waves < 0, bad metric or extra_passes outside [0, 2].
  */
@@ -232,7 +232,7 @@ int vd_wait_labels(vd_ctx* ctx);
 int vd_labels_device_ptr(vd_ctx* ctx, const int32_t** labels);
 
 /*
- * Similarity counts of Section V-A for the current map against optional
+ * Similarity counts of Section VI-A for the current map against optional
  * dense references (host or device per on_device):
  *   n_match = #pixels whose label equals ref_labels (the paper's similarity
  *             is 100 n_match / (w h) against a same-frame JFA);
@@ -301,7 +301,7 @@ int vd_exact_noalloc(const int32_t* seeds_xy, int32_t n_seeds, int32_t grid_w, i
  * together.  Every simulation computes exactly what a context would compute
  * for it alone (vd_jfa, vd_move_seeds with stream_id = its index,
  * vd_djfa_step): the same per-pixel code, the same exact-integer results.
- * The paper runs one simulation at a time (Section V); batching is this
+ * The paper runs one simulation at a time (Section VI); batching is this
  * library's way of filling a GPU with many small grids.
  */
 typedef struct vd_batch vd_batch;

@@ -11,10 +11,10 @@ the paper ("GPU Voronoi Diagrams for Random Moving Seeds") that it follows:
 
 * Eq. 1 (Section II)   -- :func:`exact_brute`, :func:`exact_dist_edt`
 * Eq. 2 (Section III)  -- :func:`jfa_first_step`, :func:`jfa_schedule`
-* Table I (Section III)-- :func:`jump_pass` (Moore), Section IV-B (Von Neumann)
-* Eq. 3-4 (Section IV-A) -- :func:`djfa_first_step`, :func:`djfa_schedule`
-* Algorithm 1 (Section IV-D) -- :func:`stamp`, :func:`jfa`, :func:`djfa_step`
-* Section V-A          -- :func:`similarity`
+* Table I (Section III)-- :func:`jump_pass` (Moore), Section V-B (Von Neumann)
+* Eq. 3-4 (Section V-A) -- :func:`djfa_first_step`, :func:`djfa_schedule`
+* Algorithm 1 (Section V-D) -- :func:`stamp`, :func:`jfa`, :func:`djfa_step`
+* Section VI-A         -- :func:`similarity`
 
 Parity status: pinned (see ``tests/test_oracle_pins.py``); no function here is
 unpinned.
@@ -120,7 +120,7 @@ def get_threads() -> int:
 
 
 def distance(sx, sy, px, py, metric=EUCLID) -> int:
-    """Section II distance d (squared Euclidean, or Manhattan of Section IV-C)."""
+    """Section II distance d (squared Euclidean, or Manhattan of Section V-C)."""
     return int(_load().orc_distance(sx, sy, px, py, metric))
 
 
@@ -150,7 +150,7 @@ def jfa_schedule(w: int, h: int, extra: int = 0):
 
 
 def djfa_schedule(w: int, h: int, s: int, d_max: int, vn_waves: int = 2, extra: int = 0):
-    """[(k, neighbourhood), ...] of a dJFA frame (Eq. 4, Section IV-B)."""
+    """[(k, neighbourhood), ...] of a dJFA frame (Eq. 4, Section V-B)."""
     return _schedule(_load().orc_djfa_schedule, w, h, s, d_max, vn_waves, extra)
 
 
@@ -205,7 +205,7 @@ def stamp(w: int, h: int, xy, label) -> np.ndarray:
 
 
 def jump_pass(w: int, h: int, xy, src, k: int, nb=MOORE, metric=EUCLID) -> np.ndarray:
-    """One gather pass at step k (Table I / Section IV-B); returns the new map."""
+    """One gather pass at step k (Table I / Section V-B); returns the new map."""
     xy = _seeds(xy)
     src = _map(src, w, h)
     dst = np.empty_like(src)
@@ -256,7 +256,7 @@ def repair_step(w: int, h: int, xy, label, extra: int = 0, metric=EUCLID) -> np.
 
 
 def similarity(w: int, h: int, xy, label, exact_dist=None, ref_label=None, metric=EUCLID):
-    """(n_exact, n_match) of Section V-A: distance-correct and label-equal pixel counts."""
+    """(n_exact, n_match) of Section VI-A: distance-correct and label-equal pixel counts."""
     xy = _seeds(xy)
     label = _map(label, w, h)
     ed = None if exact_dist is None else _map(exact_dist, w, h)

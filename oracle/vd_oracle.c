@@ -66,7 +66,7 @@ int orc_get_threads(void) {
 }
 
 /* ------------------------------------------------------------------------ */
-/* distance (Section II, d; Section IV-C for the Manhattan variant)          */
+/* distance (Section II, d; Section V-C for the Manhattan variant)           */
 /* ------------------------------------------------------------------------ */
 
 static int64_t orc_dist(int64_t sx, int64_t sy, int64_t px, int64_t py, int metric) {
@@ -142,7 +142,7 @@ int64_t orc_djfa_first_step_uncapped(int32_t w, int32_t h, int64_t s, int32_t d_
 }
 
 /*
- * delta_1 capped at JFA's k_1: by Section IV-A, sparse seeds make dJFA fall
+ * delta_1 capped at JFA's k_1: by Section V-A, sparse seeds make dJFA fall
  * back to JFA's cost at worst, and Algorithm 1 derives k_m from the diagram
  * before its loop; k_m is read as that cap.
  */
@@ -158,7 +158,7 @@ int32_t orc_djfa_first_step(int32_t w, int32_t h, int64_t s, int32_t d_max) {
  * (log2(first) + 1 passes, Section III and Eq. 4), then `extra` more passes
  * (JFA+1 appends k = 1; JFA+2 appends k = 2 then k = 1; Section III), all
  * Moore except the first `vn_waves` which use the Von Neumann neighbourhood
- * (Section IV-B).  Returns the number of passes written (at most `cap`).
+ * (Section V-B).  Returns the number of passes written (at most `cap`).
  */
 static int orc_fill_schedule(int32_t first, int vn_waves, int extra,
                              int32_t* ks, int32_t* nbs, int cap) {
@@ -334,7 +334,7 @@ void orc_exact_dist_edt(int32_t w, int32_t h, int64_t s, const int32_t* xy, int 
 }
 
 /* ------------------------------------------------------------------------ */
-/* the moving seeds (Section IV-A dynamic model, Algorithm 1 SimulateParticles) */
+/* the moving seeds (Sections IV and V-A, Algorithm 1 SimulateParticles)      */
 /* ------------------------------------------------------------------------ */
 
 /* Each seed moves by its given integer displacement, clamped to the grid. */
@@ -408,7 +408,7 @@ void orc_fill(int32_t w, int32_t h, int32_t* label, int32_t value) {
  * Stamp: every seed pixel gets the lowest index among the seeds standing on
  * it, overwriting what the map held there (the flood starts from the seeds,
  * Section III; dJFA re-stamps the moved seeds onto the previous frame's map,
- * Section IV).  Writing the indices from the highest down makes the last
+ * Section V).  Writing the indices from the highest down makes the last
  * write the lowest.
  */
 void orc_stamp(int32_t w, int32_t h, int64_t s, const int32_t* xy, int32_t* label) {
@@ -487,7 +487,7 @@ void orc_jfa(int32_t w, int32_t h, int64_t s, const int32_t* xy, int extra, int 
 }
 
 /*
- * One dJFA step (Section IV, Algorithm 1, after SimulateParticles): the
+ * One dJFA step (Section V, Algorithm 1, after SimulateParticles): the
  * moved seeds are stamped onto the previous frame's map held in `label`,
  * then the passes delta_1, ..., 1 of Eq. 4 run, the first `vn_waves` with
  * the Von Neumann neighbourhood and the rest Moore, plus `extra` passes.
@@ -501,7 +501,7 @@ void orc_djfa_step(int32_t w, int32_t h, int64_t s, const int32_t* xy, int32_t d
 }
 
 /* ------------------------------------------------------------------------ */
-/* seed insertion and removal (Section V leaves it to future work; the rule   */
+/* seed insertion and removal (Section VII leaves it to future work; the rule */
 /* below is this library's reading, pinned by the invariants in the tests)    */
 /* ------------------------------------------------------------------------ */
 
@@ -572,7 +572,7 @@ void orc_repair_step(int32_t w, int32_t h, int64_t s, const int32_t* xy, int ext
 }
 
 /* ------------------------------------------------------------------------ */
-/* similarity (Section V-A)                                                  */
+/* similarity (Section VI-A)                                                 */
 /* ------------------------------------------------------------------------ */
 
 /*

@@ -17,7 +17,7 @@ constexpr int kManhattan = 1;
 constexpr int kMoore = 0;
 constexpr int kVonNeumann = 1;
 
-// Distance of Section II (squared Euclidean) or Section IV-C (Manhattan),
+// Distance of Section II (squared Euclidean) or Section V-C (Manhattan),
 // exact in 32 bits for grid sides up to 32768 (2 * 32767^2 < 2^31).
 template <int METRIC>
 __device__ __forceinline__ uint32_t seed_dist(int2 s, int x, int y) {
@@ -378,7 +378,7 @@ __device__ __forceinline__ void fold_sides(Q& q, const int32_t* __restrict__ row
   group_fence();
 }
 
-// One jump pass (Table I / Section IV-B) for the four horizontally adjacent
+// One jump pass (Table I / Section V-B) for the four horizontally adjacent
 // pixels (x0 .. x0+3, y) of one thread: it starts from their own labels and
 // folds in the neighbour offsets one source row at a time (16-byte label
 // loads, seed gathers and minimums).  Candidate order does not matter: every
@@ -724,7 +724,7 @@ static __global__ void k_check_seeds(const int2* __restrict__ seeds, int n, int 
 
 // ---------------------------------------------------------------------------
 // Seed insertion and removal between frames (the paper leaves both to future
-// work, Section V; the rule is this library's: survivors keep their order and
+// work, Section VII; the rule is this library's: survivors keep their order and
 // are renumbered, new seeds follow, a removed seed's pixels become empty)
 // ---------------------------------------------------------------------------
 
@@ -771,7 +771,7 @@ static __global__ void k_update_relabel(int32_t* __restrict__ labels, int64_t co
 }
 
 // ---------------------------------------------------------------------------
-// Similarity counts (Section V-A)
+// Similarity counts (Section VI-A)
 // ---------------------------------------------------------------------------
 
 __device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {

@@ -5,9 +5,9 @@ displacements, populations of independent simulations and request arrival
 times.  It holds none of the method's arithmetic (no distances, no clamping, no
 schedules), and both the CUDA path and the CPU oracle consume what it returns.
 
-The paper's experiments (Section V) place seeds uniformly at random on an n x n
+The paper's experiments (Section VI) place seeds uniformly at random on an n x n
 pixel grid and move every seed each step by a uniformly random integer amount
-(Section II and Section IV-A); there is no dataset.  The named workloads below
+(Section IV and Section V-A); there is no dataset.  The named workloads below
 restate those experiments at fixed sizes:
 
 * ``single256``   256 x 256 grid, 64 seeds, 10 steps, moves in [-1, 1]

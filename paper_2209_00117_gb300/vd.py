@@ -68,7 +68,7 @@ def jfa_schedule(w: int, h: int, extra: int = 0):
 
 
 def djfa_schedule(w: int, h: int, n_seeds: int, d_max: int, vn_waves: int = 2, extra: int = 0):
-    """[(k, neighbourhood)] of a dJFA frame (Eq. 3-4, Section IV-B)."""
+    """[(k, neighbourhood)] of a dJFA frame (Eq. 3-4, Section V-B)."""
     return _schedule(N.lib().vd_djfa_schedule, w, h, n_seeds, d_max, vn_waves, extra)
 
 
@@ -269,7 +269,7 @@ class VoronoiSim:
         return int(p.value or 0)
 
     def similarity(self, exact_dist=None, ref_labels=None, metric: int = EUCLID):
-        """(n_exact, n_match) counts of Section V-A."""
+        """(n_exact, n_match) counts of Section VI-A."""
         n = self.w * self.h
         pe, de = _buf(exact_dist, n)
         pr, dr = _buf(ref_labels, n)

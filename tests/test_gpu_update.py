@@ -1,5 +1,5 @@
 """Seed removal and insertion between frames (the paper leaves both to future
-work, Section V; the rule is the library's own and the oracle's): the update
+work, Section VII; the rule is the library's own and the oracle's): the update
 and the frames after it equal the oracle bit for bit (integer maps,
 tolerance 0)."""
 import numpy as np

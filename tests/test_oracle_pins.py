@@ -84,7 +84,7 @@ def test_djfa_first_step_matches_floating_formula(orc):
 
 
 def test_djfa_behaviour_claims(orc):
-    """Section IV-A: more seeds never lengthen the schedule; few seeds give
+    """Section V-A: more seeds never lengthen the schedule; few seeds give
     JFA's schedule; a large d_max takes over."""
     w = h = 1024
     prev = None
@@ -183,7 +183,7 @@ def test_edt_no_seeds(orc):
 
 
 # --------------------------------------------------------------------------
-# One jump pass: Table I, Section IV-B
+# One jump pass: Table I, Section V-B
 # --------------------------------------------------------------------------
 
 @pytest.mark.parametrize("nb", [M, VN])
@@ -373,7 +373,7 @@ def test_similarity_counts(orc):
 
 
 def test_djfa_similarity_level_single256(orc):
-    """Section V-B: Euclidean dJFA stays close to JFA on the 256^2, 64-seed,
+    """Section VI-B: Euclidean dJFA stays close to JFA on the 256^2, 64-seed,
     [-1, 1]-move workload (reported near 100%)."""
     w, h, s, steps, D = inputs.SINGLE["single256"]
     xy = inputs.uniform_seeds(w, h, s, seed=0)
@@ -388,7 +388,7 @@ def test_djfa_similarity_level_single256(orc):
 
 
 # --------------------------------------------------------------------------
-# Seed insertion and removal (future work in Section V; the library's rule)
+# Seed insertion and removal (future work in Section VII; the library's rule)
 # --------------------------------------------------------------------------
 
 def _random_update(g, w, h, s, n_remove, n_add):
