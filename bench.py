@@ -50,7 +50,8 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="single2048",
-                    help="single2048 (default), single256, or sweep8192 with --seeds and --max-disp")
+                    help="single2048 (default), single256, sweep8192 with --seeds and --max-disp, "
+                         "batched256, serve1000, churn2048")
     ap.add_argument("--seeds", type=int, default=None, help="sweep8192: seed count (2^10, 2^14, 2^18, 2^22)")
     ap.add_argument("--max-disp", type=int, default=None, help="sweep8192: maximum move per axis (1, 4, 16)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
@@ -63,6 +64,7 @@ def parse_args():
     ap.add_argument("--rates", default="2000,5000,10000,20000",
                     help="serve1000: Poisson request rates (per second)")
     ap.add_argument("--duration", type=float, default=1.0, help="serve1000: seconds of arrivals per rate")
+    ap.add_argument("--churn", type=int, default=164, help="churn2048: seeds removed and inserted per step")
     return ap.parse_args()
 
 
@@ -647,10 +649,80 @@ def run_serve(args):
     return 0
 
 
+def run_churn(args):
+    """Seed churn on the 2048^2, 16384-seed simulation: every step moves the
+    seeds, removes `--churn` random seeds and inserts as many new ones
+    (vd_update_seeds), then runs the frame (the repair schedule after a
+    removal).  Against plain dJFA steps of the same simulation."""
+    import torch
+
+    from paper_2209_00117_gb300 import build, inputs, vd
+
+    rank, world, local = dist_env()
+    build.build()
+    torch.cuda.set_device(local)
+    w = h = 2048
+    s, D, K, W = 16384, 2, args.steps, args.warmup
+    c = args.churn
+    g = np.random.default_rng(rank)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    sim = vd.VoronoiSim(w, h, s, stream=stream)
+    sim.set_option(vd.OPT_USE_GRAPHS, 1)
+    sim.set_seeds(inputs.uniform_seeds(w, h, s, seed=rank))
+    sim.jfa()
+
+    def plain(t):
+        sim.move(None, max_disp=D, rng_seed=rank, stream_id=0, step=t)
+        sim.djfa_step(d_max=D)
+
+    def churn(t):
+        sim.move(None, max_disp=D, rng_seed=rank, stream_id=0, step=t)
+        remove = g.choice(sim.n_seeds, size=c, replace=False).astype(np.int32)
+        add = np.stack([g.integers(0, w, c), g.integers(0, h, c)], axis=1).astype(np.int32)
+        t0 = time.perf_counter()
+        sim.update_seeds(remove, add)
+        t_upd.append(time.perf_counter() - t0)
+        sim.djfa_step(d_max=D)
+
+    def timed(fn, step0):
+        for i in range(W):
+            fn(step0 + i)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for i in range(K):
+            fn(step0 + W + i)
+        torch.cuda.synchronize()
+        return (time.perf_counter() - t0) / K * 1e3
+
+    t_upd = []
+    ms_plain = timed(plain, 0)
+    t_upd.clear()
+    ms_churn = timed(churn, 10 * (K + W))
+    upd_ms = 1e3 * float(np.mean(t_upd[W:])) if len(t_upd) > W else None
+    lab = sim.labels()
+    ex_l, ex_d = sim.exact()
+    n_exact, _ = sim.similarity(exact_dist=ex_d)
+    print(json.dumps({
+        "workload": f"churn2048: 2048x2048 int32 map, 16384 seeds, moves in [-{D},{D}], {c} seeds removed and "
+                    f"{c} inserted per step (vd_update_seeds), each step's frame the repair schedule",
+        "unit": "ms per step (host wall clock, K steps)", "steps": K, "warmup": W, "dtype": "int32",
+        "data": "synthetic", "churn_per_step": c,
+        "ms_per_step_plain_djfa": ms_plain, "ms_per_step_with_churn": ms_churn,
+        "ms_update_seeds_alone": upd_ms,
+        "empty_pixels_after": int((lab < 0).sum()),
+        "distance_correct_pct_after": round(100.0 * n_exact / (w * h), 4),
+    }))
+    sim.close()
+    return 0
+
+
 def main():
     args = parse_args()
     if args.workload == "batched256":
         return run_batched(args)
+    if args.workload == "churn2048":
+        return run_churn(args)
     if args.workload == "serve1000":
         return run_serve(args)
     _SWEEP["seeds"] = args.seeds

@@ -168,7 +168,10 @@ int vd_move_seeds(vd_ctx* ctx, const int32_t* dxy, int dxy_on_device, int32_t ma
  * are reallocated, synchronously); at least one seed must remain.  Both
  * arrays are host (on_device = 0) or device pointers; they are copied.
  * Returns VD_EINVAL, changing nothing, for an index out of range or repeated,
- * a new seed off the grid, or no seed left.  Synchronises the stream.
+ * a new seed off the grid, or no seed left.  Host inputs are validated on the
+ * host and the update is queued on the stream; device inputs are validated on
+ * the device, which synchronises the stream once.  Growing past the
+ * allocation synchronises too.
  */
 int vd_update_seeds(vd_ctx* ctx, const int32_t* remove_ids, int32_t n_remove, const int32_t* add_xy,
                     int32_t n_add, int on_device);

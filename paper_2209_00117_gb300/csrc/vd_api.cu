@@ -766,19 +766,42 @@ extern "C" int vd_update_seeds(vd_ctx* c, const int32_t* remove_ids, int32_t n_r
     return rc;
   }
   // validate first: nothing of the context changes unless every removal
-  // names a distinct seed and every new seed lies on the grid
+  // names a distinct seed and every new seed lies on the grid.  Host inputs
+  // are checked on the host (the update then stays asynchronous); device
+  // inputs by the flagging kernels, read back once.
+  if (!on_device) {
+    std::vector<char> seen(static_cast<size_t>(c->n), 0);
+    for (int32_t j = 0; j < n_remove && !rc; ++j) {
+      const int32_t id = remove_ids[j];
+      if (id < 0 || id >= c->n) rc = vd_fail(VD_EINVAL, "removal %d names seed %d of %d", j, id, c->n);
+      else if (seen[id]++) rc = vd_fail(VD_EINVAL, "seed %d removed twice", id);
+    }
+    for (int32_t j = 0; j < n_add && !rc; ++j) {
+      const int32_t x = add_xy[2 * j], y = add_xy[2 * j + 1];
+      if (x < 0 || x >= c->w || y < 0 || y >= c->h)
+        rc = vd_fail(VD_EINVAL, "new seed %d at (%d, %d) outside the %dx%d grid", j, x, y, c->w, c->h);
+    }
+    if (rc) {
+      release();
+      return rc;
+    }
+  }
   vdk::k_fill_i32<<<std::min((c->n + 255) / 256, 152 * 8), 256, 0, st>>>(keep, c->n, 1);
   if (n_remove > 0)
     vdk::k_update_remove<<<(n_remove + 255) / 256, 256, 0, st>>>(rem, n_remove, c->n, keep, c->counters + 2);
-  if (n_add > 0) vdk::k_check_seeds<<<(n_add + 255) / 256, 256, 0, st>>>(add, n_add, c->w, c->h, c->counters + 2);
-  c->launches += 1 + (n_remove > 0) + (n_add > 0);
+  c->launches += 1 + (n_remove > 0);
   rc = vd_cuda_check(cudaGetLastError(), "validate update");
-  if (!rc) rc = vd_cuda_check(cudaMemcpyAsync(c->host_counters + 2, c->counters + 2, sizeof(unsigned long long),
-                                              cudaMemcpyDeviceToHost, st), "copy flag");
-  if (!rc) rc = vd_cuda_check(cudaStreamSynchronize(st), "synchronize");
-  if (!rc && c->host_counters[2] != 0)
-    rc = vd_fail(VD_EINVAL, "%llu invalid entries (a removal out of range or repeated, or a new seed off the grid)",
-                 c->host_counters[2]);
+  if (!rc && on_device) {
+    if (n_add > 0) vdk::k_check_seeds<<<(n_add + 255) / 256, 256, 0, st>>>(add, n_add, c->w, c->h, c->counters + 2);
+    c->launches += n_add > 0;
+    rc = vd_cuda_check(cudaGetLastError(), "validate update");
+    if (!rc) rc = vd_cuda_check(cudaMemcpyAsync(c->host_counters + 2, c->counters + 2, sizeof(unsigned long long),
+                                                cudaMemcpyDeviceToHost, st), "copy flag");
+    if (!rc) rc = vd_cuda_check(cudaStreamSynchronize(st), "synchronize");
+    if (!rc && c->host_counters[2] != 0)
+      rc = vd_fail(VD_EINVAL, "%llu invalid entries (a removal out of range or repeated, or a new seed off the grid)",
+                   c->host_counters[2]);
+  }
   if (rc) {
     release();
     return rc;
