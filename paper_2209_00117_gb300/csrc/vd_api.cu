@@ -973,8 +973,11 @@ extern "C" int vd_djfa_step(vd_ctx* c, int32_t d_max, int32_t vn_waves, int32_t 
     const int rc = vdi::launch_stamp(view(c), c->buf[c->cur], true, c->stream, &c->launches, c->tune.pdl != 0);
     if (pr) pr->end(pi, c->stream);
     if (rc) return rc;
+    // a repair frame's map is right except in the emptied cells: the key
+    // choices of a dJFA frame suit it (a quad that sees only empty labels
+    // falls back to the exact key)
     return vdi::run_passes(view(c), c->buf, &c->cur, ks, nbs, n, metric, c->tune, c->stream, &c->launches, pr,
-                           !repair);
+                           true);
   };
   const int rc = run_frame(c, std::make_tuple(1, c->cur, d_max, vn_waves, extra, metric, repair ? 1 : 0), nl + 2,
                            cur_after, body);
