@@ -42,13 +42,17 @@ def _sim(vd, w, h, xy, **opts):
 SHAPES = [(1, 1), (1, 9), (13, 1), (5, 3), (37, 29), (64, 64), (100, 37), (257, 129), (300, 200)]
 
 
+@pytest.mark.parametrize("clamp,dedup", [(-1, -1), (1, 1), (0, 1)])
 @pytest.mark.parametrize("w,h", SHAPES)
-def test_single_pass_matches_oracle(vd, orc, w, h):
+def test_single_pass_matches_oracle(vd, orc, w, h, clamp, dedup):
+    """One pass at every kind of step (vector, k = 1, 2, scalar), both
+    neighbourhoods and metrics, in the default, forced 32-bit and forced exact
+    key forms with and without de-duplicated gathers, over random maps."""
     g = np.random.default_rng(w * 1000 + h)
     s = max(1, min(40, w * h // 3))
     xy = inputs.uniform_seeds(w, h, s, seed=w + h)
     src = g.integers(-1, s, size=(h, w), dtype=np.int32)
-    sim = _sim(vd, w, h, xy)
+    sim = _sim(vd, w, h, xy, clamped_keys=clamp, dedup_gathers=dedup)
     for k in [1, 2, 3, 4, 5, 6, 8, 12, 16, 64, 256, 1024]:
         for nb in [M, VN]:
             for metric in [E, L1]:
