@@ -335,8 +335,8 @@ def run_ours(args):
     dj.jfa(metric=metric)  # frame 0 of the dJFA chain
 
     def djfa_step(i):
-        dj.move(disp_dev[i])
-        dj.djfa_step(d_max=d, vn_waves=2, extra=args.extra, metric=metric)
+        # move + stamp + passes: one vd_step call (one graph)
+        dj.step(disp_dev[i], d_max=d, vn_waves=2, extra=args.extra, metric=metric)
 
     def jfa_step(i):
         jf.move(disp_dev[i])
@@ -393,14 +393,12 @@ def run_ours(args):
     pr.set_seeds(xy)
     pr.jfa(metric=metric)
     for i in range(W):
-        pr.move(disp_dev[i])
-        pr.djfa_step(d_max=d, vn_waves=2, extra=args.extra, metric=metric)
+        pr.step(disp_dev[i], d_max=d, vn_waves=2, extra=args.extra, metric=metric)
     pr.set_option(vd.OPT_PROFILE, 1)
     pr.profile_reset()
     for j in range(K):
         flush.zero_()
-        pr.move(disp_dev[W + j])
-        pr.djfa_step(d_max=d, vn_waves=2, extra=args.extra, metric=metric)
+        pr.step(disp_dev[W + j], d_max=d, vn_waves=2, extra=args.extra, metric=metric)
     prof = pr.profile()
     pr.close()
     dom = max(prof, key=lambda k: prof[k]["ms"])
@@ -445,8 +443,7 @@ def run_ours(args):
         pin_disp = torch.from_numpy(disp_host).pin_memory()
         pin_out = [torch.empty((h, w), dtype=torch.int32).pin_memory() for _ in range(2)]
         for i in range(W):
-            ee.move(pin_disp[i])
-            ee.djfa_step(d_max=d, vn_waves=2, extra=args.extra, metric=metric)
+            ee.step(pin_disp[i], d_max=d, vn_waves=2, extra=args.extra, metric=metric)
             ee.labels_async(pin_out[i % 2])
         ee.wait_labels()
         barrier()
@@ -454,8 +451,7 @@ def run_ours(args):
         for j in range(K):
             # inputs in from pinned memory; every step's map copied out while
             # the next step computes (two read-back slots)
-            ee.move(pin_disp[W + j])
-            ee.djfa_step(d_max=d, vn_waves=2, extra=args.extra, metric=metric)
+            ee.step(pin_disp[W + j], d_max=d, vn_waves=2, extra=args.extra, metric=metric)
             ee.labels_async(pin_out[j % 2])
         ee.wait_labels()
         barrier()

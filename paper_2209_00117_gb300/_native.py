@@ -44,6 +44,7 @@ SIGNATURES = {
     "vd_update_seeds": (_int, [_p, _p, _i32, _p, _i32, _int]),
     "vd_jfa": (_int, [_p, _i32, _i32]),
     "vd_djfa_step": (_int, [_p, _i32, _i32, _i32, _i32]),
+    "vd_step": (_int, [_p, _p, _int, _i32, _u64, _u64, _i64, _i32, _i32, _i32, _i32]),
     "vd_stamp": (_int, [_p]),
     "vd_pass": (_int, [_p, _i32, _i32, _i32]),
     "vd_set_labels": (_int, [_p, _p, _int]),

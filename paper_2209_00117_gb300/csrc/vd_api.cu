@@ -401,7 +401,20 @@ int launch_stamp(const MapView& m, int32_t* labels, bool mark, cudaStream_t st, 
 
 int launch_move(int2* seeds, int2* table, uint32_t* ptable, int n, const int2* dxy, int w, int h, int max_disp,
                 uint64_t key, uint64_t step, cudaStream_t st) {
-  vdk::k_move<<<grid1d(n, 256), 256, 0, st>>>(seeds, table, ptable, n, dxy, w, h, max_disp, key, step);
+  vdk::MoveArgs a;
+  a.seeds = seeds;
+  a.table = table;
+  a.ptable = ptable;
+  a.n = n;
+  a.dxy = dxy;
+  a.w = w;
+  a.h = h;
+  a.max_disp = max_disp;
+  a.key = key;
+  a.step = step;
+  a.mark = nullptr;
+  a.pitch = 0;
+  vdk::k_move<<<grid1d(n, 256), 256, 0, st>>>(a);
   return vd_cuda_check(cudaGetLastError(), "move launch");
 }
 
@@ -517,10 +530,25 @@ struct vd_ctx {
   vdi::Tuning tune;
   vdi::Profiler prof;
   int64_t launches = 0;
-  std::map<std::tuple<int, int, int, int, int, int, int>, cudaGraphExec_t> graphs;
+  // captured frames: the executable graph, and for a whole step the graph and
+  // its move node, whose arguments change every call
+  struct FrameGraph {
+    cudaGraphExec_t exec = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphNode_t move = nullptr;
+  };
+  std::map<std::tuple<int, int, int, int, int, int, int>, FrameGraph> graphs;
 };
 
 static vdi::Profiler* prof_of(vd_ctx* c) { return c->tune.profile ? &c->prof : nullptr; }
+
+static void clear_graphs(vd_ctx* c) {
+  for (auto& kv : c->graphs) {
+    cudaGraphExecDestroy(kv.second.exec);
+    if (kv.second.graph) cudaGraphDestroy(kv.second.graph);
+  }
+  c->graphs.clear();
+}
 
 static vdi::MapView view(const vd_ctx* c) {
   vdi::MapView m;
@@ -553,8 +581,7 @@ static void ctx_free(vd_ctx* c) {
   }
   if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
   c->prof.destroy();
-  for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
-  c->graphs.clear();
+  clear_graphs(c);
   cudaFree(c->buf[0]);
   cudaFree(c->buf[1]);
   cudaFree(c->seeds);
@@ -626,8 +653,7 @@ extern "C" int vd_destroy(vd_ctx* c) {
 extern "C" int vd_set_stream(vd_ctx* c, void* stream) {
   VD_CHECK_CTX(c);
   c->stream = static_cast<cudaStream_t>(stream);
-  for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
-  c->graphs.clear();
+  clear_graphs(c);
   return VD_OK;
 }
 
@@ -834,8 +860,7 @@ extern "C" int vd_update_seeds(vd_ctx* c, const int32_t* remove_ids, int32_t n_r
   c->n = static_cast<int32_t>(n_new);
   if (n_remove > 0) c->repair = true;
   // captured frames hold the old seed count and buffers
-  for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
-  c->graphs.clear();
+  clear_graphs(c);
   ++c->launches;
   return vdi::launch_build_table(c->seeds, c->n, c->table, c->ptable, st);
 }
@@ -885,9 +910,12 @@ static int check_metric(int32_t metric) {
 
 // Runs a frame body either eagerly or as a cached CUDA graph.  `key` must
 // identify the launch sequence completely (it includes the buffer parity).
+// With `move`, the body's first launch is the move kernel, whose arguments
+// (displacements, RNG step) change every call: the graph keeps that node and
+// its arguments are replaced before each launch.
 template <typename F>
 static int run_frame(vd_ctx* c, const std::tuple<int, int, int, int, int, int, int>& key, int n_launch,
-                     int cur_after, F&& body) {
+                     int cur_after, F&& body, const vdk::MoveArgs* move = nullptr) {
   if (!c->tune.use_graphs || c->tune.profile || c->stream == nullptr) {
     return body();
   }
@@ -908,13 +936,50 @@ static int run_frame(vd_ctx* c, const std::tuple<int, int, int, int, int, int, i
     }
     rc = vd_cuda_check(ee, "end capture");
     if (rc) return rc;
-    cudaGraphExec_t ex = nullptr;
-    rc = vd_cuda_check(cudaGraphInstantiate(&ex, g, 0), "graph instantiate");
-    cudaGraphDestroy(g);
-    if (rc) return rc;
-    it = c->graphs.emplace(key, ex).first;
+    vd_ctx::FrameGraph fg;
+    if (move) {
+      // the move node: the graph's kernel node running vdk::k_move
+      size_t count = 0;
+      rc = vd_cuda_check(cudaGraphGetNodes(g, nullptr, &count), "graph nodes");
+      std::vector<cudaGraphNode_t> nodes(count);
+      if (!rc && count) rc = vd_cuda_check(cudaGraphGetNodes(g, nodes.data(), &count), "graph nodes");
+      for (size_t i = 0; !rc && i < count && !fg.move; ++i) {
+        cudaGraphNodeType t;
+        if (cudaGraphNodeGetType(nodes[i], &t) != cudaSuccess || t != cudaGraphNodeTypeKernel) continue;
+        cudaKernelNodeParams p;
+        if (cudaGraphKernelNodeGetParams(nodes[i], &p) == cudaSuccess &&
+            p.func == reinterpret_cast<void*>(vdk::k_move))
+          fg.move = nodes[i];
+      }
+      if (!rc && !fg.move) rc = vd_fail(VD_ECUDA, "captured step has no move kernel");
+      if (rc) {
+        cudaGraphDestroy(g);
+        return rc;
+      }
+    }
+    rc = vd_cuda_check(cudaGraphInstantiate(&fg.exec, g, 0), "graph instantiate");
+    if (rc) {
+      cudaGraphDestroy(g);
+      return rc;
+    }
+    if (move) fg.graph = g;  // kept: its move node addresses the executable's copy
+    else cudaGraphDestroy(g);
+    it = c->graphs.emplace(key, fg).first;
   }
-  const int rc = vd_cuda_check(cudaGraphLaunch(it->second, c->stream), "graph launch");
+  if (move) {
+    cudaKernelNodeParams p{};
+    p.func = reinterpret_cast<void*>(vdk::k_move);
+    p.gridDim = dim3((c->n + 255) / 256);
+    p.blockDim = dim3(256);
+    p.sharedMemBytes = 0;
+    vdk::MoveArgs a = *move;
+    void* args[] = {&a};
+    p.kernelParams = args;
+    p.extra = nullptr;
+    const int rc = vd_cuda_check(cudaGraphExecKernelNodeSetParams(it->second.exec, it->second.move, &p), "step arguments");
+    if (rc) return rc;
+  }
+  const int rc = vd_cuda_check(cudaGraphLaunch(it->second.exec, c->stream), "graph launch");
   if (rc) return rc;
   c->cur = cur_after;
   c->launches += n_launch;
@@ -981,6 +1046,73 @@ extern "C" int vd_djfa_step(vd_ctx* c, int32_t d_max, int32_t vn_waves, int32_t 
   };
   const int rc = run_frame(c, std::make_tuple(1, c->cur, d_max, vn_waves, extra, metric, repair ? 1 : 0), nl + 2,
                            cur_after, body);
+  if (!rc) c->repair = false;
+  return rc;
+}
+
+extern "C" int vd_step(vd_ctx* c, const int32_t* dxy, int dxy_on_device, int32_t max_disp, uint64_t rng_seed,
+                       uint64_t stream_id, int64_t step, int32_t d_max, int32_t vn_waves, int32_t extra,
+                       int32_t metric) {
+  VD_CHECK_CTX(c);
+  if (check_metric(metric)) return VD_EINVAL;
+  // the move, as vd_move_seeds, with the stamp's first half folded in
+  vdk::MoveArgs ma;
+  ma.seeds = c->seeds;
+  ma.table = c->table;
+  ma.ptable = c->ptable;
+  ma.n = c->n;
+  ma.dxy = nullptr;
+  ma.w = c->w;
+  ma.h = c->h;
+  ma.max_disp = max_disp;
+  ma.key = vdi::rng_key(rng_seed, stream_id);
+  ma.step = static_cast<uint64_t>(step);
+  ma.mark = c->buf[c->cur];
+  ma.pitch = c->pitch;
+  if (dxy) {
+    if (dxy_on_device) {
+      if (reinterpret_cast<uintptr_t>(dxy) % alignof(int2) != 0)
+        return vd_fail(VD_EINVAL, "device displacements must be 8-byte aligned");
+      ma.dxy = reinterpret_cast<const int2*>(dxy);
+    } else {
+      ma.dxy = c->dxy_stage;
+    }
+  } else {
+    if (max_disp < 0 || max_disp > VD_MAX_SIDE) return vd_fail(VD_EINVAL, "max_disp %d outside [0, %d]", max_disp, VD_MAX_SIDE);
+    if (step < 0) return vd_fail(VD_EINVAL, "step %lld < 0", static_cast<long long>(step));
+  }
+  int32_t ks[VD_MAX_PASSES], nbs[VD_MAX_PASSES];
+  int n = vd_djfa_schedule(c->w, c->h, c->n, d_max, vn_waves, extra, ks, nbs, VD_MAX_PASSES);
+  if (n < 0) return n;
+  const bool repair = c->repair;
+  if (repair) {
+    n = vd_jfa_schedule(c->w, c->h, extra, ks, nbs, VD_MAX_PASSES);
+    if (n < 0) return n;
+  }
+  if (dxy && !dxy_on_device) {
+    const int rc = vd_cuda_check(cudaMemcpyAsync(c->dxy_stage, dxy, sizeof(int2) * c->n, cudaMemcpyHostToDevice,
+                                                 c->stream), "copy moves");
+    if (rc) return rc;
+  }
+  const int nl = count_launches(ks, nbs, n, c->tune);
+  const int cur_after = c->cur ^ (nl & 1);
+  auto body = [&]() -> int {
+    vdi::Profiler* pr = prof_of(c);
+    int pi = pr ? pr->begin(VD_KERNEL_MOVE, c->n, c->stream) : -1;
+    vdk::k_move<<<(c->n + 255) / 256, 256, 0, c->stream>>>(ma);
+    if (pr) pr->end(pi, c->stream);
+    ++c->launches;
+    int rc = vd_cuda_check(cudaGetLastError(), "move launch");
+    if (rc) return rc;
+    pi = pr ? pr->begin(VD_KERNEL_STAMP, c->n, c->stream) : -1;
+    rc = vdi::launch_stamp(view(c), c->buf[c->cur], false, c->stream, &c->launches, c->tune.pdl != 0);
+    if (pr) pr->end(pi, c->stream);
+    if (rc) return rc;
+    return vdi::run_passes(view(c), c->buf, &c->cur, ks, nbs, n, metric, c->tune, c->stream, &c->launches, pr,
+                           true);
+  };
+  const int rc = run_frame(c, std::make_tuple(2, c->cur, d_max, vn_waves, extra, metric, repair ? 1 : 0), nl + 2,
+                           cur_after, body, &ma);
   if (!rc) c->repair = false;
   return rc;
 }
@@ -1230,8 +1362,7 @@ extern "C" int vd_set_option(vd_ctx* c, int32_t option, int64_t value) {
   const size_t smem = 2ull * (t.tile_x + 2 * t.max_halo) * (t.tile_y + 2 * t.max_halo) * sizeof(int32_t);
   if (smem > 220 * 1024) return vd_fail(VD_EINVAL, "fused tile needs %zu bytes of shared memory", smem);
   c->tune = t;
-  for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
-  c->graphs.clear();
+  clear_graphs(c);
   return VD_OK;
 }
 

@@ -652,31 +652,43 @@ static __global__ void k_check_labels(const int32_t* __restrict__ labels, int64_
   }
 }
 
+struct MoveArgs {
+  int2* seeds;
+  int2* table;
+  uint32_t* ptable;
+  int n;
+  const int2* dxy;  // given displacements, or null: SplitMix64 draws in [-max_disp, max_disp]
+  int w, h, max_disp;
+  uint64_t key, step;
+  int32_t* mark;    // non-null: also the stamp's first half on this map (pitch below)
+  int pitch;
+};
+
 // SimulateParticles (Algorithm 1): p_k <- clamp(p_k + delta_k) on the grid;
-// also refreshes the seed's pass-table entry.
-static __global__ void k_move(int2* __restrict__ seeds, int2* __restrict__ table, uint32_t* __restrict__ ptable,
-                              int n, const int2* __restrict__ dxy, int w, int h, int max_disp, uint64_t key,
-                              uint64_t step) {
+// also refreshes the seed's pass-table entries and, when a.mark is set,
+// writes k at its new pixel (the first half of the stamp that follows).
+static __global__ void k_move(MoveArgs a) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= n) return;
-  int2 p = seeds[k];
+  if (k >= a.n) return;
+  int2 p = a.seeds[k];
   long long dx, dy;
-  if (dxy != nullptr) {
-    const int2 d = dxy[k];
+  if (a.dxy != nullptr) {
+    const int2 d = a.dxy[k];
     dx = d.x;
     dy = d.y;
   } else {
-    dx = rng_disp(key, step, static_cast<uint64_t>(k), 0, max_disp);
-    dy = rng_disp(key, step, static_cast<uint64_t>(k), 1, max_disp);
+    dx = rng_disp(a.key, a.step, static_cast<uint64_t>(k), 0, a.max_disp);
+    dy = rng_disp(a.key, a.step, static_cast<uint64_t>(k), 1, a.max_disp);
   }
   long long x = p.x + dx, y = p.y + dy;
-  x = x < 0 ? 0 : (x > w - 1 ? w - 1 : x);
-  y = y < 0 ? 0 : (y > h - 1 ? h - 1 : y);
+  x = x < 0 ? 0 : (x > a.w - 1 ? a.w - 1 : x);
+  y = y < 0 ? 0 : (y > a.h - 1 ? a.h - 1 : y);
   p.x = static_cast<int>(x);
   p.y = static_cast<int>(y);
-  seeds[k] = p;
-  table[k + 1] = table_entry(p);
-  ptable[k + 1] = pack_pos(p.x, p.y);
+  a.seeds[k] = p;
+  a.table[k + 1] = table_entry(p);
+  a.ptable[k + 1] = pack_pos(p.x, p.y);
+  if (a.mark != nullptr) a.mark[static_cast<int64_t>(p.y) * a.pitch + p.x] = k;
 }
 
 // Stamp, first half: every seed pixel is overwritten with one of the indices

@@ -232,6 +232,14 @@ class VoronoiSim:
     def djfa_step(self, d_max: int, vn_waves: int = 2, extra: int = 0, metric: int = EUCLID):
         N.check(self._lib.vd_djfa_step(self._h, int(d_max), int(vn_waves), int(extra), int(metric)))
 
+    def step(self, dxy=None, max_disp: int = 0, rng_seed: int = 0, stream_id: int = 0, step: int = 0,
+             d_max: int = 1, vn_waves: int = 2, extra: int = 0, metric: int = EUCLID):
+        """move() then djfa_step() as one call (one graph with OPT_USE_GRAPHS)."""
+        ptr, dev = _buf(dxy, 2 * self.n_seeds)
+        N.check(self._lib.vd_step(self._h, ptr, dev, int(max_disp), int(rng_seed) & (2**64 - 1),
+                                  int(stream_id) & (2**64 - 1), int(step), int(d_max), int(vn_waves),
+                                  int(extra), int(metric)))
+
     def stamp(self):
         N.check(self._lib.vd_stamp(self._h))
 

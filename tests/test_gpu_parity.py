@@ -441,3 +441,48 @@ def test_dependent_launch_chain_matches_oracle(vd, orc, graphs):
             np.testing.assert_array_equal(off.labels(), lab)
     on.close()
     off.close()
+
+
+@pytest.mark.parametrize("graphs", [0, 1])
+@pytest.mark.parametrize("moves", ["host", "device", "rng"])
+def test_step_equals_move_then_frame(vd, orc, graphs, moves):
+    """vd_step (the move with the stamp's first half folded in, one graph per
+    step) equals vd_move_seeds + vd_djfa_step and the oracle, across buffer
+    parities, a seed update (repair frame) and both metrics."""
+    import torch
+
+    w, h, s, D = 700, 500, 3000, 3
+    xy = inputs.uniform_seeds(w, h, s, seed=31)
+    a = _sim(vd, w, h, xy, use_graphs=graphs)
+    b = _sim(vd, w, h, xy, use_graphs=graphs)
+    a.jfa()
+    b.jfa()
+    lab = orc.jfa(w, h, xy)
+    g = np.random.default_rng(4)
+    for t in range(8):
+        metric = E if t < 5 else L1
+        if t == 3:  # a seed update: the next frame is the repair frame
+            remove = g.choice(len(xy), 40, replace=False).astype(np.int32)
+            add = np.stack([g.integers(0, w, 25), g.integers(0, h, 25)], axis=1).astype(np.int32)
+            for sim in (a, b):
+                sim.update_seeds(remove, add)
+            xy, lab = orc.update_seeds(w, h, xy, lab, remove, add)
+        n = len(xy)
+        if moves == "rng":
+            a.step(None, max_disp=D, rng_seed=9, stream_id=0, step=t, d_max=D, metric=metric)
+            b.move(None, max_disp=D, rng_seed=9, stream_id=0, step=t)
+            xy = orc.move_rng(w, h, xy, D, 9, 0, t)
+        else:
+            d = inputs.step_displacements(n, D, t, seed=5)
+            dd = torch.from_numpy(d).cuda() if moves == "device" else d
+            a.step(dd, d_max=D, metric=metric)
+            b.move(dd)
+            xy = orc.move(w, h, xy, d)
+        b.djfa_step(d_max=D, metric=metric)
+        lab = orc.repair_step(w, h, xy, lab, metric=metric) if t == 3 else \
+            orc.djfa_step(w, h, xy, lab, d_max=D, metric=metric)
+        np.testing.assert_array_equal(a.labels(), lab, err_msg=f"step {t}")
+        np.testing.assert_array_equal(b.labels(), lab, err_msg=f"step {t}")
+        np.testing.assert_array_equal(a.get_seeds(), xy)
+    a.close()
+    b.close()
