@@ -6,6 +6,7 @@
 #include <cstdarg>
 #include <cstdint>
 #include <cstdio>
+#include <cmath>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -203,8 +204,42 @@ bool use_clamp(int clamp_option, int32_t metric, int32_t n, int32_t k, bool djfa
   return djfa_frame;
 }
 
+// Label bits of the byte-offset key: the least lb with 2^lb > n, so that the
+// all-ones label field of an empty label names no seed.
+static int byte_label_bits(int64_t n) {
+  int lb = 0;
+  while ((int64_t{1} << lb) <= n) ++lb;
+  return lb;
+}
+
+// Half-width h of the byte-offset key's window: the largest power of two up
+// to 128 (dx and dy must fit a signed byte) with (2h^2 + 1) * 2^lb <= 2^32,
+// so that d * 2^lb + label cannot wrap inside the window; 0 if none.
+int byte_window(int64_t n) {
+  const int lb = byte_label_bits(n);
+  for (uint64_t h = 128; h >= 1; h >>= 1) {
+    if (((2 * h * h + 1) << lb) <= (uint64_t{1} << 32)) return static_cast<int>(h);
+  }
+  return 0;
+}
+
+bool use_byte_key(int byte_option, int32_t metric, int32_t w, int32_t h, int32_t n, int32_t k,
+                  bool djfa_frame) {
+  // the form falls back to the clamped one, usable from 9 seeds on
+  if (byte_option == 0 || metric != VD_METRIC_EUCLID || label_bits(n) < 4) return false;
+  const int hw = byte_window(n);
+  if (hw < 2) return false;
+  if (byte_option == 1) return true;
+  if (!djfa_frame) return false;
+  // auto: dJFA passes whose step plus three mean cell radii stays inside the
+  // window, so that a winner outside it (a recomputed quad) stays rare
+  const double r = std::sqrt(static_cast<double>(w) * h / (3.141592653589793 * n));
+  return k + 3.0 * r <= hw - 1;
+}
+
 int launch_pass(const MapView& m, const int32_t* src, int32_t* dst, int32_t k, int32_t nb,
-                int32_t metric, int64_t band_min_k, bool clamp, cudaStream_t st, bool pdl, bool dedup) {
+                int32_t metric, int64_t band_min_k, bool clamp, cudaStream_t st, bool pdl, bool dedup,
+                bool byte_key) {
   vdk::PassArgs a;
   a.src = src;
   a.dst = dst;
@@ -214,6 +249,12 @@ int launch_pass(const MapView& m, const int32_t* src, int32_t* dst, int32_t k, i
     const int lb = label_bits(m.n);
     a.mul = lb >= 32 ? 0u : (1u << lb);
     a.cap = lb >= 4 ? static_cast<uint32_t>((uint64_t{1} << (32 - lb)) - 1) : 0u;
+    const uint32_t hw = static_cast<uint32_t>(byte_window(m.n));
+    const int blb = byte_label_bits(m.n);
+    a.bmul = blb >= 32 ? 0u : (1u << blb);
+    a.bwin_bias = hw * 0x10001u;
+    a.bwin_mask = hw ? (0xFFFFu & ~(2u * hw - 1u)) * 0x10001u : 0xFFFFFFFFu;
+    a.blim = hw * hw * a.bmul;
   }
   a.n_seeds = static_cast<uint32_t>(m.n);
   a.w = m.w;
@@ -241,17 +282,19 @@ int launch_pass(const MapView& m, const int32_t* src, int32_t* dst, int32_t k, i
     grid.y = a.band_m * a.band_t;
   }
   const int ksel = (k % 4 == 0) ? 0 : (k == 1 ? 1 : (k == 2 ? 2 : 3));
-  // key form: 0 exact 64-bit, 1 32-bit, 2 clamped Manhattan 32-bit
+  // key form: 0 exact 64-bit, 1 32-bit, 2 clamped Manhattan 32-bit, 3 byte-offset
   int key = 0;
   if (clamp) {
     if (metric == VD_METRIC_MANHATTAN) key = label_bits(m.n) <= 15 ? 1 : 2;
     else if (a.cap != 0) key = 1;
   }
+  if (byte_key && metric == VD_METRIC_EUCLID && a.cap != 0 && byte_window(m.n) >= 2) key = 3;
   cudaError_t e;
   if (nb == VD_NB_MOORE) {
     if (metric == VD_METRIC_EUCLID) {
-      e = key ? launch_pass_t<vdk::kMoore, vdk::kEuclid, 1>(ksel, dedup, grid, block, st, pdl, a)
-              : launch_pass_t<vdk::kMoore, vdk::kEuclid, 0>(ksel, dedup, grid, block, st, pdl, a);
+      e = key == 3 ? launch_pass_t<vdk::kMoore, vdk::kEuclid, 3>(ksel, dedup, grid, block, st, pdl, a)
+          : key    ? launch_pass_t<vdk::kMoore, vdk::kEuclid, 1>(ksel, dedup, grid, block, st, pdl, a)
+                   : launch_pass_t<vdk::kMoore, vdk::kEuclid, 0>(ksel, dedup, grid, block, st, pdl, a);
     } else {
       e = key == 2 ? launch_pass_t<vdk::kMoore, vdk::kManhattan, 2>(ksel, dedup, grid, block, st, pdl, a)
           : key    ? launch_pass_t<vdk::kMoore, vdk::kManhattan, 1>(ksel, dedup, grid, block, st, pdl, a)
@@ -259,8 +302,9 @@ int launch_pass(const MapView& m, const int32_t* src, int32_t* dst, int32_t k, i
     }
   } else {
     if (metric == VD_METRIC_EUCLID) {
-      e = key ? launch_pass_t<vdk::kVonNeumann, vdk::kEuclid, 1>(ksel, dedup, grid, block, st, pdl, a)
-              : launch_pass_t<vdk::kVonNeumann, vdk::kEuclid, 0>(ksel, dedup, grid, block, st, pdl, a);
+      e = key == 3 ? launch_pass_t<vdk::kVonNeumann, vdk::kEuclid, 3>(ksel, dedup, grid, block, st, pdl, a)
+          : key    ? launch_pass_t<vdk::kVonNeumann, vdk::kEuclid, 1>(ksel, dedup, grid, block, st, pdl, a)
+                   : launch_pass_t<vdk::kVonNeumann, vdk::kEuclid, 0>(ksel, dedup, grid, block, st, pdl, a);
     } else {
       e = key == 2 ? launch_pass_t<vdk::kVonNeumann, vdk::kManhattan, 2>(ksel, dedup, grid, block, st, pdl, a)
           : key    ? launch_pass_t<vdk::kVonNeumann, vdk::kManhattan, 1>(ksel, dedup, grid, block, st, pdl, a)
@@ -353,7 +397,8 @@ int run_passes(const MapView& m, int32_t* const buf[2], int* cur, const int32_t*
     if (l.n == 1) {
       rc = launch_pass(m, src, dst, ks[l.first], nbs[l.first], metric, t.band_min_k,
                        use_clamp(t.clamp, metric, m.n, ks[l.first], djfa_frame), st, t.pdl != 0,
-                       use_dedup(t.dedup, m.w, m.h, m.n, djfa_frame));
+                       use_dedup(t.dedup, m.w, m.h, m.n, djfa_frame),
+                       use_byte_key(t.byte_key, metric, m.w, m.h, m.n, ks[l.first], djfa_frame));
     } else {
       rc = launch_fused(m, src, dst, ks + l.first, nbs + l.first, l.n, metric, t.tile_x, t.tile_y, st);
     }
@@ -1129,7 +1174,8 @@ extern "C" int vd_pass(vd_ctx* c, int32_t k, int32_t nb, int32_t metric) {
   if (nb != VD_NB_MOORE && nb != VD_NB_VON_NEUMANN) return vd_fail(VD_EINVAL, "neighbourhood %d", nb);
   const int rc = vdi::launch_pass(view(c), c->buf[c->cur], c->buf[c->cur ^ 1], k, nb, metric,
                                   c->tune.band_min_k, vdi::use_clamp(c->tune.clamp, metric, c->n, k, false),
-                                  c->stream, false, vdi::use_dedup(c->tune.dedup, c->w, c->h, c->n, false));
+                                  c->stream, false, vdi::use_dedup(c->tune.dedup, c->w, c->h, c->n, false),
+                                  vdi::use_byte_key(c->tune.byte_key, metric, c->w, c->h, c->n, k, false));
   if (rc) return rc;
   ++c->launches;
   c->cur ^= 1;
@@ -1356,6 +1402,10 @@ extern "C" int vd_set_option(vd_ctx* c, int32_t option, int64_t value) {
       if (value < -1 || value > 1) return vd_fail(VD_EINVAL, "dedup must be -1, 0 or 1");
       t.dedup = static_cast<int>(value);
       break;
+    case VD_OPT_BYTE_KEYS:
+      if (value < -1 || value > 1) return vd_fail(VD_EINVAL, "byte keys must be -1, 0 or 1");
+      t.byte_key = static_cast<int>(value);
+      break;
     default:
       return vd_fail(VD_EINVAL, "unknown option %d", option);
   }
@@ -1379,6 +1429,7 @@ extern "C" int vd_get_option(const vd_ctx* c, int32_t option, int64_t* value) {
     case VD_OPT_CLAMPED_KEYS: *value = c->tune.clamp; break;
     case VD_OPT_PDL: *value = c->tune.pdl; break;
     case VD_OPT_DEDUP_GATHERS: *value = c->tune.dedup; break;
+    case VD_OPT_BYTE_KEYS: *value = c->tune.byte_key; break;
     default: return vd_fail(VD_EINVAL, "unknown option %d", option);
   }
   return VD_OK;

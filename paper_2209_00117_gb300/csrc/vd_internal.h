@@ -40,6 +40,7 @@ struct Tuning {
   int clamp = -1;  // clamped 32-bit keys: -1 auto, 0 never, 1 whenever usable
   int pdl = 1;     // chain a frame's kernels with programmatic dependent launch
   int dedup = -1;  // skip repeated table gathers in a label vector: -1 auto, 0 never, 1 always
+  int byte_key = -1;  // Euclidean byte-offset keys: -1 auto, 0 never, 1 whenever usable
 };
 
 // Event pairs bracketing kernel launches (profiling mode).  Records are kept
@@ -80,8 +81,11 @@ std::vector<Launch> plan_passes(const int32_t* ks, const int32_t* nbs, int n, in
                                 int max_halo);
 int launch_pass(const MapView& m, const int32_t* src, int32_t* dst, int32_t k, int32_t nb,
                 int32_t metric, int64_t band_min_k, bool clamp, cudaStream_t st, bool pdl = false,
-                bool dedup = false);
+                bool dedup = false, bool byte_key = false);
 bool use_dedup(int dedup_option, int32_t w, int32_t h, int32_t n, bool djfa_frame);
+int byte_window(int64_t n);
+bool use_byte_key(int byte_option, int32_t metric, int32_t w, int32_t h, int32_t n, int32_t k,
+                  bool djfa_frame);
 int launch_fused(const MapView& m, const int32_t* src, int32_t* dst, const int32_t* ks,
                  const int32_t* nbs, int n, int32_t metric, int tile_x, int tile_y,
                  cudaStream_t st);

@@ -121,6 +121,10 @@ struct PassArgs {
   uint32_t cap;                         // clamped-key passes: distance cap 2^(32 - lb) - 1
   uint32_t mul;                         // and 2^lb, lb = bits of the largest label
   uint32_t n_seeds;
+  // byte-offset passes: bmul = 2^lb' > n_seeds, window half-width h, and
+  // bwin_bias = h * 0x10001, bwin_mask = (0xFFFF & ~(2h - 1)) * 0x10001,
+  // blim = h^2 * bmul
+  uint32_t bmul, bwin_bias, bwin_mask, blim;
   int w, h, pitch, k;
   int band_m;  // > 1: visit row-blocks in k-strided bands (band_m = k / rows per block)
   int band_t;  // row-blocks per band residue class
@@ -167,6 +171,7 @@ __host__ __device__ __forceinline__ uint32_t pack_pos(int x, int y) {
 template <int METRIC, bool COH, bool DEDUP = false>
 struct Quad {
   static constexpr bool kDedup = DEDUP;
+  static constexpr bool kFillOwn = false;
   long long b[4];
   int m2x, m2y, x0, y;
   const int2* __restrict__ table;
@@ -204,6 +209,7 @@ struct Quad {
 template <bool COH, bool DEDUP = false>
 struct Quad32 {
   static constexpr bool kDedup = DEDUP;
+  static constexpr bool kFillOwn = false;
   uint32_t b[4];
   int x0, y;
   uint32_t cap, mul;
@@ -240,6 +246,7 @@ constexpr int kManhattanFarY = 65535;
 template <bool COH, bool DEDUP = false, bool CAP = false>
 struct Quad32M {
   static constexpr bool kDedup = DEDUP;
+  static constexpr bool kFillOwn = false;
   uint32_t b[4];
   int x0, y;
   uint32_t cap, mul;
@@ -254,6 +261,50 @@ struct Quad32M {
   __device__ __forceinline__ uint32_t key(int i, int2 p, int c) const {
     const uint32_t d = static_cast<uint32_t>(abs(p.x - (x0 + i)) + p.y);
     return (CAP ? min(d, cap) : d) * mul + static_cast<uint32_t>(c);
+  }
+  __device__ __forceinline__ void set(int i, int2 p, int c) { b[i] = key(i, p, c); }
+  __device__ __forceinline__ void fold(int i, int2 p, int c) { b[i] = min(b[i], key(i, p, c)); }
+};
+
+// Byte-offset 32-bit form (Euclidean).  For a seed's packed position
+// e = x | y << 16 and a pixel (x_p, y_p), v = e - (x_p | y_p << 16) + 2^15
+// equals (dx + 2^15) + dy * 2^16 with no borrow between the halves, so bytes
+// 0 and 2 of v are dx and dy modulo 256, and one dp4a of v with those two
+// bytes gives dx^2 + dy^2, exact while both lie in [-128, 127].  The gathered
+// entry is used as it is: no unpacking per gather.  key = d * 2^lb + label
+// with 2^lb > n_seeds, so an empty label (-1) leaves all ones in the label
+// bits, which name no seed.  Inside the window dx, dy in [-h, h) (h a power of
+// two <= 128 with (2h^2 + 1) * 2^lb <= 2^32) every key is exact; outside it a
+// key may be anything.  After the fold each pixel's winner is looked up again:
+// when it lies in its pixel's window at d < h^2, every seed outside the window
+// (at d >= h^2) loses to it and every seed inside was scored exactly, so the
+// winner is the exact one; a quad where any pixel fails this is recomputed
+// with the clamped form.  The prepared position is e itself.
+template <bool COH, bool DEDUP = false>
+struct Quad8 {
+  static constexpr bool kDedup = DEDUP;
+  // an out-of-range side candidate is replaced by the same row's label at the
+  // pixel itself (a candidate the pixel scores anyway) instead of the empty
+  // label, whose key is arbitrary in this form
+  static constexpr bool kFillOwn = true;
+  uint32_t b[4];
+  int x0, y;
+  uint32_t k0, mul;
+  const uint32_t* __restrict__ ptable;
+  __device__ __forceinline__ Quad8(const PassArgs& a, int x0_, int y_)
+      : x0(x0_),
+        y(y_),
+        k0(0x8000u - (static_cast<uint32_t>(x0_) + (static_cast<uint32_t>(y_) << 16))),
+        mul(a.bmul),
+        ptable(a.ptable) {}
+  __device__ __forceinline__ int2 pos(int c) const {
+    const uint32_t e = COH ? __ldcg(&ptable[c]) : __ldg(&ptable[c]);
+    return make_int2(static_cast<int>(e), 0);
+  }
+  __device__ __forceinline__ uint32_t key(int i, int2 p, int c) const {
+    const uint32_t v = static_cast<uint32_t>(p.x) + k0 - static_cast<uint32_t>(i);
+    const int d = __dp4a(static_cast<int>(v), static_cast<int>(v & 0x00FF00FFu), 0);
+    return static_cast<uint32_t>(d) * mul + static_cast<uint32_t>(c);
   }
   __device__ __forceinline__ void set(int i, int2 p, int c) { b[i] = key(i, p, c); }
   __device__ __forceinline__ void fold(int i, int2 p, int c) { b[i] = min(b[i], key(i, p, c)); }
@@ -309,16 +360,18 @@ __device__ __forceinline__ void fold4(Q& q, const int4& L) {
 // of 4 (one aligned 16-byte load); columns outside [0, pitch) read as -1 and
 // the row padding [w, pitch) holds -1 already.
 template <bool COH>
-__device__ __forceinline__ int4 load_side(const int32_t* __restrict__ row, int x0, int dx, int pitch) {
+__device__ __forceinline__ int4 load_side(const int32_t* __restrict__ row, int x0, int dx, int pitch,
+                                          const int4& fill) {
   const int xs = x0 + dx;
-  return (xs >= 0 && xs < pitch) ? map4<COH>(row + xs) : make_int4(-1, -1, -1, -1);
+  return (xs >= 0 && xs < pitch) ? map4<COH>(row + xs) : fill;
 }
 
 template <bool COH>
-__device__ __forceinline__ int4 load_scalar4(const int32_t* __restrict__ row, int xs, int w) {
+__device__ __forceinline__ int4 load_scalar4(const int32_t* __restrict__ row, int xs, int w, const int4& fill) {
+  const int f[4] = {fill.x, fill.y, fill.z, fill.w};
   int v[4];
 #pragma unroll
-  for (int i = 0; i < 4; ++i) v[i] = (xs + i >= 0 && xs + i < w) ? map1<COH>(row + xs + i) : -1;
+  for (int i = 0; i < 4; ++i) v[i] = (xs + i >= 0 && xs + i < w) ? map1<COH>(row + xs + i) : f[i];
   return make_int4(v[0], v[1], v[2], v[3]);
 }
 
@@ -331,16 +384,19 @@ template <int KSEL, bool COH, class Q>
 __device__ __forceinline__ void fold_sides(Q& q, const int32_t* __restrict__ row, const int4& mid,
                                            const int2 (&mp)[4], const PassArgs& a) {
   const int x0 = q.x0;
+  // out-of-range candidates: the empty label, or (Q::kFillOwn) the row's own
+  // label at the pixel, which that pixel scores anyway
+  const int4 fill = Q::kFillOwn ? mid : make_int4(-1, -1, -1, -1);
   if (KSEL == 0) {
-    const int4 L = load_side<COH>(row, x0, -a.k, a.pitch);
-    const int4 R = load_side<COH>(row, x0, a.k, a.pitch);
+    const int4 L = load_side<COH>(row, x0, -a.k, a.pitch, fill);
+    const int4 R = load_side<COH>(row, x0, a.k, a.pitch, fill);
     fold4(q, L);
     group_fence();
     fold4(q, R);
   } else if (KSEL == 1) {
     // left of pixel i: column x0 + i - 1; right: x0 + i + 1
-    const int l = (x0 >= 4) ? map1<COH>(row + x0 - 1) : -1;
-    const int r = (x0 + 4 < a.pitch) ? map1<COH>(row + x0 + 4) : -1;
+    const int l = (x0 >= 4) ? map1<COH>(row + x0 - 1) : fill.x;
+    const int r = (x0 + 4 < a.pitch) ? map1<COH>(row + x0 + 4) : fill.w;
     const int2 pl = q.pos(l);
     const int2 pr = q.pos(r);
     q.fold(0, pl, l);
@@ -353,9 +409,8 @@ __device__ __forceinline__ void fold_sides(Q& q, const int32_t* __restrict__ row
     q.fold(3, pr, r);
   } else if (KSEL == 2) {
     // left of pixel i: column x0 + i - 2; right: x0 + i + 2
-    const int2 neg = make_int2(-1, -1);
-    const int2 l = (x0 >= 4) ? map2<COH>(row + x0 - 2) : neg;
-    const int2 r = (x0 + 4 < a.pitch) ? map2<COH>(row + x0 + 4) : neg;
+    const int2 l = (x0 >= 4) ? map2<COH>(row + x0 - 2) : make_int2(fill.x, fill.y);
+    const int2 r = (x0 + 4 < a.pitch) ? map2<COH>(row + x0 + 4) : make_int2(fill.z, fill.w);
     const int2 pl0 = q.pos(l.x);
     const int2 pl1 = q.pos(l.y);
     const int2 pr0 = q.pos(r.x);
@@ -369,8 +424,8 @@ __device__ __forceinline__ void fold_sides(Q& q, const int32_t* __restrict__ row
     q.fold(2, pr0, r.x);
     q.fold(3, pr1, r.y);
   } else {
-    const int4 L = load_scalar4<COH>(row, x0 - a.k, a.w);
-    const int4 R = load_scalar4<COH>(row, x0 + a.k, a.w);
+    const int4 L = load_scalar4<COH>(row, x0 - a.k, a.w, fill);
+    const int4 R = load_scalar4<COH>(row, x0 + a.k, a.w, fill);
     fold4(q, L);
     group_fence();
     fold4(q, R);
@@ -482,6 +537,42 @@ __device__ __forceinline__ void pass_quad_clamped(const PassArgs& a, int x0, int
              static_cast<int>(q.b[2] & mask), static_cast<int>(q.b[3] & mask));
 }
 
+// The byte-offset form's recomputation, out of line: it is rare, and kept
+// apart it leaves the common path the registers of the byte form alone.
+template <int NB, int KSEL, bool COH, bool DEDUP>
+__device__ __noinline__ void byte_fallback(const PassArgs a, int x0, int y) {
+  pass_quad_clamped<NB, KSEL, COH, kEuclid, DEDUP>(a, x0, y);
+}
+
+// Byte-offset form (Euclidean): the fold, then the winner check described at
+// Quad8; a quad that fails it is recomputed with the clamped form.
+template <int NB, int KSEL, bool COH = false, bool DEDUP = false>
+__device__ __forceinline__ void pass_quad_byte(const PassArgs& a, int x0, int y) {
+  Quad8<COH, DEDUP> q(a, x0, y);
+  fold_all<NB, KSEL, COH>(q, a, x0, y);
+  const uint32_t mask = a.bmul - 1u;
+  // packed positions with the far position first: the label bits plus one,
+  // masked, index it (all ones, an empty label, wrap to the far position)
+  const uint32_t* __restrict__ arena = a.ptable - 1;
+  const uint32_t kw = a.bwin_bias - (static_cast<uint32_t>(x0) + (static_cast<uint32_t>(y) << 16));
+  uint32_t bad = 0;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const uint32_t j = (q.b[i] + 1u) & mask;
+    const uint32_t e = COH ? __ldcg(&arena[j]) : __ldg(&arena[j]);
+    // (dx + h) | (dy + h) << 16 has no bit at or above 2h in either half
+    // exactly when dx, dy lie in [-h, h)
+    bad |= (e + kw - static_cast<uint32_t>(i)) & a.bwin_mask;
+  }
+  const uint32_t top = max(max(q.b[0], q.b[1]), max(q.b[2], q.b[3]));
+  if (bad != 0 || top >= a.blim) {
+    byte_fallback<NB, KSEL, COH, DEDUP>(a, x0, y);
+    return;
+  }
+  store_quad(a, x0, y, static_cast<int>(q.b[0] & mask), static_cast<int>(q.b[1] & mask),
+             static_cast<int>(q.b[2] & mask), static_cast<int>(q.b[3] & mask));
+}
+
 // Pass launch shape: 128-thread blocks (64 quads x 2 rows on wide maps), 10
 // resident per SM, which leaves 48 registers a thread: measured on the GB300
 // against 256-thread blocks at 40 and 64 registers, and 64-thread blocks, this
@@ -492,9 +583,17 @@ constexpr int kPassThreads = 128;
 #endif
 
 // KEY: 0 the exact 64-bit form, 1 the 32-bit form of METRIC, 2 the clamped
-// Manhattan 32-bit form (more than 2^15 labels).
+// Manhattan 32-bit form (more than 2^15 labels), 3 the Euclidean byte-offset
+// form.
+// The byte-offset form needs fewer registers: 16 blocks (32 registers a
+// thread, full occupancy) measured faster than 10 and 12 on the GB300; its
+// rare recomputation (byte_fallback) spills at that budget.
+#ifndef VD_BYTE_MIN_BLOCKS
+#define VD_BYTE_MIN_BLOCKS 16
+#endif
 template <int NB, int METRIC, int KSEL, int KEY = 0, bool DEDUP = false>
-__global__ void __launch_bounds__(kPassThreads, VD_PASS_MIN_BLOCKS) k_pass(PassArgs a) {
+__global__ void __launch_bounds__(kPassThreads, KEY == 3 ? VD_BYTE_MIN_BLOCKS : VD_PASS_MIN_BLOCKS)
+    k_pass(PassArgs a) {
   pdl_trigger();
   pdl_wait();
   const int x0 = 4 * static_cast<int>(blockIdx.x * blockDim.x + threadIdx.x);
@@ -502,7 +601,8 @@ __global__ void __launch_bounds__(kPassThreads, VD_PASS_MIN_BLOCKS) k_pass(PassA
   if (a.band_m > 1) rb = (blockIdx.y % a.band_t) * a.band_m + blockIdx.y / a.band_t;
   const int y = rb * static_cast<int>(blockDim.y) + static_cast<int>(threadIdx.y);
   if (x0 >= a.pitch || y >= a.h) return;
-  if (KEY != 0) pass_quad_clamped<NB, KSEL, false, METRIC, DEDUP, KEY == 2>(a, x0, y);
+  if (KEY == 3) pass_quad_byte<NB, KSEL, false, DEDUP>(a, x0, y);
+  else if (KEY != 0) pass_quad_clamped<NB, KSEL, false, METRIC, DEDUP, KEY == 2>(a, x0, y);
   else pass_quad<NB, METRIC, KSEL, false, DEDUP>(a, x0, y);
 }
 

@@ -24,6 +24,7 @@ OPT_PROFILE = 6
 OPT_CLAMPED_KEYS = 7
 OPT_PDL = 8
 OPT_DEDUP_GATHERS = 9
+OPT_BYTE_KEYS = 10
 
 KERNEL_KINDS = ("pass", "fused", "stamp", "move", "fill")
 

@@ -486,3 +486,48 @@ def test_step_equals_move_then_frame(vd, orc, graphs, moves):
         np.testing.assert_array_equal(a.get_seeds(), xy)
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("dedup", [0, 1])
+@pytest.mark.parametrize("w,h,s", [(37, 29, 12), (100, 37, 16), (64, 64, 16), (257, 129, 9), (300, 200, 500),
+                                   (512, 512, 16384), (512, 256, 65535), (512, 256, 65536),
+                                   (2048, 1024, 1 << 20)])
+def test_byte_offset_keys(vd, orc, dedup, w, h, s):
+    """The byte-offset key form, forced on every Euclidean pass, gives the
+    oracle's maps.  Random maps with empty labels put the far position and
+    seeds far outside the key window among the candidates (winners there are
+    recomputed); maps of real labels only, JFA frames and dJFA steps exercise
+    the unchecked path.  Seed counts at and just below a power of two cover
+    the label field's empty-label code, and 2^16 .. 2^20 seeds the narrower
+    windows (h = 64 .. 16); widths not a multiple of 32 read the row padding."""
+    g = np.random.default_rng(s + w)
+    xy = inputs.uniform_seeds(w, h, s, seed=s + 3)
+    sim = _sim(vd, w, h, xy, byte_keys=1, dedup_gathers=dedup)
+    for lo in (-1, 0):
+        src = g.integers(lo, s, size=(h, w), dtype=np.int32)
+        for k in [1, 2, 3, 4, 8, 16, 128]:
+            for nb in [M, VN]:
+                sim.set_labels(src)
+                sim.jump_pass(k, nb, E)
+                np.testing.assert_array_equal(sim.labels(), orc.jump_pass(w, h, xy, src, k, nb, E),
+                                              err_msg=f"k={k} nb={nb} lo={lo}")
+    # a smooth map (the previous JFA frame) with every candidate near its seed
+    sim.jfa()
+    lab = orc.jfa(w, h, xy)
+    np.testing.assert_array_equal(sim.labels(), lab)
+    for k in [16, 4, 1]:
+        sim.set_labels(lab)
+        sim.jump_pass(k, M, E)
+        np.testing.assert_array_equal(sim.labels(), orc.jump_pass(w, h, xy, lab, k, M, E), err_msg=f"k={k}")
+    disp = inputs.displacements(s, 2, 2, seed=s)
+    for t in range(2):
+        sim.move(disp[t])
+        xy = orc.move(w, h, xy, disp[t])
+        sim.djfa_step(d_max=2)
+        lab = orc.djfa_step(w, h, xy, lab, d_max=2)
+        np.testing.assert_array_equal(sim.labels(), lab, err_msg=f"step {t}")
+    # the flag leaves Manhattan passes on their own key forms
+    sim.set_labels(src)
+    sim.jump_pass(4, M, L1)
+    np.testing.assert_array_equal(sim.labels(), orc.jump_pass(w, h, xy, src, 4, M, L1))
+    sim.close()
