@@ -491,13 +491,13 @@ int vd_server_set_max_batch(vd_server* server, int32_t max_batch);
                                     neighbour's table gather: -1 = auto (default: dJFA passes on maps
                                     of at most 256 pixels per seed), 0 = never, 1 = always.  Results
                                     never depend on it */
-#define VD_OPT_BYTE_KEYS 10      /* Euclidean passes with the byte-offset key: one dp4a of the packed
-                                    seed-minus-pixel offset gives d^2, exact for |dx|, |dy| within a
-                                    window of half-width h <= 128 (smaller beyond 2^16 seeds); each
-                                    pixel's winner is checked against its window and a failing quad
-                                    is recomputed with the clamped key, so results are exact.  -1 =
-                                    auto (default: dJFA passes whose step plus three mean cell radii
-                                    fits the window), 0 = never, 1 = always when usable (>= 9 seeds) */
+#define VD_OPT_BYTE_KEYS 10      /* Euclidean passes with the byte-offset key (fewer than 65536 seeds):
+                                    one dp4a of the packed seed-minus-pixel offset gives d^2, exact
+                                    for dx, dy in [-128, 128); each pixel's winner is checked against
+                                    that window and a failing quad is recomputed with the clamped
+                                    key, so results are exact.  -1 = auto (default: dJFA passes whose
+                                    step plus three mean cell radii fits the window), 0 = never, 1 =
+                                    always when usable (9 .. 65535 seeds) */
 int vd_set_option(vd_ctx* ctx, int32_t option, int64_t value);
 int vd_get_option(const vd_ctx* ctx, int32_t option, int64_t* value);
 

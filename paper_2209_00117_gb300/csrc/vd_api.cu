@@ -204,37 +204,20 @@ bool use_clamp(int clamp_option, int32_t metric, int32_t n, int32_t k, bool djfa
   return djfa_frame;
 }
 
-// Label bits of the byte-offset key: the least lb with 2^lb > n, so that the
-// all-ones label field of an empty label names no seed.
-static int byte_label_bits(int64_t n) {
-  int lb = 0;
-  while ((int64_t{1} << lb) <= n) ++lb;
-  return lb;
-}
-
-// Half-width h of the byte-offset key's window: the largest power of two up
-// to 128 (dx and dy must fit a signed byte) with (2h^2 + 1) * 2^lb <= 2^32,
-// so that d * 2^lb + label cannot wrap inside the window; 0 if none.
-int byte_window(int64_t n) {
-  const int lb = byte_label_bits(n);
-  for (uint64_t h = 128; h >= 1; h >>= 1) {
-    if (((2 * h * h + 1) << lb) <= (uint64_t{1} << 32)) return static_cast<int>(h);
-  }
-  return 0;
-}
+// The byte-offset key's label field is 16 bits: usable below 2^16 seeds (the
+// all-ones field of an empty label must name no seed).
+bool byte_key_usable(int64_t n) { return n >= 1 && n < 65536; }
 
 bool use_byte_key(int byte_option, int32_t metric, int32_t w, int32_t h, int32_t n, int32_t k,
                   bool djfa_frame) {
   // the form falls back to the clamped one, usable from 9 seeds on
-  if (byte_option == 0 || metric != VD_METRIC_EUCLID || label_bits(n) < 4) return false;
-  const int hw = byte_window(n);
-  if (hw < 2) return false;
+  if (byte_option == 0 || metric != VD_METRIC_EUCLID || label_bits(n) < 4 || !byte_key_usable(n)) return false;
   if (byte_option == 1) return true;
   if (!djfa_frame) return false;
   // auto: dJFA passes whose step plus three mean cell radii stays inside the
   // window, so that a winner outside it (a recomputed quad) stays rare
   const double r = std::sqrt(static_cast<double>(w) * h / (3.141592653589793 * n));
-  return k + 3.0 * r <= hw - 1;
+  return k + 3.0 * r <= vdk::kByteWindow - 1;
 }
 
 int launch_pass(const MapView& m, const int32_t* src, int32_t* dst, int32_t k, int32_t nb,
@@ -249,12 +232,7 @@ int launch_pass(const MapView& m, const int32_t* src, int32_t* dst, int32_t k, i
     const int lb = label_bits(m.n);
     a.mul = lb >= 32 ? 0u : (1u << lb);
     a.cap = lb >= 4 ? static_cast<uint32_t>((uint64_t{1} << (32 - lb)) - 1) : 0u;
-    const uint32_t hw = static_cast<uint32_t>(byte_window(m.n));
-    const int blb = byte_label_bits(m.n);
-    a.bmul = blb >= 32 ? 0u : (1u << blb);
-    a.bwin_bias = hw * 0x10001u;
-    a.bwin_mask = hw ? (0xFFFFu & ~(2u * hw - 1u)) * 0x10001u : 0xFFFFFFFFu;
-    a.blim = hw * hw * a.bmul;
+    a.bmul = 1u << 16;
   }
   a.n_seeds = static_cast<uint32_t>(m.n);
   a.w = m.w;
@@ -288,7 +266,7 @@ int launch_pass(const MapView& m, const int32_t* src, int32_t* dst, int32_t k, i
     if (metric == VD_METRIC_MANHATTAN) key = label_bits(m.n) <= 15 ? 1 : 2;
     else if (a.cap != 0) key = 1;
   }
-  if (byte_key && metric == VD_METRIC_EUCLID && a.cap != 0 && byte_window(m.n) >= 2) key = 3;
+  if (byte_key && metric == VD_METRIC_EUCLID && a.cap != 0 && byte_key_usable(m.n)) key = 3;
   cudaError_t e;
   if (nb == VD_NB_MOORE) {
     if (metric == VD_METRIC_EUCLID) {

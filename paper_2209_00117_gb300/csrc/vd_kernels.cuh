@@ -121,10 +121,7 @@ struct PassArgs {
   uint32_t cap;                         // clamped-key passes: distance cap 2^(32 - lb) - 1
   uint32_t mul;                         // and 2^lb, lb = bits of the largest label
   uint32_t n_seeds;
-  // byte-offset passes: bmul = 2^lb' > n_seeds, window half-width h, and
-  // bwin_bias = h * 0x10001, bwin_mask = (0xFFFF & ~(2h - 1)) * 0x10001,
-  // blim = h^2 * bmul
-  uint32_t bmul, bwin_bias, bwin_mask, blim;
+  uint32_t bmul;  // byte-offset passes: 2^16 (a runtime value: see Quad8::key)
   int w, h, pitch, k;
   int band_m;  // > 1: visit row-blocks in k-strided bands (band_m = k / rows per block)
   int band_t;  // row-blocks per band residue class
@@ -266,21 +263,25 @@ struct Quad32M {
   __device__ __forceinline__ void fold(int i, int2 p, int c) { b[i] = min(b[i], key(i, p, c)); }
 };
 
-// Byte-offset 32-bit form (Euclidean).  For a seed's packed position
-// e = x | y << 16 and a pixel (x_p, y_p), v = e - (x_p | y_p << 16) + 2^15
-// equals (dx + 2^15) + dy * 2^16 with no borrow between the halves, so bytes
-// 0 and 2 of v are dx and dy modulo 256, and one dp4a of v with those two
-// bytes gives dx^2 + dy^2, exact while both lie in [-128, 127].  The gathered
-// entry is used as it is: no unpacking per gather.  key = d * 2^lb + label
-// with 2^lb > n_seeds, so an empty label (-1) leaves all ones in the label
-// bits, which name no seed.  Inside the window dx, dy in [-h, h) (h a power of
-// two <= 128 with (2h^2 + 1) * 2^lb <= 2^32) every key is exact; outside it a
-// key may be anything.  After the fold each pixel's winner is looked up again:
-// when it lies in its pixel's window at d < h^2, every seed outside the window
-// (at d >= h^2) loses to it and every seed inside was scored exactly, so the
-// winner is the exact one; a quad where any pixel fails this is recomputed
-// with the clamped form.  The prepared position is e itself.
-template <bool COH, bool DEDUP = false>
+// Byte-offset 32-bit form (Euclidean, fewer than 2^16 seeds).  For a seed's
+// packed position e = x | y << 16 and a pixel (x_p, y_p),
+// v = e - (x_p | y_p << 16) + 2^15 equals (dx + 2^15) + dy * 2^16 with no
+// borrow between the halves, so bytes 0 and 2 of v are dx and dy modulo 256,
+// and one dp4a of v with those two bytes gives dx^2 + dy^2, exact while both
+// lie in [-128, 127].  The gathered entry is used as it is: no unpacking per
+// gather.  key = d * 2^16 + label: an empty label (-1) leaves all ones in
+// the label field, which names no seed.  Inside the window dx, dy in [-128, 128)
+// every key is exact (d <= 2^15); outside it a key may be anything.  After
+// the fold each pixel's winner is looked up again: when it lies in its
+// pixel's window at d < 128^2, every seed outside the window (at d >= 128^2)
+// loses to it and every seed inside was scored exactly, so the winner is the
+// exact one; a quad where any pixel fails this is recomputed with the
+// clamped form.  The prepared position is e itself.  PRMT packs the key with
+// one byte permute (integer ALU pipe) instead of a multiply-add (FMA pipe):
+// faster for the k = 1, 2 passes, slower for the others (GB300).
+constexpr uint32_t kByteWindow = 128;  // h: dx, dy in [-h, h)
+
+template <bool COH, bool DEDUP = false, bool PRMT = false>
 struct Quad8 {
   static constexpr bool kDedup = DEDUP;
   // an out-of-range side candidate is replaced by the same row's label at the
@@ -295,7 +296,7 @@ struct Quad8 {
       : x0(x0_),
         y(y_),
         k0(0x8000u - (static_cast<uint32_t>(x0_) + (static_cast<uint32_t>(y_) << 16))),
-        mul(a.bmul),
+        mul(a.bmul),  // 2^16
         ptable(a.ptable) {}
   __device__ __forceinline__ int2 pos(int c) const {
     const uint32_t e = COH ? __ldcg(&ptable[c]) : __ldg(&ptable[c]);
@@ -304,6 +305,7 @@ struct Quad8 {
   __device__ __forceinline__ uint32_t key(int i, int2 p, int c) const {
     const uint32_t v = static_cast<uint32_t>(p.x) + k0 - static_cast<uint32_t>(i);
     const int d = __dp4a(static_cast<int>(v), static_cast<int>(v & 0x00FF00FFu), 0);
+    if (PRMT) return __byte_perm(static_cast<uint32_t>(c), static_cast<uint32_t>(d), 0x5410);
     return static_cast<uint32_t>(d) * mul + static_cast<uint32_t>(c);
   }
   __device__ __forceinline__ void set(int i, int2 p, int c) { b[i] = key(i, p, c); }
@@ -548,29 +550,29 @@ __device__ __noinline__ void byte_fallback(const PassArgs a, int x0, int y) {
 // Quad8; a quad that fails it is recomputed with the clamped form.
 template <int NB, int KSEL, bool COH = false, bool DEDUP = false>
 __device__ __forceinline__ void pass_quad_byte(const PassArgs& a, int x0, int y) {
-  Quad8<COH, DEDUP> q(a, x0, y);
+  Quad8<COH, DEDUP, KSEL != 0> q(a, x0, y);
   fold_all<NB, KSEL, COH>(q, a, x0, y);
-  const uint32_t mask = a.bmul - 1u;
-  // packed positions with the far position first: the label bits plus one,
-  // masked, index it (all ones, an empty label, wrap to the far position)
+  // packed positions with the far position first: the label field plus one,
+  // masked, indexes it (all ones, an empty label, wraps to the far position)
   const uint32_t* __restrict__ arena = a.ptable - 1;
-  const uint32_t kw = a.bwin_bias - (static_cast<uint32_t>(x0) + (static_cast<uint32_t>(y) << 16));
+  constexpr uint32_t h = kByteWindow;
+  const uint32_t kw = h * 0x10001u - (static_cast<uint32_t>(x0) + (static_cast<uint32_t>(y) << 16));
   uint32_t bad = 0;
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
-    const uint32_t j = (q.b[i] + 1u) & mask;
+    const uint32_t j = (q.b[i] + 1u) & 0xFFFFu;
     const uint32_t e = COH ? __ldcg(&arena[j]) : __ldg(&arena[j]);
     // (dx + h) | (dy + h) << 16 has no bit at or above 2h in either half
     // exactly when dx, dy lie in [-h, h)
-    bad |= (e + kw - static_cast<uint32_t>(i)) & a.bwin_mask;
+    bad |= (e + kw - static_cast<uint32_t>(i)) & ((0xFFFFu & ~(2u * h - 1u)) * 0x10001u);
   }
   const uint32_t top = max(max(q.b[0], q.b[1]), max(q.b[2], q.b[3]));
-  if (bad != 0 || top >= a.blim) {
+  if (bad != 0 || top >= (h * h) << 16) {
     byte_fallback<NB, KSEL, COH, DEDUP>(a, x0, y);
     return;
   }
-  store_quad(a, x0, y, static_cast<int>(q.b[0] & mask), static_cast<int>(q.b[1] & mask),
-             static_cast<int>(q.b[2] & mask), static_cast<int>(q.b[3] & mask));
+  store_quad(a, x0, y, static_cast<int>(q.b[0] & 0xFFFFu), static_cast<int>(q.b[1] & 0xFFFFu),
+             static_cast<int>(q.b[2] & 0xFFFFu), static_cast<int>(q.b[3] & 0xFFFFu));
 }
 
 // Pass launch shape: 128-thread blocks (64 quads x 2 rows on wide maps), 10
@@ -582,15 +584,16 @@ constexpr int kPassThreads = 128;
 #define VD_PASS_MIN_BLOCKS 10
 #endif
 
-// KEY: 0 the exact 64-bit form, 1 the 32-bit form of METRIC, 2 the clamped
-// Manhattan 32-bit form (more than 2^15 labels), 3 the Euclidean byte-offset
-// form.
 // The byte-offset form needs fewer registers: 16 blocks (32 registers a
 // thread, full occupancy) measured faster than 10 and 12 on the GB300; its
 // rare recomputation (byte_fallback) spills at that budget.
 #ifndef VD_BYTE_MIN_BLOCKS
 #define VD_BYTE_MIN_BLOCKS 16
 #endif
+
+// KEY: 0 the exact 64-bit form, 1 the 32-bit form of METRIC, 2 the clamped
+// Manhattan 32-bit form (more than 2^15 labels), 3 the Euclidean byte-offset
+// form.
 template <int NB, int METRIC, int KSEL, int KEY = 0, bool DEDUP = false>
 __global__ void __launch_bounds__(kPassThreads, KEY == 3 ? VD_BYTE_MIN_BLOCKS : VD_PASS_MIN_BLOCKS)
     k_pass(PassArgs a) {

@@ -497,9 +497,9 @@ def test_byte_offset_keys(vd, orc, dedup, w, h, s):
     oracle's maps.  Random maps with empty labels put the far position and
     seeds far outside the key window among the candidates (winners there are
     recomputed); maps of real labels only, JFA frames and dJFA steps exercise
-    the unchecked path.  Seed counts at and just below a power of two cover
-    the label field's empty-label code, and 2^16 .. 2^20 seeds the narrower
-    windows (h = 64 .. 16); widths not a multiple of 32 read the row padding."""
+    the unchecked path.  65535 seeds fill the 16-bit label field up to the
+    empty-label code; from 65536 seeds on the flag leaves the clamped form in
+    place.  Widths not a multiple of 32 read the row padding."""
     g = np.random.default_rng(s + w)
     xy = inputs.uniform_seeds(w, h, s, seed=s + 3)
     sim = _sim(vd, w, h, xy, byte_keys=1, dedup_gathers=dedup)
