@@ -495,9 +495,10 @@ int vd_server_set_max_batch(vd_server* server, int32_t max_batch);
                                     one dp4a of the packed seed-minus-pixel offset gives d^2, exact
                                     for dx, dy in [-128, 128); each pixel's winner is checked against
                                     that window and a failing quad is recomputed with the clamped
-                                    key, so results are exact.  -1 = auto (default: dJFA passes whose
-                                    step plus three mean cell radii fits the window), 0 = never, 1 =
-                                    always when usable (9 .. 65535 seeds) */
+                                    key, so results are exact.  -1 = auto (default: dJFA passes with steps up
+                                    to 128 on maps of at least 2^21 pixels with a mean cell radius
+                                    of at most 40 pixels), 0 = never, 1 = always when usable (9 ..
+                                    65535 seeds) */
 int vd_set_option(vd_ctx* ctx, int32_t option, int64_t value);
 int vd_get_option(const vd_ctx* ctx, int32_t option, int64_t* value);
 

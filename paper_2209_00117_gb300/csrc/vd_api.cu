@@ -214,10 +214,18 @@ bool use_byte_key(int byte_option, int32_t metric, int32_t w, int32_t h, int32_t
   if (byte_option == 0 || metric != VD_METRIC_EUCLID || label_bits(n) < 4 || !byte_key_usable(n)) return false;
   if (byte_option == 1) return true;
   if (!djfa_frame) return false;
-  // auto: dJFA passes whose step plus three mean cell radii stays inside the
-  // window, so that a winner outside it (a recomputed quad) stays rare
-  const double r = std::sqrt(static_cast<double>(w) * h / (3.141592653589793 * n));
-  return k + 3.0 * r <= vdk::kByteWindow - 1;
+  // auto: dJFA passes on maps of at least 2^21 pixels (on smaller ones a pass
+  // is a wave or two of quads, and the winner check's second lookup adds more
+  // latency than the saved instructions gain: 1024^2 2% slower, 2048^2 6%
+  // faster on the GB300) with a mean cell radius of at most 40 pixels, so
+  // that nearly every pixel's winner lies inside the window and recomputed
+  // quads stay rare, whatever the step (8192^2: 2^14 seeds, radius 36, 14%
+  // faster with every pass on the byte-offset key; 2^10 seeds, radius 144,
+  // 1.7x slower), at steps up to 128: a seed k >= 256 away wraps to a small
+  // byte offset, and such garbage keys would often beat the true winner
+  // (the repair frame's JFA schedule, 2048^2: 0.275 -> 0.338 ms a step)
+  if (static_cast<int64_t>(w) * h < (int64_t{1} << 21) || k > 128) return false;
+  return static_cast<double>(w) * h <= 3.141592653589793 * 40.0 * 40.0 * n;
 }
 
 int launch_pass(const MapView& m, const int32_t* src, int32_t* dst, int32_t k, int32_t nb,
