@@ -491,14 +491,16 @@ int vd_server_set_max_batch(vd_server* server, int32_t max_batch);
                                     neighbour's table gather: -1 = auto (default: dJFA passes on maps
                                     of at most 256 pixels per seed), 0 = never, 1 = always.  Results
                                     never depend on it */
-#define VD_OPT_BYTE_KEYS 10      /* Euclidean passes with the byte-offset key (fewer than 65536 seeds):
-                                    one dp4a of the packed seed-minus-pixel offset gives d^2, exact
-                                    for dx, dy in [-128, 128); each pixel's winner is checked against
-                                    that window and a failing quad is recomputed with the clamped
-                                    key, so results are exact.  -1 = auto (default: dJFA passes with steps up
-                                    to 128 on maps of at least 2^21 pixels with a mean cell radius
-                                    of at most 40 pixels), 0 = never, 1 = always when usable (9 ..
-                                    65535 seeds) */
+#define VD_OPT_BYTE_KEYS 10      /* Euclidean passes with the byte-offset key: one dp4a of the packed
+                                    seed-minus-pixel offset gives d^2, exact for dx, dy in [-h, h)
+                                    (h = 128 below 65536 seeds; from 65536 seeds on the label field
+                                    widens and h narrows: 64 .. 32 below 2^20 seeds, 16 .. 8 at up
+                                    to 2^22); each pixel's winner is checked against that window and
+                                    a failing quad is recomputed with the clamped key, so results
+                                    are exact.  -1 = auto (default: dJFA passes with steps up to
+                                    min(128, 2h) on maps of at least 2^21 pixels whose mean cell
+                                    radius is at most 40 h / 128 pixels, with h >= 32), 0 = never,
+                                    1 = always when usable (>= 9 seeds) */
 int vd_set_option(vd_ctx* ctx, int32_t option, int64_t value);
 int vd_get_option(const vd_ctx* ctx, int32_t option, int64_t* value);
 

@@ -204,28 +204,50 @@ bool use_clamp(int clamp_option, int32_t metric, int32_t n, int32_t k, bool djfa
   return djfa_frame;
 }
 
-// The byte-offset key's label field is 16 bits: usable below 2^16 seeds (the
-// all-ones field of an empty label must name no seed).
-bool byte_key_usable(int64_t n) { return n >= 1 && n < 65536; }
+// Byte-offset key: below 2^16 seeds a 16-bit label field and the window
+// h = 128; from 2^16 seeds on (the wide form) lb bits with 2^lb > n (so that
+// the all-ones field of an empty label names no seed) and the largest power
+// of two h with (2h^2 + 1) * 2^lb <= 2^32, so that no key inside the window
+// wraps.  Returns h, or 0 where the form does not apply.
+int byte_key_window(int64_t n, int* lb_out) {
+  if (n < 1) return 0;
+  if (n < 65536) {
+    if (lb_out) *lb_out = 16;
+    return static_cast<int>(vdk::kByteWindow);
+  }
+  int lb = 0;
+  while ((int64_t{1} << lb) <= n) ++lb;
+  if (lb_out) *lb_out = lb;
+  for (uint64_t h = 64; h >= 2; h >>= 1) {
+    if (((2 * h * h + 1) << lb) <= (uint64_t{1} << 32)) return static_cast<int>(h);
+  }
+  return 0;
+}
 
 bool use_byte_key(int byte_option, int32_t metric, int32_t w, int32_t h, int32_t n, int32_t k,
                   bool djfa_frame) {
   // the form falls back to the clamped one, usable from 9 seeds on
-  if (byte_option == 0 || metric != VD_METRIC_EUCLID || label_bits(n) < 4 || !byte_key_usable(n)) return false;
+  if (byte_option == 0 || metric != VD_METRIC_EUCLID || label_bits(n) < 4) return false;
+  const int hw = byte_key_window(n, nullptr);
+  if (hw == 0) return false;
   if (byte_option == 1) return true;
   if (!djfa_frame) return false;
   // auto: dJFA passes on maps of at least 2^21 pixels (on smaller ones a pass
   // is a wave or two of quads, and the winner check's second lookup adds more
   // latency than the saved instructions gain: 1024^2 2% slower, 2048^2 6%
-  // faster on the GB300) with a mean cell radius of at most 40 pixels, so
-  // that nearly every pixel's winner lies inside the window and recomputed
-  // quads stay rare, whatever the step (8192^2: 2^14 seeds, radius 36, 14%
-  // faster with every pass on the byte-offset key; 2^10 seeds, radius 144,
-  // 1.7x slower), at steps up to 128: a seed k >= 256 away wraps to a small
-  // byte offset, and such garbage keys would often beat the true winner
-  // (the repair frame's JFA schedule, 2048^2: 0.275 -> 0.338 ms a step)
-  if (static_cast<int64_t>(w) * h < (int64_t{1} << 21) || k > 128) return false;
-  return static_cast<double>(w) * h <= 3.141592653589793 * 40.0 * 40.0 * n;
+  // faster on the GB300) with a mean cell radius of at most 40 pixels per 128
+  // of window, so that nearly every pixel's winner lies inside the window and
+  // recomputed quads stay rare (8192^2: 2^14 seeds, radius 36, 14% faster
+  // with every pass on the byte-offset key; 2^10 seeds, radius 144, 1.7x
+  // slower), at steps up to min(128, 2h): a seed k >= 256 away wraps to a
+  // small byte offset, and such garbage keys would often beat the true
+  // winner (the repair frame's JFA schedule, 2048^2: 0.275 -> 0.338 ms a step).
+  // Not with windows narrower than 32 (2^20 seeds and more): moves of a few
+  // pixels then already put the previous frame's seeds outside the window,
+  // where their keys wrap (8192^2, 2^22 seeds, moves up to 16: 1.6x slower)
+  if (static_cast<int64_t>(w) * h < (int64_t{1} << 21) || k > 128 || k > 2 * hw || hw < 32) return false;
+  const double r_max = 40.0 * hw / 128.0;
+  return static_cast<double>(w) * h <= 3.141592653589793 * r_max * r_max * n;
 }
 
 int launch_pass(const MapView& m, const int32_t* src, int32_t* dst, int32_t k, int32_t nb,
@@ -240,7 +262,12 @@ int launch_pass(const MapView& m, const int32_t* src, int32_t* dst, int32_t k, i
     const int lb = label_bits(m.n);
     a.mul = lb >= 32 ? 0u : (1u << lb);
     a.cap = lb >= 4 ? static_cast<uint32_t>((uint64_t{1} << (32 - lb)) - 1) : 0u;
-    a.bmul = 1u << 16;
+    int blb = 16;
+    const uint32_t hw = static_cast<uint32_t>(byte_key_window(m.n, &blb));
+    a.bmul = blb >= 32 ? 0u : (1u << blb);
+    a.bwin_bias = hw * 0x10001u;
+    a.bwin_mask = hw ? (0xFFFFu & ~(2u * hw - 1u)) * 0x10001u : 0xFFFFFFFFu;
+    a.blim = hw * hw * a.bmul;
   }
   a.n_seeds = static_cast<uint32_t>(m.n);
   a.w = m.w;
@@ -274,11 +301,12 @@ int launch_pass(const MapView& m, const int32_t* src, int32_t* dst, int32_t k, i
     if (metric == VD_METRIC_MANHATTAN) key = label_bits(m.n) <= 15 ? 1 : 2;
     else if (a.cap != 0) key = 1;
   }
-  if (byte_key && metric == VD_METRIC_EUCLID && a.cap != 0 && byte_key_usable(m.n)) key = 3;
+  if (byte_key && metric == VD_METRIC_EUCLID && a.cap != 0 && a.bwin_bias != 0) key = m.n < 65536 ? 3 : 4;
   cudaError_t e;
   if (nb == VD_NB_MOORE) {
     if (metric == VD_METRIC_EUCLID) {
-      e = key == 3 ? launch_pass_t<vdk::kMoore, vdk::kEuclid, 3>(ksel, dedup, grid, block, st, pdl, a)
+      e = key == 4 ? launch_pass_t<vdk::kMoore, vdk::kEuclid, 4>(ksel, dedup, grid, block, st, pdl, a)
+          : key == 3 ? launch_pass_t<vdk::kMoore, vdk::kEuclid, 3>(ksel, dedup, grid, block, st, pdl, a)
           : key    ? launch_pass_t<vdk::kMoore, vdk::kEuclid, 1>(ksel, dedup, grid, block, st, pdl, a)
                    : launch_pass_t<vdk::kMoore, vdk::kEuclid, 0>(ksel, dedup, grid, block, st, pdl, a);
     } else {
@@ -288,7 +316,8 @@ int launch_pass(const MapView& m, const int32_t* src, int32_t* dst, int32_t k, i
     }
   } else {
     if (metric == VD_METRIC_EUCLID) {
-      e = key == 3 ? launch_pass_t<vdk::kVonNeumann, vdk::kEuclid, 3>(ksel, dedup, grid, block, st, pdl, a)
+      e = key == 4 ? launch_pass_t<vdk::kVonNeumann, vdk::kEuclid, 4>(ksel, dedup, grid, block, st, pdl, a)
+          : key == 3 ? launch_pass_t<vdk::kVonNeumann, vdk::kEuclid, 3>(ksel, dedup, grid, block, st, pdl, a)
           : key    ? launch_pass_t<vdk::kVonNeumann, vdk::kEuclid, 1>(ksel, dedup, grid, block, st, pdl, a)
                    : launch_pass_t<vdk::kVonNeumann, vdk::kEuclid, 0>(ksel, dedup, grid, block, st, pdl, a);
     } else {

@@ -83,7 +83,7 @@ int launch_pass(const MapView& m, const int32_t* src, int32_t* dst, int32_t k, i
                 int32_t metric, int64_t band_min_k, bool clamp, cudaStream_t st, bool pdl = false,
                 bool dedup = false, bool byte_key = false);
 bool use_dedup(int dedup_option, int32_t w, int32_t h, int32_t n, bool djfa_frame);
-bool byte_key_usable(int64_t n);
+int byte_key_window(int64_t n, int* lb_out);
 bool use_byte_key(int byte_option, int32_t metric, int32_t w, int32_t h, int32_t n, int32_t k,
                   bool djfa_frame);
 int launch_fused(const MapView& m, const int32_t* src, int32_t* dst, const int32_t* ks,

@@ -121,7 +121,11 @@ struct PassArgs {
   uint32_t cap;                         // clamped-key passes: distance cap 2^(32 - lb) - 1
   uint32_t mul;                         // and 2^lb, lb = bits of the largest label
   uint32_t n_seeds;
-  uint32_t bmul;  // byte-offset passes: 2^16 (a runtime value: see Quad8::key)
+  // byte-offset passes: bmul = 2^lb (2^16 below 2^16 seeds, a runtime value:
+  // see Quad8::key); the wide form (2^16 seeds and more, 2^lb > n_seeds) also
+  // reads its window h as bwin_bias = h * 0x10001, bwin_mask =
+  // (0xFFFF & ~(2h - 1)) * 0x10001 and blim = h^2 * 2^lb
+  uint32_t bmul, bwin_bias, bwin_mask, blim;
   int w, h, pitch, k;
   int band_m;  // > 1: visit row-blocks in k-strided bands (band_m = k / rows per block)
   int band_t;  // row-blocks per band residue class
@@ -278,7 +282,11 @@ struct Quad32M {
 // exact one; a quad where any pixel fails this is recomputed with the
 // clamped form.  The prepared position is e itself.  PRMT packs the key with
 // one byte permute (integer ALU pipe) instead of a multiply-add (FMA pipe):
-// faster for the k = 1, 2 passes, slower for the others (GB300).
+// faster for the k = 1, 2 passes, slower for the others (GB300).  The wide
+// form (2^16 seeds and more) widens the label field to lb bits with 2^lb > n
+// and narrows the window to the largest power of two h with
+// (2h^2 + 1) * 2^lb <= 2^32 (h = 8 at 2^22 seeds), so that no key inside it
+// wraps; the same argument then holds with h in place of 128.
 constexpr uint32_t kByteWindow = 128;  // h: dx, dy in [-h, h)
 
 template <bool COH, bool DEDUP = false, bool PRMT = false>
@@ -548,31 +556,34 @@ __device__ __noinline__ void byte_fallback(const PassArgs a, int x0, int y) {
 
 // Byte-offset form (Euclidean): the fold, then the winner check described at
 // Quad8; a quad that fails it is recomputed with the clamped form.
-template <int NB, int KSEL, bool COH = false, bool DEDUP = false>
+template <int NB, int KSEL, bool COH = false, bool DEDUP = false, bool WIDE = false>
 __device__ __forceinline__ void pass_quad_byte(const PassArgs& a, int x0, int y) {
-  Quad8<COH, DEDUP, KSEL != 0> q(a, x0, y);
+  Quad8<COH, DEDUP, !WIDE && KSEL != 0> q(a, x0, y);
   fold_all<NB, KSEL, COH>(q, a, x0, y);
   // packed positions with the far position first: the label field plus one,
   // masked, indexes it (all ones, an empty label, wraps to the far position)
   const uint32_t* __restrict__ arena = a.ptable - 1;
   constexpr uint32_t h = kByteWindow;
-  const uint32_t kw = h * 0x10001u - (static_cast<uint32_t>(x0) + (static_cast<uint32_t>(y) << 16));
+  const uint32_t mask = WIDE ? a.bmul - 1u : 0xFFFFu;
+  const uint32_t wmask = WIDE ? a.bwin_mask : (0xFFFFu & ~(2u * h - 1u)) * 0x10001u;
+  const uint32_t kw = (WIDE ? a.bwin_bias : h * 0x10001u) -
+                      (static_cast<uint32_t>(x0) + (static_cast<uint32_t>(y) << 16));
   uint32_t bad = 0;
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
-    const uint32_t j = (q.b[i] + 1u) & 0xFFFFu;
+    const uint32_t j = (q.b[i] + 1u) & mask;
     const uint32_t e = COH ? __ldcg(&arena[j]) : __ldg(&arena[j]);
     // (dx + h) | (dy + h) << 16 has no bit at or above 2h in either half
     // exactly when dx, dy lie in [-h, h)
-    bad |= (e + kw - static_cast<uint32_t>(i)) & ((0xFFFFu & ~(2u * h - 1u)) * 0x10001u);
+    bad |= (e + kw - static_cast<uint32_t>(i)) & wmask;
   }
   const uint32_t top = max(max(q.b[0], q.b[1]), max(q.b[2], q.b[3]));
-  if (bad != 0 || top >= (h * h) << 16) {
+  if (bad != 0 || top >= (WIDE ? a.blim : (h * h) << 16)) {
     byte_fallback<NB, KSEL, COH, DEDUP>(a, x0, y);
     return;
   }
-  store_quad(a, x0, y, static_cast<int>(q.b[0] & 0xFFFFu), static_cast<int>(q.b[1] & 0xFFFFu),
-             static_cast<int>(q.b[2] & 0xFFFFu), static_cast<int>(q.b[3] & 0xFFFFu));
+  store_quad(a, x0, y, static_cast<int>(q.b[0] & mask), static_cast<int>(q.b[1] & mask),
+             static_cast<int>(q.b[2] & mask), static_cast<int>(q.b[3] & mask));
 }
 
 // Pass launch shape: 128-thread blocks (64 quads x 2 rows on wide maps), 10
@@ -593,9 +604,9 @@ constexpr int kPassThreads = 128;
 
 // KEY: 0 the exact 64-bit form, 1 the 32-bit form of METRIC, 2 the clamped
 // Manhattan 32-bit form (more than 2^15 labels), 3 the Euclidean byte-offset
-// form.
+// form, 4 its wide form (2^16 seeds and more).
 template <int NB, int METRIC, int KSEL, int KEY = 0, bool DEDUP = false>
-__global__ void __launch_bounds__(kPassThreads, KEY == 3 ? VD_BYTE_MIN_BLOCKS : VD_PASS_MIN_BLOCKS)
+__global__ void __launch_bounds__(kPassThreads, KEY >= 3 ? VD_BYTE_MIN_BLOCKS : VD_PASS_MIN_BLOCKS)
     k_pass(PassArgs a) {
   pdl_trigger();
   pdl_wait();
@@ -604,7 +615,7 @@ __global__ void __launch_bounds__(kPassThreads, KEY == 3 ? VD_BYTE_MIN_BLOCKS : 
   if (a.band_m > 1) rb = (blockIdx.y % a.band_t) * a.band_m + blockIdx.y / a.band_t;
   const int y = rb * static_cast<int>(blockDim.y) + static_cast<int>(threadIdx.y);
   if (x0 >= a.pitch || y >= a.h) return;
-  if (KEY == 3) pass_quad_byte<NB, KSEL, false, DEDUP>(a, x0, y);
+  if (KEY == 3 || KEY == 4) pass_quad_byte<NB, KSEL, false, DEDUP, KEY == 4>(a, x0, y);
   else if (KEY != 0) pass_quad_clamped<NB, KSEL, false, METRIC, DEDUP, KEY == 2>(a, x0, y);
   else pass_quad<NB, METRIC, KSEL, false, DEDUP>(a, x0, y);
 }

@@ -498,8 +498,9 @@ def test_byte_offset_keys(vd, orc, dedup, w, h, s):
     seeds far outside the key window among the candidates (winners there are
     recomputed); maps of real labels only, JFA frames and dJFA steps exercise
     the unchecked path.  65535 seeds fill the 16-bit label field up to the
-    empty-label code; from 65536 seeds on the flag leaves the clamped form in
-    place.  Widths not a multiple of 32 read the row padding."""
+    empty-label code; 65536 and 2^20 seeds run the wide form (17- and 21-bit
+    label fields, windows of half-width 64 and 16).  Widths not a multiple of
+    32 read the row padding."""
     g = np.random.default_rng(s + w)
     xy = inputs.uniform_seeds(w, h, s, seed=s + 3)
     sim = _sim(vd, w, h, xy, byte_keys=1, dedup_gathers=dedup)
