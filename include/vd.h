@@ -236,7 +236,16 @@ int vd_get_labels(vd_ctx* ctx, int32_t* labels, int on_device);
  * snapshot maps on first use.
  */
 int vd_get_labels_async(vd_ctx* ctx, int32_t* labels);
-/* Waits until every vd_get_labels_async copy of the context has landed. */
+/*
+ * As vd_get_labels_async, into a dense w x h map of 16-bit labels (half the
+ * bytes to copy): each label as it is, the empty label -1 as 0xFFFF.  Needs
+ * at most 65535 seeds (VD_EINVAL otherwise).  The map is narrowed on the
+ * context's stream into one of the same two snapshot slots, so the two calls
+ * share the limit of two outstanding copies.
+ */
+int vd_get_labels16_async(vd_ctx* ctx, uint16_t* labels);
+/* Waits until every vd_get_labels_async / vd_get_labels16_async copy of the
+   context has landed. */
 int vd_wait_labels(vd_ctx* ctx);
 
 /*

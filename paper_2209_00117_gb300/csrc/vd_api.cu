@@ -1618,6 +1618,48 @@ extern "C" int vd_get_labels_async(vd_ctx* c, int32_t* labels) {
   return VD_OK;
 }
 
+// Dense 16-bit copy of a label map (rows of w out of a pitched map): labels
+// below 2^16 - 1 as they are, the empty label -1 as 0xFFFF.  One thread per
+// pixel of row blockIdx.y.
+static __global__ void k_narrow16(const int32_t* __restrict__ src, int pitch, int w, uint16_t* __restrict__ dst) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t y = blockIdx.y;
+  if (x < w) dst[y * w + x] = static_cast<uint16_t>(src[y * pitch + x]);
+}
+
+extern "C" int vd_get_labels16_async(vd_ctx* c, uint16_t* labels) {
+  VD_CHECK_CTX(c);
+  if (!labels) return vd_fail(VD_EINVAL, "null output");
+  if (c->n > 65535) return vd_fail(VD_EINVAL, "16-bit labels need at most 65535 seeds (have %d)", c->n);
+  int rc = ensure_async(c);
+  if (rc) return rc;
+  const int i = c->snap_next;
+  c->snap_next ^= 1;
+  if (c->copy_pending[i]) {
+    // the slot's previous copy must have left the snapshot before it is reused
+    rc = vd_cuda_check(cudaEventSynchronize(c->copy_done[i]), "wait for read-back");
+    if (rc) return rc;
+    c->copy_pending[i] = false;
+  }
+  // narrow the current map into the slot on the compute stream (later frames
+  // rewrite the map), then copy the dense 16-bit map out on the copy stream
+  uint16_t* snap = reinterpret_cast<uint16_t*>(c->snap[i]);
+  const dim3 grid((c->w + 255) / 256, c->h);
+  k_narrow16<<<grid, 256, 0, c->stream>>>(c->buf[c->cur], c->pitch, c->w, snap);
+  rc = vd_cuda_check(cudaGetLastError(), "narrow labels");
+  if (!rc) rc = vd_cuda_check(cudaEventRecord(c->snap_ready[i], c->stream), "event");
+  if (!rc) rc = vd_cuda_check(cudaStreamWaitEvent(c->copy_stream, c->snap_ready[i], 0), "wait event");
+  const size_t bytes = sizeof(uint16_t) * static_cast<size_t>(c->w) * c->h;
+  if (!rc)
+    rc = vd_cuda_check(cudaMemcpyAsync(labels, snap, bytes, cudaMemcpyDeviceToHost, c->copy_stream),
+                       "copy labels out");
+  if (!rc) rc = vd_cuda_check(cudaEventRecord(c->copy_done[i], c->copy_stream), "event");
+  if (rc) return rc;
+  ++c->launches;
+  c->copy_pending[i] = true;
+  return VD_OK;
+}
+
 extern "C" int vd_wait_labels(vd_ctx* c) {
   VD_CHECK_CTX(c);
   for (int i = 0; i < 2; ++i) {

@@ -269,6 +269,26 @@ class VoronoiSim:
         N.check(self._lib.vd_get_labels_async(self._h, ptr))
         return out
 
+    def labels16_async(self, out):
+        """As :meth:`labels_async` into a contiguous host uint16 array or tensor
+        of h * w elements (the empty label as 0xFFFF; at most 65535 seeds)."""
+        if _is_torch(out):
+            import torch
+
+            if out.dtype not in (torch.uint16, torch.int16) or not out.is_contiguous() or out.is_cuda:
+                raise TypeError("out must be a contiguous host uint16/int16 tensor")
+            n, ptr = out.numel(), out.data_ptr()
+        else:
+            if not isinstance(out, np.ndarray) or out.dtype != np.uint16 or not out.flags.c_contiguous:
+                raise TypeError("out must be a C-contiguous uint16 numpy array")
+            if not out.flags.writeable:
+                raise ValueError("output array is read-only")
+            n, ptr = out.size, out.ctypes.data
+        if n != self.w * self.h:
+            raise ValueError(f"expected {self.w * self.h} elements, got {n}")
+        N.check(self._lib.vd_get_labels16_async(self._h, ptr))
+        return out
+
     def wait_labels(self):
         N.check(self._lib.vd_wait_labels(self._h))
 

@@ -386,6 +386,60 @@ def test_async_label_readback(vd):
     b.close()
 
 
+@pytest.mark.parametrize("w,h,s", [(601, 403, 2500), (1000, 70, 65535), (33, 5, 9)])
+def test_async_label_readback_16bit(vd, w, h, s):
+    """The 16-bit read-back: every frame's dense map, interleaved with 32-bit
+    read-backs through the same two slots, equals the synchronous int32 read
+    (empty labels as 0xFFFF; odd widths; the largest seed count it takes)."""
+    import torch
+
+    D = 2
+    xy = inputs.uniform_seeds(w, h, s, seed=13)
+    disp = inputs.displacements(s, D, 5, seed=13)
+    a = _sim(vd, w, h, xy)
+    b = _sim(vd, w, h, xy)
+    # frame 0: a map with empty labels
+    src = np.random.default_rng(s).integers(-1, s, size=(h, w), dtype=np.int32)
+    a.set_labels(src)
+    b.set_labels(src)
+    o16 = [torch.empty((h, w), dtype=torch.int16).pin_memory() for _ in range(6)]
+    o32 = [torch.empty((h, w), dtype=torch.int32).pin_memory() for _ in range(6)]
+    want = []
+    for t in range(6):
+        if t:
+            for sim in (a, b):
+                sim.move(disp[t - 1])
+                sim.djfa_step(d_max=D)
+        a.labels16_async(o16[t])
+        a.labels_async(o32[t])
+        want.append(b.labels())
+    a.wait_labels()
+    for t in range(6):
+        got = o16[t].numpy().view(np.uint16).astype(np.int64)
+        exp = want[t].astype(np.int64)
+        exp[exp == -1] = 0xFFFF
+        np.testing.assert_array_equal(got, exp, err_msg=f"frame {t}")
+        np.testing.assert_array_equal(o32[t].numpy(), want[t], err_msg=f"frame {t}")
+    arr = np.empty((h, w), np.uint16)
+    a.labels16_async(arr)
+    a.wait_labels()
+    np.testing.assert_array_equal(arr.astype(np.int64), exp)
+    a.close()
+    b.close()
+
+
+def test_async_label_readback_16bit_refuses_large_counts(vd):
+    """From 65536 seeds on a label no longer fits 16 bits: VD_EINVAL."""
+    from paper_2209_00117_gb300._native import VD_EINVAL, VDError
+
+    w, h, s = 300, 256, 65536
+    sim = _sim(vd, w, h, inputs.uniform_seeds(w, h, s, seed=1))
+    with pytest.raises(VDError) as ei:
+        sim.labels16_async(np.empty((h, w), np.uint16))
+    assert ei.value.code == VD_EINVAL
+    sim.close()
+
+
 @pytest.mark.parametrize("w,h", [(32768, 8), (8, 32768), (32768, 3)])
 def test_maximum_side_grids(vd, orc, w, h):
     """Grids at the maximum side (coordinates up to 32767, squared distances up
