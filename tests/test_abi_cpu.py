@@ -87,3 +87,33 @@ def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
     monkeypatch.setattr(_native, "LIB_PATH", str(tmp_path / "missing.so"))
     with pytest.raises(RuntimeError, match="missing"):
         _native.lib()
+
+
+def _defines(header):
+    """{name: value} of the header's integer #defines (plain or parenthesised)."""
+    text = open(os.path.join(ROOT, "include", header)).read()
+    out = {}
+    for name, val in re.findall(r"^#define (VD_[A-Z0-9_]+)\s+\(?(-?\d+)\)?", text, flags=re.M):
+        out[name] = int(val)
+    return out
+
+
+def test_binding_constants_match_header(native):
+    """The Python binding's option, error, metric and neighbourhood constants
+    equal the header's, so a caller of either sees the same numbers."""
+    from paper_2209_00117_gb300 import vd
+
+    d = _defines("vd.h")
+    opts = {k[len("VD_OPT_"):]: v for k, v in d.items() if k.startswith("VD_OPT_")}
+    bopts = {k[len("VD_BOPT_"):]: v for k, v in d.items() if k.startswith("VD_BOPT_")}
+    assert opts and bopts
+    for name, v in opts.items():
+        assert getattr(vd, "OPT_" + name) == v, name
+    for name, v in bopts.items():
+        assert getattr(vd, "BOPT_" + name) == v, name
+    for name in ("VD_OK", "VD_EINVAL", "VD_ENOMEM", "VD_ECUDA", "VD_ETIMEOUT", "VD_EBUSY", "VD_ENOTFOUND"):
+        assert getattr(native, name) == d[name], name
+    assert (vd.EUCLID, vd.MANHATTAN) == (d["VD_METRIC_EUCLID"], d["VD_METRIC_MANHATTAN"])
+    assert (vd.MOORE, vd.VON_NEUMANN) == (d["VD_NB_MOORE"], d["VD_NB_VON_NEUMANN"])
+    assert vd.MAX_PASSES == d["VD_MAX_PASSES"]
+    assert len(vd.KERNEL_KINDS) == d["VD_KERNEL_KINDS"]
