@@ -1,15 +1,16 @@
 #!/usr/bin/env python
 """Benchmark: dJFA vs JFA frames of a moving-seed Voronoi simulation on GB300.
 
-One step = one simulation timestep of the hot path.  By default (``single2048``)
-that is one 2048 x 2048 grid with 16384 uniform seeds moving by uniform
-integers in [-2, 2] per axis (``--workload sweep8192 --seeds S --max-disp D``
-selects a point of the 8192 x 8192 sweep instead): the seed
-move (Algorithm 1's SimulateParticles), the stamp and the dJFA passes of Eq. 4
-(6 passes, the first two Von Neumann).  The same trajectory is also run with a
-full JFA frame per step (11 passes, Eq. 2) for the speedup, and every 10th frame
-both are scored against each other (the paper's similarity, Section VI-A) and
-against the exact diagram (distance-correct pixels).
+One step = one simulation timestep of the hot path.  By default that is one
+point of the 8192 x 8192 sweep: a 8192 x 8192 grid with 2^18 uniform seeds
+moving by uniform integers in [-4, 4] per axis (``--seeds S --max-disp D``
+select another point; ``--workload single2048`` the 2048 x 2048, 16384-seed
+workload): the seed move (Algorithm 1's SimulateParticles), the stamp and the
+dJFA passes of Eq. 4 (6 passes at the default point, the first two Von
+Neumann).  The same trajectory is also run with a full JFA frame per step (13
+passes, Eq. 2) for the speedup, and every 10th frame both are scored against
+each other (the paper's similarity, Section VI-A) and against the exact
+diagram (distance-correct pixels).
 
 Printed: one JSON line (rank 0).  ``value`` is whole-job dJFA throughput in
 Gpixel-passes/s from CUDA events around each step (inputs resident in HBM, L2
@@ -49,11 +50,12 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="single2048",
-                    help="single2048 (default), single256, sweep8192 with --seeds and --max-disp, "
+    ap.add_argument("--workload", default="sweep8192",
+                    help="sweep8192 (default; --seeds and --max-disp pick the point), single2048, single256, "
                          "batched256, serve1000, churn2048")
-    ap.add_argument("--seeds", type=int, default=None, help="sweep8192: seed count (2^10, 2^14, 2^18, 2^22)")
-    ap.add_argument("--max-disp", type=int, default=None, help="sweep8192: maximum move per axis (1, 4, 16)")
+    ap.add_argument("--seeds", type=int, default=None,
+                    help="sweep8192: seed count (2^10, 2^14, 2^18 (default), 2^22)")
+    ap.add_argument("--max-disp", type=int, default=None, help="sweep8192: maximum move per axis (1, 4 (default), 16)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="bounded CPU-oracle sample for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -85,7 +87,7 @@ def workload(name):
 
     if name == "sweep8192":
         sw = inputs.SWEEP8192
-        s = _SWEEP.get("seeds") or sw["seeds"][1]
+        s = _SWEEP.get("seeds") or sw["seeds"][2]
         d = _SWEEP.get("max_disp") or sw["max_disp"][1]
         if s not in sw["seeds"] or d not in sw["max_disp"]:
             raise SystemExit(f"sweep8192 takes --seeds in {sw['seeds']} and --max-disp in {sw['max_disp']}")
@@ -94,6 +96,22 @@ def workload(name):
         raise SystemExit(f"unknown workload {name}; choose from {sorted(inputs.SINGLE)} or sweep8192")
     w, h, s, steps, d = inputs.SINGLE[name]
     return w, h, s, steps, d
+
+
+def workload_key(name, s, d):
+    """Name of a workload in lines and in profiles/traffic.txt."""
+    return name if name != "sweep8192" else f"sweep8192_s{s}_d{d}"
+
+
+def l2_note(w, h, gpu):
+    """How the timed steps avoid a warm L2: two int32 maps larger than the
+    129 MB L2 need nothing more; smaller ones are flushed between steps."""
+    if 4 * w * h > (129 << 20):
+        return (f"inputs larger than L2 (two {4 * w * h >> 20} MB label maps a simulation); "
+                f"the GPU arm also writes {L2_FLUSH_BYTES >> 20} MB between timed steps, outside the step events")
+    if gpu:
+        return f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MB write, outside the step events)"
+    return "host memory"
 
 
 def config_dict(name, w, h, s, d, n_jfa, n_djfa, world, l2):
@@ -178,6 +196,42 @@ def max_over_ranks(pg, value, device):
 def whole_job_gpx(pixel_passes_per_step, steps, world, t_max_ms):
     """Gpixel-passes/s of the whole job: every rank's units over the max time."""
     return pixel_passes_per_step * steps * world / (t_max_ms * 1e-3) / 1e9
+
+
+def owned(n_items, world, rank):
+    """The simulations rank `rank` of `world` owns: indices i with
+    i % world == rank.  Every simulation belongs to exactly one rank, and the
+    ranks' shares differ by at most one."""
+    return list(range(rank, n_items, world))
+
+
+def sum_over_ranks(pg, value, device):
+    """The sum of `value` over all ranks (host-side aggregation of counts)."""
+    if pg is None:
+        return value
+    import torch
+
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.SUM)
+    return float(t.item())
+
+
+def gather_arrays(pg, arr):
+    """Every rank's 1-D float array, concatenated in rank order (host objects:
+    latencies and the like, never device data)."""
+    arr = np.asarray(arr, dtype=np.float64)
+    if pg is None:
+        return arr
+    parts = [None] * pg.get_world_size()
+    pg.all_gather_object(parts, arr)
+    return np.concatenate(parts) if parts else arr
+
+
+def latency_summary(lat):
+    """p50 / p99 / mean (ms) of a latency array in seconds."""
+    lat = np.asarray(lat, dtype=np.float64)
+    return {"p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * float(np.percentile(lat, 99)),
+            "mean_ms": 1e3 * float(lat.mean())}
 
 
 # ---------------------------------------------------------------------------
@@ -275,7 +329,8 @@ def run_reference(args):
         "n_gpus": world, "steps": res["steps"], "warmup": args.warmup,
         "ms_per_step": res["ms_per_step"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-        "config": config_dict(args.workload, w, h, s, d, n_jfa, n_djfa, 1, "host memory"),
+        "config": config_dict(workload_key(args.workload, s, d), w, h, s, d, n_jfa, n_djfa, world,
+                              l2_note(w, h, gpu=False)),
         "cpu_baseline": {k: res[k] for k in ("value", "unit", "cores", "kind", "sample")},
         "e2e": {"value": res["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -308,7 +363,7 @@ def run_ours(args):
         torch.cuda.synchronize()
 
     w, h, s, _, d = workload(args.workload)
-    wkey = args.workload if args.workload != "sweep8192" else f"sweep8192_s{s}_d{d}"
+    wkey = workload_key(args.workload, s, d)
     K, W = args.steps, args.warmup
     if W < 3:
         raise SystemExit("--warmup must be >= 3")
@@ -403,7 +458,8 @@ def run_ours(args):
     pr.close()
     dom = max(prof, key=lambda k: prof[k]["ms"])
     pd = prof[dom]
-    avg_ms = pd["ms"] / max(pd["launches"], 1)
+    n_dom = max(pd["launches"], 1)
+    avg_ms_eager = pd["ms"] / n_dom
     if dom in ("pass", "fused"):
         alg_bytes = 8.0 * px + 8.0 * s  # read + write one int32 per pixel, the seed table once
     elif dom == "fill":
@@ -411,27 +467,31 @@ def run_ours(args):
     else:
         alg_bytes = 16.0 * s
     peak, peak_src = hbm_peak()
-    achieved = alg_bytes / (avg_ms * 1e-3) / 1e9
     tot_ms = sum(v["ms"] for v in prof.values())
+    share = pd["ms"] / tot_ms if tot_ms > 0 else 1.0
+    # The dominant kernel's mean launch time in the timed region: the timed
+    # (graph-replayed, event-bracketed) dJFA frame time, times that kernel's
+    # share of GPU time in an eager replay of the same steps with events around
+    # every launch, divided by its launches per frame.  Its time x launches per
+    # step is then at most ms_per_step by construction.
+    per_step = n_dom / K
+    live_ms = (t_djfa / K) * share / per_step
+    achieved = alg_bytes / (live_ms * 1e-3) / 1e9
+    eager_gbs = alg_bytes / (avg_ms_eager * 1e-3) / 1e9
     roofline = {
         "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
         "traffic": recorded_traffic(dom, wkey),
-        "kernel": dom, "alg_bytes_per_launch": alg_bytes, "avg_launch_us": avg_ms * 1e3,
+        "kernel": dom, "alg_bytes_per_launch": alg_bytes, "avg_launch_us": live_ms * 1e3,
+        "launches_per_step": per_step,
+        "kernel_ms_per_step": live_ms * per_step,
         "peak_source": peak_src,
         "share": {k: round(v["ms"] / tot_ms, 4) for k, v in prof.items() if tot_ms > 0},
-        "measured": "CUDA events around every launch on its stream over K replayed dJFA steps",
+        "measured": "timed-region dJFA frame time (CUDA events around each graph-replayed step on the launching "
+                    "stream) x the kernel's share of GPU time in an eager replay of the same K steps with CUDA "
+                    "events around every launch / its launches per step",
+        "eager_replay": {"avg_launch_us": avg_ms_eager * 1e3, "achieved": eager_gbs, "frac": eager_gbs / peak,
+                         "method": "CUDA events around every launch (eager, serialised launches)"},
     }
-    if dom == "pass" and tot_ms > 0:
-        # The bracketing events above turn each frame into eager, serialised
-        # launches; the timed frames run from graphs with the launches chained.
-        # Informational: the timed frames' event-measured time, times the pass
-        # kernels' share of GPU time in the replay, per pass launch.
-        live_us = 1e3 * (t_djfa / K) * (prof["pass"]["ms"] / tot_ms) / n_djfa
-        live_gbs = alg_bytes / (live_us * 1e-6) / 1e9
-        roofline["from_timed_frames"] = {
-            "avg_launch_us": live_us, "achieved": live_gbs, "frac": live_gbs / peak,
-            "method": "timed-region frame time (CUDA events) x pass share of the replay's GPU time / passes per frame",
-        }
 
     # --- end to end through the API with host buffers
     e2e = None
@@ -492,8 +552,7 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": t_djfa_max / K, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-        "config": config_dict(args.workload, w, h, s, d, n_jfa, n_djfa, world,
-                              f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MB write, outside the step events)"),
+        "config": config_dict(wkey, w, h, s, d, n_jfa, n_djfa, world, l2_note(w, h, gpu=True)),
         "ms_per_frame": {"djfa": t_djfa_max / K, "jfa": t_jfa_max / K},
         "jfa": {"value": jfa_value, "unit": UNIT, "ms_per_step": t_jfa_max / K},
         "speedup_djfa_vs_jfa": t_jfa_max / t_djfa_max,
@@ -511,47 +570,69 @@ def run_ours(args):
     return 0
 
 
+def init_ranks():
+    """(rank, world, local, process group or None): NCCL ranks under a
+    multi-rank launch, used only for host-side aggregation and barriers."""
+    import torch
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+        pg = dist
+    return rank, world, local, pg
+
+
 def run_batched(args):
     """256 independent simulations (sides in {256, 512, 1024, 2048}, seeds
     uniform in [64, side^2/64], moves in [-2, 2]) stepped as one batch per
     timestep, against the same simulations run one by one with one launch per
-    pass (plain JFA frames, and unbatched dJFA frames)."""
+    pass (plain JFA frames, and unbatched dJFA frames).  Under N ranks each
+    rank steps its own disjoint share of the 256 (simulation i on rank
+    i % N): no data-path collective, the counts and times are aggregated on
+    the host (sum of work, maximum of time)."""
     import torch
 
     from paper_2209_00117_gb300 import build, inputs, vd
 
-    rank, world, local = dist_env()
     build.build()
-    torch.cuda.set_device(local)
+    rank, world, local, pg = init_ranks()
+    dev = f"cuda:{local}"
     K, W, D = args.steps, args.warmup, 2
-    pop = inputs.batched_population(256, seed=rank)
-    shapes = [(p.w, p.h, p.s) for p in pop]
-    xys = [inputs.uniform_seeds(w, h, s_, seed=1000 * rank + i) for i, (w, h, s_) in enumerate(shapes)]
+    pop = inputs.batched_population(256, seed=0)
+    mine = owned(len(pop), world, rank)
+    shapes = [(pop[i].w, pop[i].h, pop[i].s) for i in mine]
+    xys = [inputs.uniform_seeds(w, h, s_, seed=i) for i, (w, h, s_) in zip(mine, shapes)]
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     b = vd.VoronoiBatch(shapes, stream=stream)
     b.set_seeds(np.concatenate(xys))
     b.jfa()
     b.configure(d_max=D)
-    best, cand_ms = b.autotune(steps=3, max_disp=D, rng_seed=rank)
+    best, cand_ms = b.autotune(steps=3, max_disp=D, rng_seed=0)
     px, pp, n_seeds = b.work()
     for _ in range(W):
-        b.step(None, max_disp=D, rng_seed=rank)
+        b.step(None, max_disp=D, rng_seed=0)
     b.synchronize()
+    if pg is not None:
+        pg.barrier()
     e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
     e[0].record(stream)
     for _ in range(K):
-        b.step(None, max_disp=D, rng_seed=rank)
+        b.step(None, max_disp=D, rng_seed=0)
     e[1].record(stream)
     b.synchronize()
-    t_batch = e[0].elapsed_time(e[1])
+    t_batch = max_over_ranks(pg, e[0].elapsed_time(e[1]), dev)
     steps_done = W + K
 
     # the same simulations one by one, one launch per pass: JFA frames and dJFA frames
     sims = []
-    for i, (w, h, s_) in enumerate(shapes):
+    for j, (w, h, s_) in enumerate(shapes):
         c = vd.VoronoiSim(w, h, s_, stream=stream)
-        c.set_seeds(xys[i])
+        c.set_seeds(xys[j])
         c.set_option(vd.OPT_USE_GRAPHS, 0)
         sims.append(c)
     K1 = max(1, min(K, 5))
@@ -561,8 +642,8 @@ def run_batched(args):
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for t in range(n_steps):
-            for i, c in enumerate(sims):
-                c.move(None, max_disp=D, rng_seed=rank, stream_id=i, step=step0 + t)
+            for j, c in enumerate(sims):
+                c.move(None, max_disp=D, rng_seed=0, stream_id=j, step=step0 + t)
                 frame(c)
         e1.record(stream)
         torch.cuda.synchronize()
@@ -572,34 +653,45 @@ def run_batched(args):
     for c in sims:
         c.jfa()
     per_sim_steps(lambda c: c.jfa(), steps_done - K1, 0)
-    t_jfa = per_sim_steps(lambda c: c.jfa(), K1, steps_done - K1)
+    t_jfa = max_over_ranks(pg, per_sim_steps(lambda c: c.jfa(), K1, steps_done - K1), dev)
     # similarity of the batch's dJFA maps to same-frame JFA maps, on the GPU
     match = 0
-    for i, (w, h, _) in enumerate(shapes):
-        lab = torch.empty((h, w), dtype=torch.int32, device=f"cuda:{local}")
-        b.labels(i, out=lab)
-        match += sims[i].similarity(ref_labels=lab)[1]
+    for j, (w, h, _) in enumerate(shapes):
+        lab = torch.empty((h, w), dtype=torch.int32, device=dev)
+        b.labels(j, out=lab)
+        match += sims[j].similarity(ref_labels=lab)[1]
     # unbatched dJFA, one launch per pass, from the JFA maps
-    t_djfa_alone = per_sim_steps(lambda c: c.djfa_step(d_max=D), K1, steps_done)
+    t_djfa_alone = max_over_ranks(pg, per_sim_steps(lambda c: c.djfa_step(d_max=D), K1, steps_done), dev)
     pp_jfa = sum(w * h * len(vd.jfa_schedule(w, h)) for (w, h, _) in shapes)
     for c in sims:
         c.close()
     b.close()
+    # whole-job sums of this rank's work (host-side aggregation)
+    px_all = sum_over_ranks(pg, px, dev)
+    pp_all = sum_over_ranks(pg, pp, dev)
+    pp_jfa_all = sum_over_ranks(pg, pp_jfa, dev)
+    seeds_all = sum_over_ranks(pg, n_seeds, dev)
+    match_all = sum_over_ranks(pg, match, dev)
+    sims_all = sum_over_ranks(pg, len(shapes), dev)
+    if pg is not None:
+        pg.destroy_process_group()
     if rank != 0:
         return 0
     line = {
         "workload": "batched256: 256 independent simulations, sides uniform in {256, 512, 1024, 2048}, "
                     "seeds uniform in [64, side^2/64], moves uniform in [-2, 2]",
         "metric": METRIC, "unit": UNIT, "steps": K, "warmup": W, "dtype": "int32", "data": "synthetic",
-        "pixels": px, "seeds": n_seeds, "pixel_passes_per_step": pp,
-        "batched_djfa": {"value": pp / (t_batch / K * 1e-3) / 1e9, "ms_per_step": t_batch / K,
+        "n_gpus": world, "scaling": "strong", "simulations": int(sims_all),
+        "parallelism": f"simulation i on rank i % {world}" if world > 1 else "single",
+        "pixels": int(px_all), "seeds": int(seeds_all), "pixel_passes_per_step": int(pp_all),
+        "batched_djfa": {"value": pp_all / (t_batch / K * 1e-3) / 1e9, "ms_per_step": t_batch / K,
                          "launch_shape": {"candidate": best, "candidate_ms": cand_ms,
                                           "mode": "persistent" if b_mode(best) else "per round (graph)"}},
-        "unbatched_djfa_one_launch_per_pass": {"value": pp / (t_djfa_alone * 1e-3) / 1e9,
+        "unbatched_djfa_one_launch_per_pass": {"value": pp_all / (t_djfa_alone * 1e-3) / 1e9,
                                                "ms_per_step": t_djfa_alone},
-        "plain_jfa_one_launch_per_pass": {"value": pp_jfa / (t_jfa * 1e-3) / 1e9, "ms_per_step": t_jfa},
+        "plain_jfa_one_launch_per_pass": {"value": pp_jfa_all / (t_jfa * 1e-3) / 1e9, "ms_per_step": t_jfa},
         "speedup_batched_djfa_vs_plain_jfa": t_jfa / (t_batch / K),
-        "similarity_djfa_vs_jfa_pct": round(100.0 * match / px, 4),
+        "similarity_djfa_vs_jfa_pct": round(100.0 * match_all / px_all, 4),
         "l2": "working set (2 maps per simulation) is larger than L2",
     }
     print(json.dumps(line))
@@ -614,49 +706,73 @@ def b_mode(candidate):
 def run_serve(args):
     """1000 resident simulations (sides in {512, 1024, 2048, 4096}, density as
     the batched workload) admitted under an 80 GB HBM budget, then Poisson
-    request traces at each rate: p50 / p99 step latency and steps/s."""
+    request traces at each rate: p50 / p99 step latency and steps/s.  Under N
+    ranks simulation i lives on rank i % N, each with its own server and an
+    80 GB budget of its own GPU; a rank replays the requests of the one
+    shared trace that target its simulations, and the latencies are merged on
+    the host (percentiles of all ranks' latencies together)."""
     import torch
 
     from paper_2209_00117_gb300 import build, inputs, vd
 
-    rank, world, local = dist_env()
     build.build()
-    torch.cuda.set_device(local)
+    rank, world, local, pg = init_ranks()
+    dev = f"cuda:{local}"
     D = 2
-    pop = inputs.batched_population(1000, sides=(512, 1024, 2048, 4096), seed=rank)
-    srv = vd.VoronoiServer(max_sims=1000, hbm_budget_bytes=80 * 10**9, d_max=D, max_disp=D, rng_seed=rank)
-    ids, refused = [], 0
+    pop = inputs.batched_population(1000, sides=(512, 1024, 2048, 4096), seed=0)
+    mine = owned(len(pop), world, rank)
+    srv = vd.VoronoiServer(max_sims=len(mine), hbm_budget_bytes=80 * 10**9, d_max=D, max_disp=D, rng_seed=0)
+    sid = {}  # global simulation index -> this rank's server id
+    refused = 0
     from paper_2209_00117_gb300._native import VDError
 
     t0 = time.perf_counter()
-    for i, p in enumerate(pop):
+    for i in mine:
+        p = pop[i]
         try:
-            ids.append(srv.add_sim(p.w, p.h, inputs.uniform_seeds(p.w, p.h, p.s, seed=i)))
+            sid[i] = srv.add_sim(p.w, p.h, inputs.uniform_seeds(p.w, p.h, p.s, seed=i))
         except VDError:
             refused += 1
     t_admit = time.perf_counter() - t0
     st = srv.stats()
+    admitted = sorted(sid)
+    admitted_all = gather_arrays(pg, np.asarray(admitted, np.float64)).astype(np.int64)
     out = []
     for rate in [float(r) for r in args.rates.split(",")]:
         n = max(1, int(rate * args.duration))
         arr = inputs.poisson_arrivals(rate, n, seed=int(rate))
-        tgt = np.asarray(ids, np.int32)[inputs.request_targets(n, len(ids), seed=int(rate))]
-        lat = srv.run_trace(arr, tgt)
-        span = float(np.max(arr + lat))
-        out.append({"rate_per_s": rate, "requests": n, "p50_ms": 1e3 * float(np.percentile(lat, 50)),
-                    "p99_ms": 1e3 * float(np.percentile(lat, 99)), "mean_ms": 1e3 * float(lat.mean()),
-                    "steps_per_s": n / span})
+        # the one trace over every admitted simulation, split by owner
+        tgt = admitted_all[inputs.request_targets(n, len(admitted_all), seed=int(rate))]
+        keep = np.fromiter((t % world == rank for t in tgt), dtype=bool, count=n)
+        a_mine = arr[keep]
+        t_mine = np.asarray([sid[int(t)] for t in tgt[keep]], np.int32)
+        if pg is not None:
+            pg.barrier()
+        lat = srv.run_trace(a_mine, t_mine) if len(a_mine) else np.zeros(0)
+        span = float(np.max(a_mine + lat)) if len(a_mine) else 0.0
+        lat_all = gather_arrays(pg, lat)
+        span_all = max_over_ranks(pg, span, dev)
+        out.append({"rate_per_s": rate, "requests": n, **latency_summary(lat_all),
+                    "steps_per_s": n / span_all})
     st2 = srv.stats()
     srv.close()
+    used = sum_over_ranks(pg, st["used_bytes"], dev)
+    refused_all = sum_over_ranks(pg, refused, dev)
+    launches = sum_over_ranks(pg, st2["launches"] - st["launches"], dev)
+    steps_done = sum_over_ranks(pg, st2["steps_done"], dev)
+    t_admit = max_over_ranks(pg, t_admit, dev)
+    if pg is not None:
+        pg.destroy_process_group()
     if rank != 0:
         return 0
     print(json.dumps({
         "workload": "serve1000: 1000 resident simulations, sides uniform in {512, 1024, 2048, 4096}, seeds "
                     "uniform in [64, side^2/64], dJFA step requests (moves in [-2, 2]) as Poisson streams",
-        "unit": "steps/s and ms", "dtype": "int32", "data": "synthetic",
-        "admitted": len(ids), "refused": refused, "hbm_used_gb": st["used_bytes"] / 1e9,
-        "hbm_budget_gb": st["budget_bytes"] / 1e9, "admit_s": t_admit,
-        "kernel_launches": st2["launches"] - st["launches"], "steps": st2["steps_done"],
+        "unit": "steps/s and ms", "dtype": "int32", "data": "synthetic", "n_gpus": world,
+        "parallelism": f"simulation i on rank i % {world}, one server per GPU" if world > 1 else "single",
+        "admitted": int(len(admitted_all)), "refused": int(refused_all), "hbm_used_gb": used / 1e9,
+        "hbm_budget_gb_per_gpu": st["budget_bytes"] / 1e9, "admit_s": t_admit,
+        "kernel_launches": int(launches), "steps": int(steps_done),
         "rates": out}))
     return 0
 
@@ -729,8 +845,33 @@ def run_churn(args):
     return 0
 
 
+def free_port():
+    import socket
+
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        return sk.getsockname()[1]
+
+
+def launch_ranks(n):
+    """Runs this command as n ranks, one process per GPU, through
+    torch.distributed.run on 127.0.0.1; returns the launcher's exit status."""
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={n}",
+           "--master-addr", "127.0.0.1", "--master-port", str(free_port()),
+           os.path.abspath(__file__)] + sys.argv[1:]
+    return subprocess.run(cmd).returncode
+
+
 def main():
     args = parse_args()
+    if args.gpus < 1:
+        raise SystemExit("--gpus must be >= 1")
+    if "WORLD_SIZE" in os.environ:
+        _, world, _ = dist_env()
+        if world != args.gpus:
+            raise SystemExit(f"--gpus {args.gpus} but this launch has WORLD_SIZE={world} ranks")
+    elif args.gpus > 1:
+        return launch_ranks(args.gpus)
     if args.workload == "batched256":
         return run_batched(args)
     if args.workload == "churn2048":

@@ -98,7 +98,11 @@ int vd_djfa_schedule(int32_t w, int32_t h, int64_t n_seeds, int32_t d_max, int32
 typedef struct vd_ctx vd_ctx;
 
 /*
- * Creates a simulation on the current CUDA device: a w x h label map (two
+ * Creates a simulation on the current CUDA device: the state that Algorithm 1
+ * threads through its steps, Data = (VD, S, A) -- the label map VD of the
+ * problem statement in Section IV (the discrete diagram of a w x h grid, one
+ * seed index per pixel), the seed set S and the step count -- as a w x h label
+ * map (two
  * device buffers for the Jacobi passes, rows padded to 128 bytes, the
  * padding held at -1), n_seeds seeds (all at (0, 0) until vd_set_seeds) and
  * small scratch buffers.  Labels start at -1.  The stream is the legacy
@@ -108,12 +112,15 @@ typedef struct vd_ctx vd_ctx;
  */
 vd_ctx* vd_create(int32_t grid_w, int32_t grid_h, int32_t n_seeds);
 
-/* Frees every device buffer of the context after its stream is idle.
+/* Ends a simulation (the Data = (VD, S, A) of Algorithm 1 that vd_create
+ * made): frees every device buffer of the context after its stream is idle.
  * NULL is accepted (VD_OK). */
 int vd_destroy(vd_ctx* ctx);
 
 /* Queues all later work of the context on `cuda_stream` (a cudaStream_t;
- * NULL = legacy default stream).  The caller keeps the stream alive. */
+ * NULL = legacy default stream).  The caller keeps the stream alive.  The
+ * paper runs every step of Algorithm 1 on one GPU (Section VI); the stream is
+ * where this library orders those steps.  VD_EINVAL on a null context. */
 int vd_set_stream(vd_ctx* ctx, void* cuda_stream);
 
 /* Blocks until all queued work of the context has finished. */
@@ -213,8 +220,9 @@ int vd_step(vd_ctx* ctx, const int32_t* dxy, int dxy_on_device, int32_t max_disp
  * current map gets the lowest index among the seeds standing on it. */
 int vd_stamp(vd_ctx* ctx);
 
-/* One jump pass with step k >= 1 and neighbourhood nb (Table I / Section
- * IV-B), as inside vd_jfa; exposed for tests and diagnostics. */
+/* One jump pass with step k >= 1 and neighbourhood nb (Table I for Moore,
+ * Section V-B for Von Neumann), as inside vd_jfa; exposed for tests and
+ * diagnostics. */
 int vd_pass(vd_ctx* ctx, int32_t k, int32_t nb, int32_t metric);
 
 /* Overwrites the label map with a dense w x h map.  Every label must lie in
@@ -222,7 +230,9 @@ int vd_pass(vd_ctx* ctx, int32_t k, int32_t nb, int32_t metric);
  * kernel plus a synchronisation for device input) and the map is unchanged. */
 int vd_set_labels(vd_ctx* ctx, const int32_t* labels, int on_device);
 
-/* Copies the label map out as a dense w x h map. */
+/* Copies the label map out as a dense w x h map: VD, the discrete Voronoi
+ * diagram that Algorithm 1 returns each step (Section IV states the problem as
+ * producing it every frame).  Host output synchronises the stream first. */
 int vd_get_labels(vd_ctx* ctx, int32_t* labels, int on_device);
 
 /*
@@ -300,13 +310,15 @@ int vd_exact(vd_ctx* ctx, int32_t* labels, int32_t* dist, int on_device, int32_t
  *
  * Scratch: a file-scope device array of VD_NOALLOC_SCRATCH_INTS int32 (4 MiB)
  * that every GPU loading the library holds until the process exits.  The
- * bucket grid needs 64 + 2 * buckets + 1 + n_seeds ints, with one to two
- * buckets per seed: up to about 250000 seeds always fit, beyond that it
- * depends on the grid.  Larger requests fail with VD_EINVAL and a message
+ * bucket grid needs 64 + 2 * buckets + 1 + n_seeds ints, and the bucket side
+ * is chosen so that there are at most two buckets per seed, so the need is at
+ * most 66 + 5 * n_seeds ints: up to 200000 seeds always fit, on any grid.  Larger requests fail with VD_EINVAL and a message
  * naming the need, as do bad sizes, a bad metric and seeds outside the
  * grid.  No cudaMalloc, cudaFree or allocating library routine is called.
  * The first call on a device resolves the array's device address (with that
- * device current); make that first call before any stream capture.  All calls
+ * device current) and keeps it for the life of the process; make that first
+ * call before any stream capture, and do not call cudaDeviceReset on a
+ * device between calls (the kept address would be stale).  All calls
  * share the one array, which keeps the previous call's contents (the parts
  * that must start at zero are cleared on every call): calls that overlap on
  * the GPU, on any stream, race.

@@ -1500,10 +1500,19 @@ extern "C" int vd_exact_noalloc(const int32_t* seeds_xy, int32_t n_seeds, int32_
     return vd_fail(VD_EINVAL, "seeds must be 8-byte aligned");
   if (!labels && !dist) return vd_fail(VD_EINVAL, "no output map");
   if (check_metric(metric)) return VD_EINVAL;
+  // bucket side ~ sqrt(area / seeds), then grown until there are at most two
+  // buckets per seed (with side 1 and under 4 pixels a seed the first choice
+  // alone would give up to 4): the need is then at most 66 + 5 n ints, so
+  // every request of up to 200000 seeds fits, whatever the grid
   int cell = 1;
   const double per = static_cast<double>(w) * h / n_seeds;
   while (static_cast<double>(cell + 1) * (cell + 1) <= per) ++cell;
-  const int gw = (w + cell - 1) / cell, gh = (h + cell - 1) / cell;
+  int gw = (w + cell - 1) / cell, gh = (h + cell - 1) / cell;
+  while (static_cast<int64_t>(gw) * gh > 2 * static_cast<int64_t>(n_seeds)) {
+    ++cell;
+    gw = (w + cell - 1) / cell;
+    gh = (h + cell - 1) / cell;
+  }
   const int64_t cells = static_cast<int64_t>(gw) * gh;
   const int64_t need = kNoallocHeaderInts + cells + (cells + 1) + n_seeds;
   if (need > VD_NOALLOC_SCRATCH_INTS)
@@ -1520,7 +1529,9 @@ extern "C" int vd_exact_noalloc(const int32_t* seeds_xy, int32_t n_seeds, int32_
   int* base = nullptr;
   {
     // once per device, with that device current: the host-side name of the
-    // array is only a stand-in, the kernels need its device address
+    // array is only a stand-in, the kernels need its device address.  The
+    // cached address belongs to the device's primary context: it is stale
+    // after cudaDeviceReset, so callers must not reset a device between calls
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
     if (!g_noalloc_ptr[dev]) {
       void* p = nullptr;

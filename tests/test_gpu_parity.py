@@ -89,6 +89,38 @@ def test_jfa_extra_passes(vd, orc, extra):
     sim.close()
 
 
+@pytest.mark.parametrize("metric", [E, L1])
+@pytest.mark.parametrize("w,h,s", [(333, 222, 300), (2048, 1024, 20000)])
+def test_djfa_extra_passes(vd, orc, metric, w, h, s):
+    """The optional extra step after Eq. 4's schedule (Section V-A) and the
+    JFA+1/+2 idea of Section III on dJFA frames: vd_djfa_step, eager vd_step
+    and graph-replayed vd_step with extra in {1, 2} (the graph cache must key
+    on it: the extra count changes from step to step) against the oracle's
+    dJFA chain, both metrics.  The larger map takes the byte-offset key."""
+    D = 3
+    xy = inputs.uniform_seeds(w, h, s, seed=s + 7)
+    extras = [1, 2, 1, 0, 2]
+    disp = inputs.displacements(s, D, len(extras), seed=s + 7)
+    a = _sim(vd, w, h, xy)
+    b = _sim(vd, w, h, xy, use_graphs=0)
+    c = _sim(vd, w, h, xy, use_graphs=1)
+    for sim in (a, b, c):
+        sim.jfa(metric=metric)
+    lab = orc.jfa(w, h, xy, metric=metric)
+    for t, extra in enumerate(extras):
+        a.move(disp[t])
+        a.djfa_step(d_max=D, extra=extra, metric=metric)
+        b.step(disp[t], d_max=D, extra=extra, metric=metric)
+        c.step(disp[t], d_max=D, extra=extra, metric=metric)
+        xy = orc.move(w, h, xy, disp[t])
+        lab = orc.djfa_step(w, h, xy, lab, d_max=D, extra=extra, metric=metric)
+        for name, sim in (("djfa_step", a), ("step", b), ("step+graph", c)):
+            got = sim.labels()
+            assert np.array_equal(got, lab), (name, t, extra, int((got != lab).sum()))
+    for sim in (a, b, c):
+        sim.close()
+
+
 def test_degenerate_grids(vd, orc):
     for w, h, s in [(1, 1, 1), (1, 1, 5), (1, 50, 3), (70, 1, 4), (2, 2, 9), (3, 5, 15)]:
         xy = inputs.uniform_seeds(w, h, s, seed=w * 7 + h)

@@ -6,8 +6,10 @@ plugin hosts); it uses a scratch array compiled into the library instead of
 cudaMalloc.  This file runs last so that a failure here leaves every other
 test already run.  It checks, on two calls in a row with different sizes (so
 the second call reuses scratch the first one filled), that the new entry
-point returns exactly what the context-based vd_exact returns (integer maps,
-tolerance 0), and that oversized requests and out-of-grid seeds are rejected.
+point returns exactly what the context-based vd_exact returns and what the
+CPU oracle's brute force of Eq. 1 returns (integer maps, tolerance 0), that a
+request at the documented bound (200000 seeds on the grid that needs the most
+buckets) fits, and that oversized requests and out-of-grid seeds are rejected.
 """
 import numpy as np
 import pytest
@@ -37,7 +39,7 @@ def _call(torch, native, xy_dev, w, h, metric, lab, dist):
                                 None if dist is None else dist.data_ptr(), stream)
 
 
-def test_exact_noalloc_matches_vd_exact_twice(env):
+def test_exact_noalloc_matches_vd_exact_twice(env, orc):
     torch, native, vd = env
     cases = [(300, 211, 2000, 7, vd.EUCLID), (512, 384, 700, 8, vd.MANHATTAN)]
     for w, h, s, seed, metric in cases:
@@ -51,6 +53,33 @@ def test_exact_noalloc_matches_vd_exact_twice(env):
         lab = torch.full((h, w), -7, dtype=torch.int32, device="cuda")
         dist = torch.full((h, w), -7, dtype=torch.int32, device="cuda")
         rc = _call(torch, native, xy_dev, w, h, metric, lab, dist)
+        torch.cuda.synchronize()
+        assert rc == native.VD_OK, native.last_error()
+        np.testing.assert_array_equal(lab.cpu().numpy(), want_l)
+        np.testing.assert_array_equal(dist.cpu().numpy(), want_d)
+        brute_l, brute_d = orc.exact_brute(w, h, xy, metric)
+        np.testing.assert_array_equal(lab.cpu().numpy(), brute_l)
+        np.testing.assert_array_equal(dist.cpu().numpy(), brute_d)
+
+
+def test_exact_noalloc_at_the_bound(env):
+    """200000 seeds on 632 x 632 (just under 2 pixels a seed: one bucket a
+    pixel, the most buckets per seed the bucket rule keeps, so the largest
+    scratch need at this seed count): the request fits and equals vd_exact,
+    twice in a row."""
+    torch, native, vd = env
+    w = h = 632
+    s = 200000
+    xy = inputs.uniform_seeds(w, h, s, seed=11)
+    sim = vd.VoronoiSim(w, h, s)
+    sim.set_seeds(xy)
+    want_l, want_d = sim.exact()
+    sim.close()
+    xy_dev = torch.from_numpy(xy).cuda()
+    for _ in range(2):
+        lab = torch.full((h, w), -7, dtype=torch.int32, device="cuda")
+        dist = torch.full((h, w), -7, dtype=torch.int32, device="cuda")
+        rc = _call(torch, native, xy_dev, w, h, vd.EUCLID, lab, dist)
         torch.cuda.synchronize()
         assert rc == native.VD_OK, native.last_error()
         np.testing.assert_array_equal(lab.cpu().numpy(), want_l)
