@@ -522,6 +522,26 @@ int vd_server_set_max_batch(vd_server* server, int32_t max_batch);
                                     min(128, 2h) on maps of at least 2^21 pixels whose mean cell
                                     radius is at most 40 h / 128 pixels, with h >= 32), 0 = never,
                                     1 = always when usable (>= 9 seeds) */
+#define VD_OPT_BLOCKED_PASS 11   /* byte-key passes with k a multiple of 4 run register-blocked: one
+                                    thread owns the four quads at (x, y), (x + k, y), (x, y + k),
+                                    (x + k, y + k), whose neighbour vectors overlap, and loads and
+                                    gathers each of the 16 (Moore) or 12 (Von Neumann) vectors once.
+                                    -1 = auto (default: never; it measured slower than the plain pass
+                                    on the GB300, where the pass is bound on integer issue and the
+                                    blocked form runs at half the occupancy), 0 = never, 1 = whenever
+                                    it applies.  Results never depend on it */
+#define VD_OPT_KEY_PACK 12       /* how the blocked byte-key pass packs (d, label): 0 = multiply-add
+                                    (default), 1 = byte permute (below 2^16 seeds), 2 = constant shift
+                                    (2^16 seeds and more).  Results never depend on it */
+#define VD_OPT_BLOCKED_MIN_BLOCKS 13 /* register budget of the blocked pass: 8 (default, 64 registers a
+                                    thread) or 6 (80) resident 128-thread blocks per SM */
+#define VD_OPT_SPARSE_PASS 14    /* passes with k % 4 == 0, k = 1 or k = 2 first test each quad: when
+                                    every in-grid candidate of each of its pixels carries the pixel's
+                                    own label the quad is copied through; the other quads of the block
+                                    are gathered in shared memory and scored one per thread.  -1 = auto
+                                    (default: steps of at most 1/32 of the mean cell side
+                                    sqrt(w h / n), where nearly every quad is unchanged), 0 = never,
+                                    1 = whenever it applies.  Results never depend on it */
 int vd_set_option(vd_ctx* ctx, int32_t option, int64_t value);
 int vd_get_option(const vd_ctx* ctx, int32_t option, int64_t* value);
 

@@ -252,7 +252,7 @@ bool use_byte_key(int byte_option, int32_t metric, int32_t w, int32_t h, int32_t
 
 int launch_pass(const MapView& m, const int32_t* src, int32_t* dst, int32_t k, int32_t nb,
                 int32_t metric, int64_t band_min_k, bool clamp, cudaStream_t st, bool pdl, bool dedup,
-                bool byte_key) {
+                bool byte_key, int blocked, int key_pack, int blk_min_blocks, bool sparse) {
   vdk::PassArgs a;
   a.src = src;
   a.dst = dst;
@@ -302,6 +302,14 @@ int launch_pass(const MapView& m, const int32_t* src, int32_t* dst, int32_t k, i
     else if (a.cap != 0) key = 1;
   }
   if (byte_key && metric == VD_METRIC_EUCLID && a.cap != 0 && a.bwin_bias != 0) key = m.n < 65536 ? 3 : 4;
+  if (sparse && ksel <= 2) return launch_pass_sparse(a, grid, block, nb, metric, key, ksel, dedup, st, pdl);
+  // the register-blocked form: opt-in (blocked == 1).  It loads and gathers
+  // each vector once for up to four quads, but needs 64 registers a thread
+  // (half the resident warps) and measured slower than the plain pass on the
+  // GB300 (8192^2, 2^18 seeds: Von Neumann k = 32 189 -> 244 us, Moore k = 8
+  // 268 -> 275 us; 2^14 seeds likewise), so auto leaves it off
+  if (blocked == 1 && blk_applies(k, key))
+    return launch_pass_blk(a, nb, key, dedup, key_pack, blk_min_blocks, st, pdl);
   cudaError_t e;
   if (nb == VD_NB_MOORE) {
     if (metric == VD_METRIC_EUCLID) {
@@ -399,6 +407,18 @@ std::vector<Launch> plan_passes(const int32_t* ks, const int32_t* nbs, int n, in
   return plan;
 }
 
+bool use_sparse(int sparse_option, int32_t w, int32_t h, int32_t n, int32_t k) {
+  if (sparse_option >= 0) return sparse_option == 1;
+  // auto: k <= c / 32 with c = sqrt(w h / n), the mean cell side, where
+  // nearly every quad lies inside one cell with all its candidates.  The
+  // block-wide test and compaction cost about 0.45 of a plain pass when no
+  // quad is unchanged (its second reading of the labels misses L1), so it
+  // only pays from about 85% unchanged quads on (GB300, 8192^2: 2^14 seeds,
+  // k = 1, 87% unchanged: 217 -> 200 us; k = 4, 66%: 256 -> 276 us; 2^10
+  // seeds, D = 1: dJFA frame 2.50 -> 2.38 ms)
+  return 1024.0 * k * k * static_cast<double>(n) <= static_cast<double>(w) * h;
+}
+
 int run_passes(const MapView& m, int32_t* const buf[2], int* cur, const int32_t* ks,
                const int32_t* nbs, int n, int32_t metric, const Tuning& t, cudaStream_t st,
                int64_t* launches, Profiler* prof, bool djfa_frame) {
@@ -413,7 +433,9 @@ int run_passes(const MapView& m, int32_t* const buf[2], int* cur, const int32_t*
       rc = launch_pass(m, src, dst, ks[l.first], nbs[l.first], metric, t.band_min_k,
                        use_clamp(t.clamp, metric, m.n, ks[l.first], djfa_frame), st, t.pdl != 0,
                        use_dedup(t.dedup, m.w, m.h, m.n, djfa_frame),
-                       use_byte_key(t.byte_key, metric, m.w, m.h, m.n, ks[l.first], djfa_frame));
+                       use_byte_key(t.byte_key, metric, m.w, m.h, m.n, ks[l.first], djfa_frame), t.blocked,
+                       t.key_pack, t.blk_min_blocks,
+                       use_sparse(t.sparse, m.w, m.h, m.n, ks[l.first]));
     } else {
       rc = launch_fused(m, src, dst, ks + l.first, nbs + l.first, l.n, metric, t.tile_x, t.tile_y, st);
     }
@@ -1190,7 +1212,9 @@ extern "C" int vd_pass(vd_ctx* c, int32_t k, int32_t nb, int32_t metric) {
   const int rc = vdi::launch_pass(view(c), c->buf[c->cur], c->buf[c->cur ^ 1], k, nb, metric,
                                   c->tune.band_min_k, vdi::use_clamp(c->tune.clamp, metric, c->n, k, false),
                                   c->stream, false, vdi::use_dedup(c->tune.dedup, c->w, c->h, c->n, false),
-                                  vdi::use_byte_key(c->tune.byte_key, metric, c->w, c->h, c->n, k, false));
+                                  vdi::use_byte_key(c->tune.byte_key, metric, c->w, c->h, c->n, k, false),
+                                  c->tune.blocked, c->tune.key_pack, c->tune.blk_min_blocks,
+                                  vdi::use_sparse(c->tune.sparse, c->w, c->h, c->n, k));
   if (rc) return rc;
   ++c->launches;
   c->cur ^= 1;
@@ -1421,6 +1445,22 @@ extern "C" int vd_set_option(vd_ctx* c, int32_t option, int64_t value) {
       if (value < -1 || value > 1) return vd_fail(VD_EINVAL, "byte keys must be -1, 0 or 1");
       t.byte_key = static_cast<int>(value);
       break;
+    case VD_OPT_BLOCKED_PASS:
+      if (value < -1 || value > 1) return vd_fail(VD_EINVAL, "blocked pass must be -1, 0 or 1");
+      t.blocked = static_cast<int>(value);
+      break;
+    case VD_OPT_KEY_PACK:
+      if (value < 0 || value > 2) return vd_fail(VD_EINVAL, "key pack must be 0, 1 or 2");
+      t.key_pack = static_cast<int>(value);
+      break;
+    case VD_OPT_BLOCKED_MIN_BLOCKS:
+      if (value != 6 && value != 8) return vd_fail(VD_EINVAL, "blocked-pass blocks per SM must be 6 or 8");
+      t.blk_min_blocks = static_cast<int>(value);
+      break;
+    case VD_OPT_SPARSE_PASS:
+      if (value < -1 || value > 1) return vd_fail(VD_EINVAL, "sparse pass must be -1, 0 or 1");
+      t.sparse = static_cast<int>(value);
+      break;
     default:
       return vd_fail(VD_EINVAL, "unknown option %d", option);
   }
@@ -1445,6 +1485,10 @@ extern "C" int vd_get_option(const vd_ctx* c, int32_t option, int64_t* value) {
     case VD_OPT_PDL: *value = c->tune.pdl; break;
     case VD_OPT_DEDUP_GATHERS: *value = c->tune.dedup; break;
     case VD_OPT_BYTE_KEYS: *value = c->tune.byte_key; break;
+    case VD_OPT_BLOCKED_PASS: *value = c->tune.blocked; break;
+    case VD_OPT_KEY_PACK: *value = c->tune.key_pack; break;
+    case VD_OPT_BLOCKED_MIN_BLOCKS: *value = c->tune.blk_min_blocks; break;
+    case VD_OPT_SPARSE_PASS: *value = c->tune.sparse; break;
     default: return vd_fail(VD_EINVAL, "unknown option %d", option);
   }
   return VD_OK;

@@ -41,6 +41,10 @@ struct Tuning {
   int pdl = 1;     // chain a frame's kernels with programmatic dependent launch
   int dedup = -1;  // skip repeated table gathers in a label vector: -1 auto, 0 never, 1 always
   int byte_key = -1;  // Euclidean byte-offset keys: -1 auto, 0 never, 1 whenever usable
+  int blocked = -1;   // byte-key passes with k % 4 == 0 register-blocked over 2 x 2 quads: -1 auto, 0, 1
+  int key_pack = 0;   // byte-key packing: 0 multiply-add, 1 byte permute (below 2^16 seeds), 2 shift (wide form)
+  int blk_min_blocks = 8;  // register budget of the blocked pass: 6 or 8 resident blocks per SM
+  int sparse = -1;    // unchanged quads copied through, the rest compacted per block: -1 auto, 0, 1
 };
 
 // Event pairs bracketing kernel launches (profiling mode).  Records are kept
@@ -81,7 +85,11 @@ std::vector<Launch> plan_passes(const int32_t* ks, const int32_t* nbs, int n, in
                                 int max_halo);
 int launch_pass(const MapView& m, const int32_t* src, int32_t* dst, int32_t k, int32_t nb,
                 int32_t metric, int64_t band_min_k, bool clamp, cudaStream_t st, bool pdl = false,
-                bool dedup = false, bool byte_key = false);
+                bool dedup = false, bool byte_key = false, int blocked = 0, int key_pack = 0,
+                int blk_min_blocks = 8, bool sparse = false);
+// Whether a pass with step k runs in the sparse form (auto: k at most 1/32 of
+// the mean cell side).
+bool use_sparse(int sparse_option, int32_t w, int32_t h, int32_t n, int32_t k);
 bool use_dedup(int dedup_option, int32_t w, int32_t h, int32_t n, bool djfa_frame);
 int byte_key_window(int64_t n, int* lb_out);
 bool use_byte_key(int byte_option, int32_t metric, int32_t w, int32_t h, int32_t n, int32_t k,
@@ -101,4 +109,20 @@ int launch_build_table(const int2* seeds, int n, int2* table, uint32_t* ptable, 
 uint64_t rng_key(uint64_t rng_seed, uint64_t stream_id);
 int ensure_smem(const void* fn, size_t bytes, size_t* done);
 
+}  // namespace vdi
+
+namespace vdk {
+struct PassArgs;
+}
+
+namespace vdi {
+// The register-blocked byte-key pass (vd_pass_blk.cu): usable for steps
+// k % 4 == 0, k >= 4 with the byte-offset key forms (key 3 and 4).
+bool blk_applies(int32_t k, int key);
+int launch_pass_blk(const vdk::PassArgs& a, int32_t nb, int key, bool dedup, int pack, int minb, cudaStream_t st,
+                    bool pdl);
+// The sparse pass (vd_pass_sparse.cu): steps with k % 4 == 0, k = 1 or k = 2
+// (ksel 0, 1, 2), every key form, the plain pass's launch shape.
+int launch_pass_sparse(const vdk::PassArgs& a, dim3 grid, dim3 block, int32_t nb, int32_t metric, int key, int ksel,
+                       bool dedup, cudaStream_t st, bool pdl);
 }  // namespace vdi

@@ -25,6 +25,10 @@ OPT_CLAMPED_KEYS = 7
 OPT_PDL = 8
 OPT_DEDUP_GATHERS = 9
 OPT_BYTE_KEYS = 10
+OPT_BLOCKED_PASS = 11
+OPT_KEY_PACK = 12
+OPT_BLOCKED_MIN_BLOCKS = 13
+OPT_SPARSE_PASS = 14
 
 KERNEL_KINDS = ("pass", "fused", "stamp", "move", "fill")
 

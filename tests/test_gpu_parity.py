@@ -618,3 +618,143 @@ def test_byte_offset_keys(vd, orc, dedup, w, h, s):
     sim.jump_pass(4, M, L1)
     np.testing.assert_array_equal(sim.labels(), orc.jump_pass(w, h, xy, src, 4, M, L1))
     sim.close()
+
+
+@pytest.mark.parametrize("pack,minb", [(0, 8), (1, 6), (2, 8)])
+@pytest.mark.parametrize("dedup", [0, 1])
+@pytest.mark.parametrize("w,h,s", [(37, 29, 12), (300, 211, 500), (517, 263, 65535), (640, 480, 65536),
+                                   (1000, 700, 1 << 18)])
+def test_blocked_byte_pass(vd, orc, pack, minb, dedup, w, h, s):
+    """The register-blocked byte-key pass (each thread owns the quads at
+    (x, y), (x + k, y), (x, y + k), (x + k, y + k)) against the oracle: steps
+    that are multiples of 4 (including ones not a power of two, ones wider
+    than half the grid and ones that leave a quad block's far quads off the
+    map), both neighbourhoods, every key packing and register budget, maps of
+    random labels with and without empty ones, and dJFA steps in the
+    narrow (below 2^16 seeds) and wide (17-, 19-bit label) forms."""
+    g = np.random.default_rng(s + w + pack)
+    xy = inputs.uniform_seeds(w, h, s, seed=s + 5)
+    sim = _sim(vd, w, h, xy, byte_keys=1, dedup_gathers=dedup, blocked_pass=1, key_pack=pack,
+               blocked_min_blocks=minb)
+    for lo in (-1, 0):
+        src = g.integers(lo, s, size=(h, w), dtype=np.int32)
+        for k in [4, 8, 12, 16, 20, 64, 256]:
+            for nb in [M, VN]:
+                sim.set_labels(src)
+                sim.jump_pass(k, nb, E)
+                got = sim.labels()
+                want = orc.jump_pass(w, h, xy, src, k, nb, E)
+                assert np.array_equal(got, want), (k, nb, lo, int((got != want).sum()))
+    sim.jfa()
+    lab = orc.jfa(w, h, xy)
+    np.testing.assert_array_equal(sim.labels(), lab)
+    disp = inputs.displacements(s, 3, 2, seed=s)
+    for t in range(2):
+        sim.move(disp[t])
+        xy = orc.move(w, h, xy, disp[t])
+        sim.djfa_step(d_max=3)
+        lab = orc.djfa_step(w, h, xy, lab, d_max=3)
+        np.testing.assert_array_equal(sim.labels(), lab, err_msg=f"step {t}")
+    sim.close()
+
+
+def test_blocked_pass_matches_plain_at_full_size(vd, orc):
+    """8192 x 8192 with 2^18 seeds, moves in [-4, 4] (the benchmark's default
+    point): three dJFA steps with the blocked pass forced on and off give the
+    same maps, and the first equals the oracle."""
+    w = h = 8192
+    s, D = 1 << 18, 4
+    xy = inputs.uniform_seeds(w, h, s, seed=7)
+    disp = inputs.displacements(s, D, 3, seed=7)
+    a = _sim(vd, w, h, xy, use_graphs=1, blocked_pass=1)
+    b = _sim(vd, w, h, xy, use_graphs=1, blocked_pass=0)
+    a.jfa()
+    b.jfa()
+    lab = orc.jfa(w, h, xy)
+    for t in range(3):
+        for sim in (a, b):
+            sim.step(disp[t], d_max=D)
+        la = a.labels()
+        np.testing.assert_array_equal(la, b.labels(), err_msg=f"step {t}")
+        if t == 0:
+            xy = orc.move(w, h, xy, disp[t])
+            lab = orc.djfa_step(w, h, xy, lab, d_max=D)
+            np.testing.assert_array_equal(la, lab)
+    a.close()
+    b.close()
+
+
+@pytest.mark.parametrize("key", ["exact", "clamped", "byte"])
+@pytest.mark.parametrize("dedup", [0, 1])
+@pytest.mark.parametrize("w,h,s", [(37, 29, 3), (300, 211, 40), (517, 263, 500), (1000, 700, 70000)])
+def test_sparse_pass(vd, orc, key, dedup, w, h, s):
+    """The sparse pass (unchanged quads copied through, the rest scored after
+    a per-block compaction), forced on every step it applies to (k % 4 == 0,
+    k = 1, k = 2), against the oracle: smooth maps (a JFA frame: most quads
+    unchanged), the same with scattered wrong and empty labels, and nearly
+    empty maps (the stamps of a JFA frame's first pass), both neighbourhoods
+    and metrics, each key form, with and without de-duplicated gathers; then
+    a JFA frame and two dJFA steps."""
+    g = np.random.default_rng(s + w)
+    xy = inputs.uniform_seeds(w, h, s, seed=s + 9)
+    xy[-1] = xy[0]
+    forms = {"exact": dict(clamped_keys=0, byte_keys=0), "clamped": dict(clamped_keys=1, byte_keys=0),
+             "byte": dict(byte_keys=1)}[key]
+    sim = _sim(vd, w, h, xy, sparse_pass=1, dedup_gathers=dedup, **forms)
+    smooth = orc.jfa(w, h, xy)
+    noisy = smooth.copy()
+    pick = g.random((h, w)) < 0.01
+    noisy[pick] = g.integers(-1, s, size=int(pick.sum()), dtype=np.int32)
+    stamped = orc.stamp(w, h, xy, np.full((h, w), -1, np.int32))
+    for name, src in (("smooth", smooth), ("noisy", noisy), ("stamped", stamped)):
+        for k in [1, 2, 4, 8, 16, 64]:
+            for nb in [M, VN]:
+                for metric in [E, L1]:
+                    sim.set_labels(src)
+                    sim.jump_pass(k, nb, metric)
+                    got = sim.labels()
+                    want = orc.jump_pass(w, h, xy, src, k, nb, metric)
+                    assert np.array_equal(got, want), (name, k, nb, metric, int((got != want).sum()))
+    for metric in [E, L1]:
+        sim.jfa(metric=metric)
+        lab = orc.jfa(w, h, xy, metric=metric)
+        np.testing.assert_array_equal(sim.labels(), lab)
+        cur = xy
+        disp = inputs.displacements(s, 3, 2, seed=s + metric)
+        for t in range(2):
+            sim.move(disp[t])
+            cur = orc.move(w, h, cur, disp[t])
+            sim.djfa_step(d_max=3, metric=metric)
+            lab = orc.djfa_step(w, h, cur, lab, d_max=3, metric=metric)
+            np.testing.assert_array_equal(sim.labels(), lab, err_msg=f"metric {metric} step {t}")
+        sim.set_seeds(xy)
+    sim.close()
+
+
+@pytest.mark.parametrize("s,D", [(1 << 14, 4), (1 << 10, 1)])
+def test_sparse_auto_matches_plain_at_full_size(vd, orc, s, D):
+    """8192 x 8192 sweep points where the auto rule runs the sparse pass for
+    the small steps of every frame: JFA frame 0 and three graph-replayed dJFA
+    steps equal the same frames with the sparse pass off, and frame 0 and the
+    first step equal the oracle."""
+    w = h = 8192
+    xy = inputs.uniform_seeds(w, h, s, seed=11)
+    disp = inputs.displacements(s, D, 3, seed=11)
+    a = _sim(vd, w, h, xy, use_graphs=1)
+    b = _sim(vd, w, h, xy, use_graphs=1, sparse_pass=0)
+    a.jfa()
+    b.jfa()
+    lab = orc.jfa(w, h, xy)
+    np.testing.assert_array_equal(a.labels(), lab)
+    np.testing.assert_array_equal(b.labels(), lab)
+    for t in range(3):
+        for sim in (a, b):
+            sim.step(disp[t], d_max=D)
+        la = a.labels()
+        np.testing.assert_array_equal(la, b.labels(), err_msg=f"step {t}")
+        if t == 0:
+            xy = orc.move(w, h, xy, disp[t])
+            lab = orc.djfa_step(w, h, xy, lab, d_max=D)
+            np.testing.assert_array_equal(la, lab)
+    a.close()
+    b.close()
