@@ -556,6 +556,10 @@ def run_ours(args):
         "ms_per_frame": {"djfa": t_djfa_max / K, "jfa": t_jfa_max / K},
         "jfa": {"value": jfa_value, "unit": UNIT, "ms_per_step": t_jfa_max / K},
         "speedup_djfa_vs_jfa": t_jfa_max / t_djfa_max,
+        # the pass-count ratio beside the measured speedup: a speedup well
+        # above it would mean a slow JFA arm rather than fewer passes
+        "pass_ratio_jfa_vs_djfa": n_jfa / n_djfa,
+        "ms_per_pass": {"djfa": t_djfa_max / K / n_djfa, "jfa": t_jfa_max / K / n_jfa},
         "similarity": similarity,
         "roofline": roofline,
         "e2e": e2e,

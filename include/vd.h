@@ -542,6 +542,14 @@ int vd_server_set_max_batch(vd_server* server, int32_t max_batch);
                                     (default: steps of at most 1/32 of the mean cell side
                                     sqrt(w h / n), where nearly every quad is unchanged), 0 = never,
                                     1 = whenever it applies.  Results never depend on it */
+#define VD_OPT_JFA_POSITION_MAP 15 /* the passes of a JFA frame with k % 4 == 0 read and write a map of
+                                    (label, packed position) pairs, so that a candidate's position comes
+                                    with its label and nothing is gathered (JFA's middle passes, where
+                                    neighbouring pixels name unrelated distant seeds, are otherwise
+                                    bound by scattered table reads); 16 bytes a pixel per pass instead
+                                    of 8, two such maps allocated on first use.  -1 = auto (default:
+                                    maps of at least 2^20 pixels), 0 = never, 1 = always.  Results
+                                    never depend on it */
 int vd_set_option(vd_ctx* ctx, int32_t option, int64_t value);
 int vd_get_option(const vd_ctx* ctx, int32_t option, int64_t* value);
 

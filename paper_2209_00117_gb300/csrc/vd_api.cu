@@ -589,6 +589,7 @@ struct vd_ctx {
   cudaStream_t stream = nullptr;
   int32_t* buf[2] = {nullptr, nullptr};
   int cur = 0;
+  int2* pbuf[2] = {nullptr, nullptr};  // position maps of JFA frames (allocated on first use)
   int2* seeds = nullptr;
   int2* table = nullptr;   // n + 1 entries, [0] = sentinel
   uint32_t* ptable = nullptr;  // n + 1 packed positions, [0] = far position
@@ -666,6 +667,8 @@ static void ctx_free(vd_ctx* c) {
   clear_graphs(c);
   cudaFree(c->buf[0]);
   cudaFree(c->buf[1]);
+  cudaFree(c->pbuf[0]);
+  cudaFree(c->pbuf[1]);
   cudaFree(c->seeds);
   cudaFree(c->table);
   cudaFree(c->ptable);
@@ -1072,23 +1075,77 @@ static int count_launches(const int32_t* ks, const int32_t* nbs, int n, const vd
   return static_cast<int>(vdi::plan_passes(ks, nbs, n, t.fuse_max_k, t.max_halo).size());
 }
 
+// Leading passes of a JFA schedule that run on the position map (k % 4 == 0,
+// k >= 4), or 0 when the position map is not used for this context.
+static int jfa_position_passes(const vd_ctx* c, const int32_t* ks, int n) {
+  if (c->tune.pos_map == 0) return 0;
+  // auto: maps of at least 2^20 pixels (GB300, 8192^2 JFA frames: 2^18 seeds
+  // 7.27 -> 4.27 ms, 2^22 seeds 11.96 -> 5.28 ms, 2^14 seeds 4.42 -> 4.12 ms,
+  // 2^10 seeds 4.09 -> 4.04 ms)
+  if (c->tune.pos_map < 0 && static_cast<int64_t>(c->w) * c->h < (int64_t{1} << 20)) return 0;
+  int m = 0;
+  while (m < n && ks[m] >= 4 && ks[m] % 4 == 0) ++m;
+  return m;
+}
+
 extern "C" int vd_jfa(vd_ctx* c, int32_t extra, int32_t metric) {
   VD_CHECK_CTX(c);
   if (check_metric(metric)) return VD_EINVAL;
   int32_t ks[VD_MAX_PASSES], nbs[VD_MAX_PASSES];
   const int n = vd_jfa_schedule(c->w, c->h, extra, ks, nbs, VD_MAX_PASSES);
   if (n < 0) return n;
-  const int nl = count_launches(ks, nbs, n, c->tune);
-  const int cur_after = c->cur ^ (nl & 1);
+  const int m = jfa_position_passes(c, ks, n);
+  if (m > 0 && !c->pbuf[0]) {
+    const size_t bytes = sizeof(int2) * static_cast<size_t>(c->pitch) * c->h;
+    int rc = ctx_alloc(reinterpret_cast<void**>(&c->pbuf[0]), bytes, "position map");
+    if (!rc) rc = ctx_alloc(reinterpret_cast<void**>(&c->pbuf[1]), bytes, "position map");
+    if (rc) {
+      cudaFree(c->pbuf[0]);
+      c->pbuf[0] = c->pbuf[1] = nullptr;
+      return rc;
+    }
+  }
+  // launches after the fill and the stamp: the position-map passes (the last
+  // of them writes the label map), then the rest on the label map
+  const int nl = m > 0 ? m + count_launches(ks + m, nbs + m, n - m, c->tune) : count_launches(ks, nbs, n, c->tune);
+  const int flips = m > 0 ? 1 + count_launches(ks + m, nbs + m, n - m, c->tune) : nl;
+  const int cur_after = c->cur ^ (flips & 1);
   auto body = [&]() -> int {
     vdi::Profiler* pr = prof_of(c);
-    int pi = pr ? pr->begin(VD_KERNEL_FILL, static_cast<int64_t>(c->w) * c->h, c->stream) : -1;
+    const bool pdl = c->tune.pdl != 0;
+    const int64_t px = static_cast<int64_t>(c->w) * c->h;
+    if (m > 0) {
+      int pi = pr ? pr->begin(VD_KERNEL_FILL, px, c->stream) : -1;
+      int rc = vdi::launch_fill_pos(c->pbuf[0], static_cast<int64_t>(c->pitch) * c->h, c->stream, pdl);
+      if (pr) pr->end(pi, c->stream);
+      ++c->launches;
+      if (rc) return rc;
+      pi = pr ? pr->begin(VD_KERNEL_STAMP, c->n, c->stream) : -1;
+      rc = vdi::launch_stamp_pos(view(c), c->pbuf[0], c->stream, pdl);
+      if (pr) pr->end(pi, c->stream);
+      ++c->launches;
+      if (rc) return rc;
+      for (int i = 0; i < m; ++i) {
+        const bool last = i == m - 1;
+        pi = pr ? pr->begin(VD_KERNEL_PASS, px, c->stream) : -1;
+        rc = vdi::launch_pass_pos(view(c), c->pbuf[i & 1], last ? nullptr : c->pbuf[(i + 1) & 1],
+                                  last ? c->buf[c->cur ^ 1] : nullptr, ks[i], nbs[i], metric, c->tune.band_min_k,
+                                  c->stream, pdl);
+        if (pr) pr->end(pi, c->stream);
+        ++c->launches;
+        if (rc) return rc;
+      }
+      c->cur ^= 1;
+      return vdi::run_passes(view(c), c->buf, &c->cur, ks + m, nbs + m, n - m, metric, c->tune, c->stream,
+                             &c->launches, pr, false);
+    }
+    int pi = pr ? pr->begin(VD_KERNEL_FILL, px, c->stream) : -1;
     int rc = vdi::launch_fill(c->buf[c->cur], static_cast<int64_t>(c->pitch) * c->h, -1, c->stream);
     if (pr) pr->end(pi, c->stream);
     ++c->launches;
     if (rc) return rc;
     pi = pr ? pr->begin(VD_KERNEL_STAMP, c->n, c->stream) : -1;
-    rc = vdi::launch_stamp(view(c), c->buf[c->cur], false, c->stream, &c->launches, c->tune.pdl != 0);
+    rc = vdi::launch_stamp(view(c), c->buf[c->cur], false, c->stream, &c->launches, pdl);
     if (pr) pr->end(pi, c->stream);
     if (rc) return rc;
     return vdi::run_passes(view(c), c->buf, &c->cur, ks, nbs, n, metric, c->tune, c->stream, &c->launches, pr,
@@ -1461,6 +1518,10 @@ extern "C" int vd_set_option(vd_ctx* c, int32_t option, int64_t value) {
       if (value < -1 || value > 1) return vd_fail(VD_EINVAL, "sparse pass must be -1, 0 or 1");
       t.sparse = static_cast<int>(value);
       break;
+    case VD_OPT_JFA_POSITION_MAP:
+      if (value < -1 || value > 1) return vd_fail(VD_EINVAL, "JFA position map must be -1, 0 or 1");
+      t.pos_map = static_cast<int>(value);
+      break;
     default:
       return vd_fail(VD_EINVAL, "unknown option %d", option);
   }
@@ -1489,6 +1550,7 @@ extern "C" int vd_get_option(const vd_ctx* c, int32_t option, int64_t* value) {
     case VD_OPT_KEY_PACK: *value = c->tune.key_pack; break;
     case VD_OPT_BLOCKED_MIN_BLOCKS: *value = c->tune.blk_min_blocks; break;
     case VD_OPT_SPARSE_PASS: *value = c->tune.sparse; break;
+    case VD_OPT_JFA_POSITION_MAP: *value = c->tune.pos_map; break;
     default: return vd_fail(VD_EINVAL, "unknown option %d", option);
   }
   return VD_OK;

@@ -45,6 +45,7 @@ struct Tuning {
   int key_pack = 0;   // byte-key packing: 0 multiply-add, 1 byte permute (below 2^16 seeds), 2 shift (wide form)
   int blk_min_blocks = 8;  // register budget of the blocked pass: 6 or 8 resident blocks per SM
   int sparse = -1;    // unchanged quads copied through, the rest compacted per block: -1 auto, 0, 1
+  int pos_map = -1;   // JFA frames' k % 4 == 0 passes on a (label, position) map: -1 auto, 0, 1
 };
 
 // Event pairs bracketing kernel launches (profiling mode).  Records are kept
@@ -125,4 +126,11 @@ int launch_pass_blk(const vdk::PassArgs& a, int32_t nb, int key, bool dedup, int
 // (ksel 0, 1, 2), every key form, the plain pass's launch shape.
 int launch_pass_sparse(const vdk::PassArgs& a, dim3 grid, dim3 block, int32_t nb, int32_t metric, int key, int ksel,
                        bool dedup, cudaStream_t st, bool pdl);
+// The position map of JFA frames (vd_pass_pos.cu): per pixel (label, x | y << 16).
+int launch_fill_pos(int2* map, int64_t elems, cudaStream_t st, bool pdl);
+int launch_stamp_pos(const MapView& m, int2* map, cudaStream_t st, bool pdl);
+// One pass with k % 4 == 0 from the position map `src` into `dst`, or, when
+// dst32 is set, into that label map.
+int launch_pass_pos(const MapView& m, const int2* src, int2* dst, int32_t* dst32, int32_t k, int32_t nb,
+                    int32_t metric, int64_t band_min_k, cudaStream_t st, bool pdl);
 }  // namespace vdi

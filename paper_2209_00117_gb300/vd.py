@@ -29,6 +29,7 @@ OPT_BLOCKED_PASS = 11
 OPT_KEY_PACK = 12
 OPT_BLOCKED_MIN_BLOCKS = 13
 OPT_SPARSE_PASS = 14
+OPT_JFA_POSITION_MAP = 15
 
 KERNEL_KINDS = ("pass", "fused", "stamp", "move", "fill")
 

@@ -758,3 +758,30 @@ def test_sparse_auto_matches_plain_at_full_size(vd, orc, s, D):
             np.testing.assert_array_equal(la, lab)
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("band", [0, 16])
+@pytest.mark.parametrize("w,h,s", [(5, 3, 2), (37, 29, 7), (300, 211, 500), (1000, 700, 70000), (2048, 1024, 1000)])
+def test_jfa_position_map(vd, orc, band, w, h, s):
+    """JFA frames whose k % 4 == 0 passes run on the (label, position) map,
+    forced on (with and without k-strided band order), against the oracle:
+    both metrics, JFA+2, coinciding seeds, a grid whose only such pass is
+    also its last (5 x 3), eager and graph-replayed frames around a move."""
+    xy = inputs.uniform_seeds(w, h, s, seed=s + w)
+    xy[-1] = xy[0]
+    for metric in [E, L1]:
+        for extra in [0, 2]:
+            sim = _sim(vd, w, h, xy, jfa_position_map=1, band_order_min_k=band)
+            sim.jfa(extra=extra, metric=metric)
+            got = sim.labels()
+            want = orc.jfa(w, h, xy, extra=extra, metric=metric)
+            assert np.array_equal(got, want), (metric, extra, int((got != want).sum()))
+            sim.close()
+    sim = _sim(vd, w, h, xy, jfa_position_map=1, use_graphs=1)
+    d = inputs.displacements(s, 5, 1, seed=s)[0]
+    sim.jfa()
+    np.testing.assert_array_equal(sim.labels(), orc.jfa(w, h, xy))
+    sim.move(d)
+    sim.jfa()
+    np.testing.assert_array_equal(sim.labels(), orc.jfa(w, h, orc.move(w, h, xy, d)))
+    sim.close()
