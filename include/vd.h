@@ -225,6 +225,26 @@ int vd_stamp(vd_ctx* ctx);
  * diagnostics. */
 int vd_pass(vd_ctx* ctx, int32_t k, int32_t nb, int32_t metric);
 
+/*
+ * One jump pass (as vd_pass) that computes only rows [y0, y1) of the next
+ * map, reading rows y0 - k .. y1 - 1 + k of the current one; the other rows
+ * of the next map keep whatever they held.  This is the per-band step of a
+ * map split into row bands across GPUs (each GPU owns one band and, before
+ * every pass, receives from the others the rows y0 - k .. y0 - 1 and
+ * y1 .. y1 - 1 + k its band reads -- for JFA's first steps k exceeds the
+ * band height, so they come from bands further away).  The pass reads its
+ * neighbours k rows away (Table I, Section V-B), so a band's halo is k rows
+ * deep; Eq. 4 bounds dJFA's largest step, and with it the halo.  djfa_frame
+ * = 1 picks the key forms of a dJFA frame's passes, 0 those of a JFA frame
+ * (results never depend on it).  VD_EINVAL for a bad step, neighbourhood,
+ * metric or row range (0 <= y0 < y1 <= h).
+ */
+int vd_pass_rows(vd_ctx* ctx, int32_t k, int32_t nb, int32_t metric, int32_t y0, int32_t y1, int32_t djfa_frame);
+
+/* Empties the current map (label -1 everywhere): the first step of a JFA
+ * frame (Section III), for frames assembled from vd_stamp and vd_pass_rows. */
+int vd_clear_labels(vd_ctx* ctx);
+
 /* Overwrites the label map with a dense w x h map.  Every label must lie in
  * [-1, n_seeds): VD_EINVAL otherwise (checked on the host for host input, by a
  * kernel plus a synchronisation for device input) and the map is unchanged. */

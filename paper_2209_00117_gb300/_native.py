@@ -47,6 +47,8 @@ SIGNATURES = {
     "vd_step": (_int, [_p, _p, _int, _i32, _u64, _u64, _i64, _i32, _i32, _i32, _i32]),
     "vd_stamp": (_int, [_p]),
     "vd_pass": (_int, [_p, _i32, _i32, _i32]),
+    "vd_pass_rows": (_int, [_p, _i32, _i32, _i32, _i32, _i32, _i32]),
+    "vd_clear_labels": (_int, [_p]),
     "vd_set_labels": (_int, [_p, _p, _int]),
     "vd_get_labels": (_int, [_p, _p, _int]),
     "vd_labels_device_ptr": (_int, [_p, ctypes.POINTER(_p)]),

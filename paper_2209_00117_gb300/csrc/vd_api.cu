@@ -252,7 +252,10 @@ bool use_byte_key(int byte_option, int32_t metric, int32_t w, int32_t h, int32_t
 
 int launch_pass(const MapView& m, const int32_t* src, int32_t* dst, int32_t k, int32_t nb,
                 int32_t metric, int64_t band_min_k, bool clamp, cudaStream_t st, bool pdl, bool dedup,
-                bool byte_key, int blocked, int key_pack, int blk_min_blocks, bool sparse) {
+                bool byte_key, int blocked, int key_pack, int blk_min_blocks, bool sparse, int32_t y0,
+                int32_t y1) {
+  if (y1 < 0) y1 = m.h;
+  const bool rows_only = y0 != 0 || y1 != m.h;
   vdk::PassArgs a;
   a.src = src;
   a.dst = dst;
@@ -276,10 +279,12 @@ int launch_pass(const MapView& m, const int32_t* src, int32_t* dst, int32_t k, i
   a.k = k;
   a.band_m = 1;
   a.band_t = 1;
+  a.y0 = y0;
+  a.y_end = y1;
   const int quads = m.pitch / 4;
   const int bx = quads < 64 ? quads : 64;
   const int by = vdk::kPassThreads / bx;
-  const int nrb = (m.h + by - 1) / by;
+  const int nrb = (y1 - y0 + by - 1) / by;
   dim3 block(bx, by);
   dim3 grid((quads + bx - 1) / bx, nrb);
   bool band = false;
@@ -302,13 +307,15 @@ int launch_pass(const MapView& m, const int32_t* src, int32_t* dst, int32_t k, i
     else if (a.cap != 0) key = 1;
   }
   if (byte_key && metric == VD_METRIC_EUCLID && a.cap != 0 && a.bwin_bias != 0) key = m.n < 65536 ? 3 : 4;
-  if (sparse && ksel <= 2) return launch_pass_sparse(a, grid, block, nb, metric, key, ksel, dedup, st, pdl);
+  // a pass over a row range (one band of a split map) always takes the plain kernel
+  if (!rows_only && sparse && ksel <= 2)
+    return launch_pass_sparse(a, grid, block, nb, metric, key, ksel, dedup, st, pdl);
   // the register-blocked form: opt-in (blocked == 1).  It loads and gathers
   // each vector once for up to four quads, but needs 64 registers a thread
   // (half the resident warps) and measured slower than the plain pass on the
   // GB300 (8192^2, 2^18 seeds: Von Neumann k = 32 189 -> 244 us, Moore k = 8
   // 268 -> 275 us; 2^14 seeds likewise), so auto leaves it off
-  if (blocked == 1 && blk_applies(k, key))
+  if (!rows_only && blocked == 1 && blk_applies(k, key))
     return launch_pass_blk(a, nb, key, dedup, key_pack, blk_min_blocks, st, pdl);
   cudaError_t e;
   if (nb == VD_NB_MOORE) {
@@ -1275,6 +1282,33 @@ extern "C" int vd_pass(vd_ctx* c, int32_t k, int32_t nb, int32_t metric) {
   if (rc) return rc;
   ++c->launches;
   c->cur ^= 1;
+  return VD_OK;
+}
+
+extern "C" int vd_pass_rows(vd_ctx* c, int32_t k, int32_t nb, int32_t metric, int32_t y0, int32_t y1,
+                            int32_t djfa_frame) {
+  VD_CHECK_CTX(c);
+  if (check_metric(metric)) return VD_EINVAL;
+  if (k < 1) return vd_fail(VD_EINVAL, "step %d < 1", k);
+  if (nb != VD_NB_MOORE && nb != VD_NB_VON_NEUMANN) return vd_fail(VD_EINVAL, "neighbourhood %d", nb);
+  if (y0 < 0 || y1 > c->h || y0 >= y1) return vd_fail(VD_EINVAL, "rows [%d, %d) outside [0, %d)", y0, y1, c->h);
+  const bool dj = djfa_frame != 0;
+  const int rc = vdi::launch_pass(view(c), c->buf[c->cur], c->buf[c->cur ^ 1], k, nb, metric,
+                                  c->tune.band_min_k, vdi::use_clamp(c->tune.clamp, metric, c->n, k, dj),
+                                  c->stream, false, vdi::use_dedup(c->tune.dedup, c->w, c->h, c->n, dj),
+                                  vdi::use_byte_key(c->tune.byte_key, metric, c->w, c->h, c->n, k, dj), 0, 0, 8,
+                                  false, y0, y1);
+  if (rc) return rc;
+  ++c->launches;
+  c->cur ^= 1;
+  return VD_OK;
+}
+
+extern "C" int vd_clear_labels(vd_ctx* c) {
+  VD_CHECK_CTX(c);
+  const int rc = vdi::launch_fill(c->buf[c->cur], static_cast<int64_t>(c->pitch) * c->h, -1, c->stream);
+  if (rc) return rc;
+  ++c->launches;
   return VD_OK;
 }
 

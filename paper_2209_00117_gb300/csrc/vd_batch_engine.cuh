@@ -236,6 +236,8 @@ __device__ __forceinline__ void round_tile(const BatchArgs& A, int r, int t) {
   a.n_seeds = static_cast<uint32_t>(sd->n);
   a.w = sd->w;
   a.h = sd->h;
+  a.y0 = 0;
+  a.y_end = sd->h;
   a.pitch = sd->pitch;
   a.k = k;
   a.band_m = 1;

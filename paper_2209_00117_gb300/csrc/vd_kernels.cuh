@@ -129,6 +129,7 @@ struct PassArgs {
   int w, h, pitch, k;
   int band_m;  // > 1: visit row-blocks in k-strided bands (band_m = k / rows per block)
   int band_t;  // row-blocks per band residue class
+  int y0, y_end;  // k_pass writes rows [y0, y_end) of dst (the whole map: 0, h)
 };
 
 // Stops the compiler from hoisting later loads above this point, which keeps
@@ -613,8 +614,8 @@ __global__ void __launch_bounds__(kPassThreads, KEY >= 3 ? VD_BYTE_MIN_BLOCKS : 
   const int x0 = 4 * static_cast<int>(blockIdx.x * blockDim.x + threadIdx.x);
   int rb = blockIdx.y;
   if (a.band_m > 1) rb = (blockIdx.y % a.band_t) * a.band_m + blockIdx.y / a.band_t;
-  const int y = rb * static_cast<int>(blockDim.y) + static_cast<int>(threadIdx.y);
-  if (x0 >= a.pitch || y >= a.h) return;
+  const int y = a.y0 + rb * static_cast<int>(blockDim.y) + static_cast<int>(threadIdx.y);
+  if (x0 >= a.pitch || y >= a.y_end) return;
   if (KEY == 3 || KEY == 4) pass_quad_byte<NB, KSEL, false, DEDUP, KEY == 4>(a, x0, y);
   else if (KEY != 0) pass_quad_clamped<NB, KSEL, false, METRIC, DEDUP, KEY == 2>(a, x0, y);
   else pass_quad<NB, METRIC, KSEL, false, DEDUP>(a, x0, y);

@@ -252,6 +252,16 @@ class VoronoiSim:
     def jump_pass(self, k: int, nb: int = MOORE, metric: int = EUCLID):
         N.check(self._lib.vd_pass(self._h, int(k), int(nb), int(metric)))
 
+    def pass_rows(self, k: int, nb: int, y0: int, y1: int, metric: int = EUCLID, djfa_frame: bool = True):
+        """One pass writing only rows [y0, y1) of the next map (one band of a
+        split map; see vd_pass_rows)."""
+        N.check(self._lib.vd_pass_rows(self._h, int(k), int(nb), int(metric), int(y0), int(y1),
+                                       1 if djfa_frame else 0))
+
+    def clear_labels(self):
+        """Empties the current map (label -1 everywhere)."""
+        N.check(self._lib.vd_clear_labels(self._h))
+
     # -- maps -----------------------------------------------------------
     def set_labels(self, labels):
         ptr, dev = _buf(labels, self.w * self.h)
