@@ -428,11 +428,16 @@ int vd_batch_get_option(const vd_batch* batch, int32_t option, int64_t* value);
 
 /*
  * Autotuner: times `steps` dJFA steps (after one warm-up step) for each
- * candidate launch shape (mode x rows per thread), restoring the batch's
+ * candidate launch shape, restoring the batch's
  * complete state (maps, seeds, step counters) before each candidate and at
  * the end, so tuning leaves the simulation unchanged.  Keeps the fastest
  * candidate; writes its index to *best and each candidate's ms per step to
- * ms_per_step[0 .. cap).  Returns the number of candidates.
+ * ms_per_step[0 .. cap).  Returns the number of candidates.  The candidates,
+ * in order (mode, rows per thread, blocks per SM): per-round launches with 1,
+ * 2 or 4 rows per thread (tiles of 256 x 4, 8 or 16 pixels) [0-2]; the
+ * persistent launch with 1, 2 or 4 rows per thread at the occupancy maximum
+ * [3-5]; the persistent launch with 1 or 2 rows per thread capped at 3 blocks
+ * per SM [6-7] and at 2 [8-9].
  */
 int vd_batch_autotune(vd_batch* batch, int32_t steps, int32_t max_disp, uint64_t rng_seed,
                       int32_t* best, double* ms_per_step, int32_t cap);
@@ -570,7 +575,33 @@ int vd_server_set_max_batch(vd_server* server, int32_t max_batch);
                                     of 8, two such maps allocated on first use.  -1 = auto (default:
                                     maps of at least 2^20 pixels), 0 = never, 1 = always.  Results
                                     never depend on it */
+#define VD_OPT_PASS_TILE 16      /* block tile of the jump pass: 128 threads as 64 quads (256 pixels) x 2
+                                    rows (default), 32 x 4 or 128 x 1.  Results never depend on it */
 int vd_set_option(vd_ctx* ctx, int32_t option, int64_t value);
+
+/*
+ * Autotuner of the jump passes' launch shape for this context's dJFA frames
+ * (the paper has no counterpart; the choices never change a result).  From a
+ * device snapshot of the state (map, seeds, tables), each candidate setting
+ * runs `steps` timed dJFA steps (vd_step with SplitMix64 moves in
+ * [-max_disp, max_disp], stream 0, steps 0 .. steps - 1; d_max, vn_waves and
+ * metric as for vd_djfa_step) after one untimed step; the snapshot is
+ * restored before every candidate and at the end, so the state is left as it
+ * was.  The search goes through one dimension at a time, the others held at
+ * the best so far: the pass block tile (VD_OPT_PASS_TILE 64, 32, 128),
+ * gather de-duplication (VD_OPT_DEDUP_GATHERS -1, 0, 1), the sparse form
+ * (VD_OPT_SPARSE_PASS -1, 0, 1), the register-blocked form
+ * (VD_OPT_BLOCKED_PASS -1, 1) and, when on, its blocks per SM
+ * (VD_OPT_BLOCKED_MIN_BLOCKS 8, 6), and the shared-memory fusion depth of
+ * small steps (VD_OPT_FUSE_MAX_K 0, 2, 4).  The fastest setting stays in
+ * force.  chosen (may be NULL) receives 6 values in that order; ms_per_step
+ * (at least cap entries, may be NULL with cap = 0) the time of each candidate
+ * measured, in order.  Allocates and frees one map-sized snapshot; synchronises
+ * the stream.  Returns the number of candidates measured, or a VD_E* code
+ * (the tuning is then left unchanged).
+ */
+int vd_autotune(vd_ctx* ctx, int32_t d_max, int32_t max_disp, int32_t vn_waves, int32_t metric, uint64_t rng_seed,
+                int32_t steps, int32_t* chosen, double* ms_per_step, int32_t cap);
 int vd_get_option(const vd_ctx* ctx, int32_t option, int64_t* value);
 
 /* Kernel kinds reported by vd_profile_read. */

@@ -59,6 +59,7 @@ SIGNATURES = {
     "vd_similarity_ctx": (_int, [_p, _p, _PU64]),
     "vd_exact": (_int, [_p, _p, _p, _int, _i32]),
     "vd_set_option": (_int, [_p, _i32, _i64]),
+    "vd_autotune": (_int, [_p, _i32, _i32, _i32, _i32, _u64, _i32, _P32, _p, _i32]),
     "vd_get_option": (_int, [_p, _i32, ctypes.POINTER(_i64)]),
     "vd_launch_count": (_i64, [_p]),
     "vd_profile_read": (_int, [_p, _p, _p, _p]),

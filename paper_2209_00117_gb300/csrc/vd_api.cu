@@ -253,7 +253,7 @@ bool use_byte_key(int byte_option, int32_t metric, int32_t w, int32_t h, int32_t
 int launch_pass(const MapView& m, const int32_t* src, int32_t* dst, int32_t k, int32_t nb,
                 int32_t metric, int64_t band_min_k, bool clamp, cudaStream_t st, bool pdl, bool dedup,
                 bool byte_key, int blocked, int key_pack, int blk_min_blocks, bool sparse, int32_t y0,
-                int32_t y1) {
+                int32_t y1, int pass_bx) {
   if (y1 < 0) y1 = m.h;
   const bool rows_only = y0 != 0 || y1 != m.h;
   vdk::PassArgs a;
@@ -282,7 +282,8 @@ int launch_pass(const MapView& m, const int32_t* src, int32_t* dst, int32_t k, i
   a.y0 = y0;
   a.y_end = y1;
   const int quads = m.pitch / 4;
-  const int bx = quads < 64 ? quads : 64;
+  const int tile = (pass_bx == 32 || pass_bx == 128) ? pass_bx : 64;
+  const int bx = quads < tile ? quads : tile;
   const int by = vdk::kPassThreads / bx;
   const int nrb = (y1 - y0 + by - 1) / by;
   dim3 block(bx, by);
@@ -442,7 +443,7 @@ int run_passes(const MapView& m, int32_t* const buf[2], int* cur, const int32_t*
                        use_dedup(t.dedup, m.w, m.h, m.n, djfa_frame),
                        use_byte_key(t.byte_key, metric, m.w, m.h, m.n, ks[l.first], djfa_frame), t.blocked,
                        t.key_pack, t.blk_min_blocks,
-                       use_sparse(t.sparse, m.w, m.h, m.n, ks[l.first]));
+                       use_sparse(t.sparse, m.w, m.h, m.n, ks[l.first]), 0, -1, t.pass_bx);
     } else {
       rc = launch_fused(m, src, dst, ks + l.first, nbs + l.first, l.n, metric, t.tile_x, t.tile_y, st);
     }
@@ -1278,11 +1279,156 @@ extern "C" int vd_pass(vd_ctx* c, int32_t k, int32_t nb, int32_t metric) {
                                   c->stream, false, vdi::use_dedup(c->tune.dedup, c->w, c->h, c->n, false),
                                   vdi::use_byte_key(c->tune.byte_key, metric, c->w, c->h, c->n, k, false),
                                   c->tune.blocked, c->tune.key_pack, c->tune.blk_min_blocks,
-                                  vdi::use_sparse(c->tune.sparse, c->w, c->h, c->n, k));
+                                  vdi::use_sparse(c->tune.sparse, c->w, c->h, c->n, k), 0, -1, c->tune.pass_bx);
   if (rc) return rc;
   ++c->launches;
   c->cur ^= 1;
   return VD_OK;
+}
+
+// Times `steps` dJFA steps (vd_step, RNG moves of steps 0 .. steps - 1) from
+// the snapshot with the tuning `t`; returns ms per step in *ms.
+struct TuneSnapshot {
+  int32_t* map = nullptr;
+  int2* seeds = nullptr;
+  int2* table = nullptr;
+  uint32_t* ptable = nullptr;
+  int cur = 0;
+  bool repair = false;
+  void release() {
+    cudaFree(map);
+    cudaFree(seeds);
+    cudaFree(table);
+    cudaFree(ptable);
+    map = nullptr;
+    seeds = nullptr;
+    table = nullptr;
+    ptable = nullptr;
+  }
+};
+
+static int tune_snapshot(vd_ctx* c, TuneSnapshot& sn, bool save) {
+  const size_t map_bytes = sizeof(int32_t) * static_cast<size_t>(c->pitch) * c->h;
+  const size_t n = static_cast<size_t>(c->n);
+  cudaError_t e;
+  if (save) {
+    sn.cur = c->cur;
+    sn.repair = c->repair;
+    e = cudaMemcpyAsync(sn.map, c->buf[c->cur], map_bytes, cudaMemcpyDeviceToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(sn.seeds, c->seeds, sizeof(int2) * n, cudaMemcpyDeviceToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(sn.table, c->table, sizeof(int2) * (n + 1), cudaMemcpyDeviceToDevice, c->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(sn.ptable, c->ptable, sizeof(uint32_t) * (n + 1), cudaMemcpyDeviceToDevice, c->stream);
+  } else {
+    c->cur = sn.cur;
+    c->repair = sn.repair;
+    e = cudaMemcpyAsync(c->buf[c->cur], sn.map, map_bytes, cudaMemcpyDeviceToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->seeds, sn.seeds, sizeof(int2) * n, cudaMemcpyDeviceToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->table, sn.table, sizeof(int2) * (n + 1), cudaMemcpyDeviceToDevice, c->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(c->ptable, sn.ptable, sizeof(uint32_t) * (n + 1), cudaMemcpyDeviceToDevice, c->stream);
+  }
+  return vd_cuda_check(e, "autotune snapshot copy");
+}
+
+extern "C" int vd_autotune(vd_ctx* c, int32_t d_max, int32_t max_disp, int32_t vn_waves, int32_t metric,
+                           uint64_t rng_seed, int32_t steps, int32_t* chosen, double* ms_per_step, int32_t cap) {
+  VD_CHECK_CTX(c);
+  if (check_metric(metric)) return VD_EINVAL;
+  if (steps < 1 || steps > 1000) return vd_fail(VD_EINVAL, "steps outside [1, 1000]");
+  if (max_disp < 0 || d_max < 0) return vd_fail(VD_EINVAL, "negative displacement bound");
+  if (cap > 0 && !ms_per_step) return vd_fail(VD_EINVAL, "null times with cap > 0");
+  int32_t ks[VD_MAX_PASSES], nbs[VD_MAX_PASSES];
+  if (vd_djfa_schedule(c->w, c->h, c->n, d_max, vn_waves, 0, ks, nbs, VD_MAX_PASSES) < 0) return VD_EINVAL;
+  TuneSnapshot sn;
+  const size_t map_bytes = sizeof(int32_t) * static_cast<size_t>(c->pitch) * c->h;
+  int rc = ctx_alloc(reinterpret_cast<void**>(&sn.map), map_bytes, "autotune snapshot");
+  if (!rc) rc = ctx_alloc(reinterpret_cast<void**>(&sn.seeds), sizeof(int2) * c->n, "autotune snapshot");
+  if (!rc) rc = ctx_alloc(reinterpret_cast<void**>(&sn.table), sizeof(int2) * (static_cast<size_t>(c->n) + 1), "autotune snapshot");
+  if (!rc) rc = ctx_alloc(reinterpret_cast<void**>(&sn.ptable), sizeof(uint32_t) * (static_cast<size_t>(c->n) + 1), "autotune snapshot");
+  if (!rc) rc = tune_snapshot(c, sn, true);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (!rc) rc = vd_cuda_check(cudaEventCreate(&e0), "event");
+  if (!rc) rc = vd_cuda_check(cudaEventCreate(&e1), "event");
+  const vdi::Tuning t0 = c->tune;
+  const int64_t launches0 = c->launches;
+  int measured = 0;
+  auto measure = [&](const vdi::Tuning& t, double* ms) -> int {
+    c->tune = t;
+    c->tune.profile = 0;
+    clear_graphs(c);
+    int r = tune_snapshot(c, sn, false);
+    // one untimed step (graph capture), then the timed ones, each from the snapshot
+    for (int s = 0; !r && s <= steps; ++s) {
+      if (s == 1) r = vd_cuda_check(cudaEventRecord(e0, c->stream), "event");
+      if (!r) r = vd_step(c, nullptr, 0, max_disp, rng_seed, 0, s, d_max, vn_waves, 0, metric);
+    }
+    if (!r) r = vd_cuda_check(cudaEventRecord(e1, c->stream), "event");
+    if (!r) r = vd_cuda_check(cudaEventSynchronize(e1), "event sync");
+    float el = 0.f;
+    if (!r) r = vd_cuda_check(cudaEventElapsedTime(&el, e0, e1), "elapsed");
+    if (!r) {
+      *ms = static_cast<double>(el) / steps;
+      if (ms_per_step && measured < cap) ms_per_step[measured] = *ms;
+      ++measured;
+    }
+    return r;
+  };
+  // coordinate search: each dimension in turn, the others at the best so far
+  vdi::Tuning best = t0;
+  double best_ms = 0.0;
+  if (!rc) rc = measure(best, &best_ms);
+  struct Dim {
+    int vdi::Tuning::*field;
+    std::vector<int> values;
+  };
+  const Dim dims[] = {
+      {&vdi::Tuning::pass_bx, {64, 32, 128}},      // block tile
+      {&vdi::Tuning::dedup, {-1, 0, 1}},           // gather de-duplication
+      {&vdi::Tuning::sparse, {-1, 0, 1}},          // sparse form of small steps
+      {&vdi::Tuning::blocked, {-1, 1}},            // register-blocked byte-key form
+      {&vdi::Tuning::blk_min_blocks, {8, 6}},      // its blocks per SM
+      {&vdi::Tuning::fuse_max_k, {0, 2, 4}},       // shared-memory fusion depth of small steps
+  };
+  for (const Dim& d : dims) {
+    if (rc) break;
+    if (d.field == &vdi::Tuning::blk_min_blocks && best.blocked != 1) continue;  // no effect
+    const int start = best.*(d.field);
+    for (int v : d.values) {
+      if (rc) break;
+      if (v == start) continue;
+      vdi::Tuning t = best;
+      t.*(d.field) = v;
+      double ms = 0.0;
+      rc = measure(t, &ms);
+      if (!rc && ms < best_ms) {
+        best_ms = ms;
+        best = t;
+      }
+    }
+  }
+  // the state exactly as it was, and the fastest setting kept
+  const int rrc = tune_snapshot(c, sn, false);
+  if (!rc) rc = rrc;
+  if (!rc) rc = vd_cuda_check(cudaStreamSynchronize(c->stream), "synchronize");
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  sn.release();
+  c->tune = rc ? t0 : best;
+  c->tune.profile = t0.profile;
+  c->tune.use_graphs = t0.use_graphs;
+  c->launches = launches0;
+  clear_graphs(c);
+  if (rc) return rc;
+  if (chosen) {
+    chosen[0] = best.pass_bx;
+    chosen[1] = best.dedup;
+    chosen[2] = best.sparse;
+    chosen[3] = best.blocked;
+    chosen[4] = best.blk_min_blocks;
+    chosen[5] = best.fuse_max_k;
+  }
+  return measured;
 }
 
 extern "C" int vd_pass_rows(vd_ctx* c, int32_t k, int32_t nb, int32_t metric, int32_t y0, int32_t y1,
@@ -1297,7 +1443,7 @@ extern "C" int vd_pass_rows(vd_ctx* c, int32_t k, int32_t nb, int32_t metric, in
                                   c->tune.band_min_k, vdi::use_clamp(c->tune.clamp, metric, c->n, k, dj),
                                   c->stream, false, vdi::use_dedup(c->tune.dedup, c->w, c->h, c->n, dj),
                                   vdi::use_byte_key(c->tune.byte_key, metric, c->w, c->h, c->n, k, dj), 0, 0, 8,
-                                  false, y0, y1);
+                                  false, y0, y1, c->tune.pass_bx);
   if (rc) return rc;
   ++c->launches;
   c->cur ^= 1;
@@ -1556,6 +1702,10 @@ extern "C" int vd_set_option(vd_ctx* c, int32_t option, int64_t value) {
       if (value < -1 || value > 1) return vd_fail(VD_EINVAL, "JFA position map must be -1, 0 or 1");
       t.pos_map = static_cast<int>(value);
       break;
+    case VD_OPT_PASS_TILE:
+      if (value != 32 && value != 64 && value != 128) return vd_fail(VD_EINVAL, "pass tile must be 32, 64 or 128");
+      t.pass_bx = static_cast<int>(value);
+      break;
     default:
       return vd_fail(VD_EINVAL, "unknown option %d", option);
   }
@@ -1585,6 +1735,7 @@ extern "C" int vd_get_option(const vd_ctx* c, int32_t option, int64_t* value) {
     case VD_OPT_BLOCKED_MIN_BLOCKS: *value = c->tune.blk_min_blocks; break;
     case VD_OPT_SPARSE_PASS: *value = c->tune.sparse; break;
     case VD_OPT_JFA_POSITION_MAP: *value = c->tune.pos_map; break;
+    case VD_OPT_PASS_TILE: *value = c->tune.pass_bx; break;
     default: return vd_fail(VD_EINVAL, "unknown option %d", option);
   }
   return VD_OK;

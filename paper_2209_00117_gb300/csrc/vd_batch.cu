@@ -601,7 +601,11 @@ extern "C" int vd_batch_autotune(vd_batch* b, int32_t steps, int32_t max_disp, u
   struct Cand {
     int mode, rpt, bps;
   };
-  const Cand cands[] = {{0, 1, 0}, {0, 2, 0}, {0, 4, 0}, {1, 1, 0}, {1, 2, 0}, {1, 4, 0}};
+  // per-round launches with tiles of 256 x 4 r pixels (r rows per thread), and
+  // the persistent launch at the occupancy maximum or capped at 3 or 2 blocks
+  // per SM (fewer co-resident blocks: fewer arrivals at each grid barrier)
+  const Cand cands[] = {{0, 1, 0}, {0, 2, 0}, {0, 4, 0}, {1, 1, 0}, {1, 2, 0}, {1, 4, 0},
+                        {1, 1, 3}, {1, 2, 3}, {1, 1, 2}, {1, 2, 2}};
   const int nc = static_cast<int>(sizeof(cands) / sizeof(cands[0]));
   int rc = vd_batch_synchronize(b);
   if (rc) return rc;

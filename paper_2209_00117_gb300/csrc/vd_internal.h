@@ -46,6 +46,7 @@ struct Tuning {
   int blk_min_blocks = 8;  // register budget of the blocked pass: 6 or 8 resident blocks per SM
   int sparse = -1;    // unchanged quads copied through, the rest compacted per block: -1 auto, 0, 1
   int pos_map = -1;   // JFA frames' k % 4 == 0 passes on a (label, position) map: -1 auto, 0, 1
+  int pass_bx = 64;   // pass block tile: quads per row (32, 64, 128) x 128 / that many rows
 };
 
 // Event pairs bracketing kernel launches (profiling mode).  Records are kept
@@ -87,7 +88,8 @@ std::vector<Launch> plan_passes(const int32_t* ks, const int32_t* nbs, int n, in
 int launch_pass(const MapView& m, const int32_t* src, int32_t* dst, int32_t k, int32_t nb,
                 int32_t metric, int64_t band_min_k, bool clamp, cudaStream_t st, bool pdl = false,
                 bool dedup = false, bool byte_key = false, int blocked = 0, int key_pack = 0,
-                int blk_min_blocks = 8, bool sparse = false, int32_t y0 = 0, int32_t y1 = -1);
+                int blk_min_blocks = 8, bool sparse = false, int32_t y0 = 0, int32_t y1 = -1,
+                int pass_bx = 64);
 // Whether a pass with step k runs in the sparse form (auto: k at most 1/32 of
 // the mean cell side).
 bool use_sparse(int sparse_option, int32_t w, int32_t h, int32_t n, int32_t k);

@@ -30,6 +30,7 @@ OPT_KEY_PACK = 12
 OPT_BLOCKED_MIN_BLOCKS = 13
 OPT_SPARSE_PASS = 14
 OPT_JFA_POSITION_MAP = 15
+OPT_PASS_TILE = 16
 
 KERNEL_KINDS = ("pass", "fused", "stamp", "move", "fill")
 
@@ -251,6 +252,20 @@ class VoronoiSim:
 
     def jump_pass(self, k: int, nb: int = MOORE, metric: int = EUCLID):
         N.check(self._lib.vd_pass(self._h, int(k), int(nb), int(metric)))
+
+    def autotune(self, d_max: int, max_disp: int, vn_waves: int = 2, metric: int = EUCLID, rng_seed: int = 0,
+                 steps: int = 5):
+        """Times the pass launch shapes on this context's dJFA steps and keeps
+        the fastest (state left as it was; see vd_autotune).  Returns
+        ({option: value}, [ms per step of each candidate measured])."""
+        chosen = np.zeros(6, np.int32)
+        times = np.zeros(64, np.float64)
+        n = self._lib.vd_autotune(self._h, int(d_max), int(max_disp), int(vn_waves), int(metric),
+                                  int(rng_seed) & (2**64 - 1), int(steps),
+                                  chosen.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), times.ctypes.data, 64)
+        N.check(min(n, 0))
+        names = ["pass_tile", "dedup_gathers", "sparse_pass", "blocked_pass", "blocked_min_blocks", "fuse_max_k"]
+        return dict(zip(names, (int(v) for v in chosen))), [float(t) for t in times[:n]]
 
     def pass_rows(self, k: int, nb: int, y0: int, y1: int, metric: int = EUCLID, djfa_frame: bool = True):
         """One pass writing only rows [y0, y1) of the next map (one band of a

@@ -785,3 +785,62 @@ def test_jfa_position_map(vd, orc, band, w, h, s):
     sim.jfa()
     np.testing.assert_array_equal(sim.labels(), orc.jfa(w, h, orc.move(w, h, xy, d)))
     sim.close()
+
+
+@pytest.mark.parametrize("w,h,s,D", [(1024, 768, 4000, 2), (2048, 2048, 1 << 14, 4)])
+def test_autotune_keeps_state_and_results(vd, orc, w, h, s, D):
+    """vd_autotune times the pass launch shapes on the context's own dJFA
+    steps and keeps the fastest: the state after tuning equals the state
+    before it, and the tuned context's next steps equal an untuned twin's
+    (and the oracle's) bit for bit."""
+    import torch
+
+    xy = inputs.uniform_seeds(w, h, s, seed=13)
+    disp = inputs.displacements(s, D, 3, seed=13)
+    a = _sim(vd, w, h, xy, use_graphs=1)
+    b = _sim(vd, w, h, xy, use_graphs=1)
+    a.jfa()
+    b.jfa()
+    before = a.labels()
+    chosen, times = a.autotune(d_max=D, max_disp=D, steps=3)
+    assert len(times) >= 8 and all(t > 0 for t in times)
+    assert chosen["pass_tile"] in (32, 64, 128) and chosen["fuse_max_k"] in (0, 2, 4)
+    np.testing.assert_array_equal(a.labels(), before)
+    np.testing.assert_array_equal(a.get_seeds(), xy)
+    assert a.get_option(vd.OPT_PASS_TILE) == chosen["pass_tile"]
+    lab = orc.jfa(w, h, xy)
+    np.testing.assert_array_equal(before, lab)
+    for t in range(3):
+        for sim in (a, b):
+            sim.step(disp[t], d_max=D)
+        xy = orc.move(w, h, xy, disp[t])
+        lab = orc.djfa_step(w, h, xy, lab, d_max=D)
+        np.testing.assert_array_equal(a.labels(), b.labels(), err_msg=f"step {t}")
+        np.testing.assert_array_equal(a.labels(), lab, err_msg=f"step {t}")
+    torch.cuda.synchronize()
+    a.close()
+    b.close()
+
+
+@pytest.mark.parametrize("tile", [32, 128])
+def test_pass_tiles(vd, orc, tile):
+    """The 32 x 4 and 128 x 1 block tiles of the pass give the oracle's maps
+    (ragged widths: fewer quads per row than the tile)."""
+    for w, h, s in [(37, 29, 12), (300, 211, 500), (1000, 700, 70000)]:
+        xy = inputs.uniform_seeds(w, h, s, seed=w)
+        sim = _sim(vd, w, h, xy, pass_tile=tile)
+        g = np.random.default_rng(w)
+        src = g.integers(-1, s, size=(h, w), dtype=np.int32)
+        for k in [1, 2, 3, 4, 16]:
+            for nb in [M, VN]:
+                sim.set_labels(src)
+                sim.jump_pass(k, nb)
+                np.testing.assert_array_equal(sim.labels(), orc.jump_pass(w, h, xy, src, k, nb, E))
+        sim.jfa()
+        lab = orc.jfa(w, h, xy)
+        np.testing.assert_array_equal(sim.labels(), lab)
+        d = inputs.displacements(s, 2, 1, seed=w)[0]
+        sim.move(d)
+        sim.djfa_step(d_max=2)
+        np.testing.assert_array_equal(sim.labels(), orc.djfa_step(w, h, orc.move(w, h, xy, d), lab, d_max=2))
+        sim.close()
