@@ -60,6 +60,8 @@ def parse_args():
                     help="bounded CPU-oracle sample for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="skip vd_autotune (the pass launch-shape search) before the timed steps")
     ap.add_argument("--metric", choices=["euclid", "manhattan"], default="euclid",
                     help="dJFA distance: euclid (dJFAe) or manhattan (dJFAm, scored against Euclidean JFA)")
     ap.add_argument("--extra", type=int, default=0, help="extra dJFA passes after the schedule (0, 1, 2)")
@@ -314,6 +316,12 @@ def cpu_oracle_run(name, steps, seconds, seed=0, warmup=0, threads=None):
             "ms_per_step": 1e3 * t_acc / max(done, 1), "steps": done, "jfa_ms_per_frame": 1e3 * t_jfa}
 
 
+def apply_tuning(vd, sim, chosen):
+    """Puts a vd_autotune choice on another context of the same workload."""
+    for name, v in chosen.items():
+        sim.set_option(getattr(vd, "OPT_" + name.upper()), v)
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -388,6 +396,12 @@ def run_ours(args):
         sim.set_seeds(xy)
         sim.set_option(vd.OPT_USE_GRAPHS, 1)
     dj.jfa(metric=metric)  # frame 0 of the dJFA chain
+    tuned = None
+    if not args.no_autotune:
+        # the library's launch-shape search on this simulation's own steps
+        # (state restored afterwards); its choice stays in force
+        chosen, cand_ms = dj.autotune(d_max=d, max_disp=d, vn_waves=2, metric=metric, rng_seed=12345, steps=4)
+        tuned = {"chosen": chosen, "candidate_ms_per_step": [round(t, 4) for t in cand_ms]}
 
     def djfa_step(i):
         # move + stamp + passes: one vd_step call (one graph)
@@ -446,6 +460,8 @@ def run_ours(args):
     #     events around every launch (eager launches, L2 flushed between steps)
     pr = vd.VoronoiSim(w, h, s, stream=stream)
     pr.set_seeds(xy)
+    if tuned:
+        apply_tuning(vd, pr, tuned["chosen"])
     pr.jfa(metric=metric)
     for i in range(W):
         pr.step(disp_dev[i], d_max=d, vn_waves=2, extra=args.extra, metric=metric)
@@ -499,6 +515,8 @@ def run_ours(args):
         ee = vd.VoronoiSim(w, h, s, stream=stream)
         ee.set_seeds(xy)
         ee.set_option(vd.OPT_USE_GRAPHS, 1)
+        if tuned:
+            apply_tuning(vd, ee, tuned["chosen"])
         ee.jfa(metric=metric)
         pin_disp = torch.from_numpy(disp_host).pin_memory()
         pin_out = [torch.empty((h, w), dtype=torch.int32).pin_memory() for _ in range(2)]
@@ -562,6 +580,7 @@ def run_ours(args):
         "ms_per_pass": {"djfa": t_djfa_max / K / n_djfa, "jfa": t_jfa_max / K / n_jfa},
         "similarity": similarity,
         "roofline": roofline,
+        "autotune": tuned,
         "e2e": e2e,
         "cpu_baseline": cpu,
         "gpu_launches": int(launches),

@@ -423,6 +423,12 @@ int vd_batch_step_subset(vd_batch* batch, const int32_t* sims, int32_t n, int32_
                                         other blocks' wait must run out (default 0) */
 #define VD_BOPT_CLAMPED_KEYS 7       /* as VD_OPT_CLAMPED_KEYS (-1 auto, 0 never, 1 always when usable);
                                         applied at the next vd_batch_configure / vd_batch_jfa */
+#define VD_BOPT_PERSISTENT_BYTE_KEYS 8 /* persistent mode: 1 (default) = the byte-offset key on the passes
+                                        whose simulations the auto rules give it, as the per-round
+                                        launches do; 0 = the clamped key there.  Results never depend
+                                        on it */
+#define VD_BOPT_PERSISTENT_MIN_BLOCKS 9 /* persistent mode: register budget of the kernel, 4 (default, 64
+                                        registers a thread) or 5 (48) resident 256-thread blocks per SM */
 int vd_batch_set_option(vd_batch* batch, int32_t option, int64_t value);
 int vd_batch_get_option(const vd_batch* batch, int32_t option, int64_t* value);
 
@@ -437,7 +443,10 @@ int vd_batch_get_option(const vd_batch* batch, int32_t option, int64_t* value);
  * 2 or 4 rows per thread (tiles of 256 x 4, 8 or 16 pixels) [0-2]; the
  * persistent launch with 1, 2 or 4 rows per thread at the occupancy maximum
  * [3-5]; the persistent launch with 1 or 2 rows per thread capped at 3 blocks
- * per SM [6-7] and at 2 [8-9].
+ * per SM [6-7] and at 2 [8-9]; the persistent launch with 1 or 2 rows per
+ * thread on the clamped key only (VD_BOPT_PERSISTENT_BYTE_KEYS = 0) [10-11];
+ * the persistent launch with 1, 2 or 4 rows per thread compiled for 5
+ * blocks per SM (VD_BOPT_PERSISTENT_MIN_BLOCKS = 5) [12-14].
  */
 int vd_batch_autotune(vd_batch* batch, int32_t steps, int32_t max_disp, uint64_t rng_seed,
                       int32_t* best, double* ms_per_step, int32_t cap);

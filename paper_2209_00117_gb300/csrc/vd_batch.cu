@@ -49,6 +49,8 @@ struct vd_batch {
   long long timeout_ns = 2000000000LL;
   int test_skip_arrive = 0;
   int clamp = -1;  // clamped 32-bit keys: -1 auto, 0 never, 1 whenever usable
+  int persistent_byte = 1;  // persistent launch: byte-offset keys where the auto rules pick them
+  int persistent_min_blocks = 4;  // persistent launch: register budget for 4 (64 registers) or 5 (48) blocks per SM
   int64_t launches = 0;
   // cached full-batch dJFA plan + graph
   int full_plan_valid = 0;
@@ -80,9 +82,13 @@ int launch_plan(vd_batch* b, const HostPlan& p, vdb::BatchArgs& A) {
   if (b->mode == 1) {
     int rc = vd_cuda_check(cudaMemsetAsync(b->bar, 0, 2 * sizeof(unsigned int), st), "barrier reset");
     if (rc) return rc;
-    const void* fn = b->metric == VD_METRIC_MANHATTAN
-                         ? reinterpret_cast<const void*>(&vdb::k_batch_persistent<vdk::kManhattan>)
-                         : reinterpret_cast<const void*>(&vdb::k_batch_persistent<vdk::kEuclid>);
+    const bool m5 = b->persistent_min_blocks == 5;
+    const void* fn =
+        b->metric == VD_METRIC_MANHATTAN
+            ? (m5 ? reinterpret_cast<const void*>(&vdb::k_batch_persistent<vdk::kManhattan, 5>)
+                  : reinterpret_cast<const void*>(&vdb::k_batch_persistent<vdk::kManhattan, 4>))
+            : (m5 ? reinterpret_cast<const void*>(&vdb::k_batch_persistent<vdk::kEuclid, 5>)
+                  : reinterpret_cast<const void*>(&vdb::k_batch_persistent<vdk::kEuclid, 4>));
     int per_sm = 0;
     rc = vd_cuda_check(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, vdb::kThreads, 0), "occupancy");
     if (rc) return rc;
@@ -99,7 +105,7 @@ int launch_plan(vd_batch* b, const HostPlan& p, vdb::BatchArgs& A) {
 }
 
 vdb::BatchArgs base_args(const vd_batch* b) {
-  return vdb::make_args(b->rows_per_thread, b->bar, b->timeout_ns, b->test_skip_arrive);
+  return vdb::make_args(b->rows_per_thread, b->bar, b->timeout_ns, b->test_skip_arrive, b->persistent_byte);
 }
 
 void drop_graph(vd_batch* b) {
@@ -518,6 +524,14 @@ extern "C" int vd_batch_set_option(vd_batch* b, int32_t option, int64_t value) {
       b->clamp = static_cast<int>(value);
       // takes effect at the next vd_batch_configure / vd_batch_jfa
       break;
+    case VD_BOPT_PERSISTENT_BYTE_KEYS:
+      if (value != 0 && value != 1) return vd_fail(VD_EINVAL, "persistent byte keys must be 0 or 1");
+      b->persistent_byte = static_cast<int>(value);
+      break;
+    case VD_BOPT_PERSISTENT_MIN_BLOCKS:
+      if (value != 4 && value != 5) return vd_fail(VD_EINVAL, "persistent blocks per SM must be 4 or 5");
+      b->persistent_min_blocks = static_cast<int>(value);
+      break;
     default:
       return vd_fail(VD_EINVAL, "unknown batch option %d", option);
   }
@@ -536,6 +550,8 @@ extern "C" int vd_batch_get_option(const vd_batch* b, int32_t option, int64_t* v
     case VD_BOPT_BARRIER_TIMEOUT_US: *value = b->timeout_ns / 1000; break;
     case VD_BOPT_TEST_SKIP_ARRIVE: *value = b->test_skip_arrive; break;
     case VD_BOPT_CLAMPED_KEYS: *value = b->clamp; break;
+    case VD_BOPT_PERSISTENT_BYTE_KEYS: *value = b->persistent_byte; break;
+    case VD_BOPT_PERSISTENT_MIN_BLOCKS: *value = b->persistent_min_blocks; break;
     default: return vd_fail(VD_EINVAL, "unknown batch option %d", option);
   }
   return VD_OK;
@@ -599,13 +615,14 @@ extern "C" int vd_batch_autotune(vd_batch* b, int32_t steps, int32_t max_disp, u
   if (!b->configured) return vd_fail(VD_EINVAL, "vd_batch_configure has not been called");
   if (steps < 1 || steps > 1000) return vd_fail(VD_EINVAL, "steps outside [1, 1000]");
   struct Cand {
-    int mode, rpt, bps;
+    int mode, rpt, bps, pbyte, minb;
   };
   // per-round launches with tiles of 256 x 4 r pixels (r rows per thread), and
   // the persistent launch at the occupancy maximum or capped at 3 or 2 blocks
   // per SM (fewer co-resident blocks: fewer arrivals at each grid barrier)
-  const Cand cands[] = {{0, 1, 0}, {0, 2, 0}, {0, 4, 0}, {1, 1, 0}, {1, 2, 0}, {1, 4, 0},
-                        {1, 1, 3}, {1, 2, 3}, {1, 1, 2}, {1, 2, 2}};
+  const Cand cands[] = {{0, 1, 0, 1, 4}, {0, 2, 0, 1, 4}, {0, 4, 0, 1, 4}, {1, 1, 0, 1, 4}, {1, 2, 0, 1, 4},
+                        {1, 4, 0, 1, 4}, {1, 1, 3, 1, 4}, {1, 2, 3, 1, 4}, {1, 1, 2, 1, 4}, {1, 2, 2, 1, 4},
+                        {1, 1, 0, 0, 4}, {1, 2, 0, 0, 4}, {1, 1, 0, 1, 5}, {1, 2, 0, 1, 5}, {1, 4, 0, 1, 5}};
   const int nc = static_cast<int>(sizeof(cands) / sizeof(cands[0]));
   int rc = vd_batch_synchronize(b);
   if (rc) return rc;
@@ -619,7 +636,8 @@ extern "C" int vd_batch_autotune(vd_batch* b, int32_t steps, int32_t max_disp, u
     sn.release();
     return vd_cuda_check(e, "autotune snapshot");
   }
-  const int mode0 = b->mode, rpt0 = b->rows_per_thread, bps0 = b->blocks_per_sm;
+  const int mode0 = b->mode, rpt0 = b->rows_per_thread, bps0 = b->blocks_per_sm, pb0 = b->persistent_byte;
+  const int mb0 = b->persistent_min_blocks;
   rc = snapshot_copy(b, sn, true);
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (!rc) rc = vd_cuda_check(cudaEventCreate(&e0), "event");
@@ -630,6 +648,8 @@ extern "C" int vd_batch_autotune(vd_batch* b, int32_t steps, int32_t max_disp, u
     b->mode = cands[c].mode;
     b->rows_per_thread = cands[c].rpt;
     b->blocks_per_sm = cands[c].bps;
+    b->persistent_byte = cands[c].pbyte;
+    b->persistent_min_blocks = cands[c].minb;
     drop_graph(b);
     rc = snapshot_copy(b, sn, false);
     if (!rc) rc = vd_batch_step(b, nullptr, 0, max_disp, rng_seed);  // warm-up (plan, graph)
@@ -658,10 +678,14 @@ extern "C" int vd_batch_autotune(vd_batch* b, int32_t steps, int32_t max_disp, u
     b->mode = cands[best_i].mode;
     b->rows_per_thread = cands[best_i].rpt;
     b->blocks_per_sm = cands[best_i].bps;
+    b->persistent_byte = cands[best_i].pbyte;
+    b->persistent_min_blocks = cands[best_i].minb;
   } else {
     b->mode = mode0;
     b->rows_per_thread = rpt0;
     b->blocks_per_sm = bps0;
+    b->persistent_byte = pb0;
+    b->persistent_min_blocks = mb0;
   }
   drop_graph(b);
   if (best) *best = best_i;

@@ -72,6 +72,7 @@ struct BatchArgs {
   Barrier* bar;
   long long timeout_ns;
   int test_skip_arrive;
+  int coh_byte;  // persistent launch: the byte-offset key on the passes that take it (else clamped)
 };
 
 __device__ __forceinline__ unsigned long long global_ns() {
@@ -248,9 +249,7 @@ __device__ __forceinline__ void round_tile(const BatchArgs& A, int r, int t) {
   const int rows = 4 * A.rows_per_thread;
   const bool dedup = sd->dedup[A.sched] != 0;
   const bool mcap = sd->mul > (1u << 15);
-  // the persistent kernel (COH) keeps the clamped key: the byte form's code
-  // there pushed its register spills up and made it 1.2x slower
-  const bool byte = !COH && METRIC == vdk::kEuclid && ((sd->bytemask[A.sched] >> r) & 1u);
+  const bool byte = (COH ? A.coh_byte : true) && METRIC == vdk::kEuclid && ((sd->bytemask[A.sched] >> r) & 1u);
   for (int i = 0; i < A.rows_per_thread; ++i) {
     const int y = ty * rows + static_cast<int>(threadIdx.x / kQuadsX) + 4 * i;
     if (x0 >= a.pitch || y >= a.h) continue;
@@ -291,8 +290,10 @@ static __global__ void k_batch_finish(BatchArgs A) {
 
 // ---- the persistent kernel -------------------------------------------------
 
-template <int METRIC>
-__global__ void __launch_bounds__(kThreads, 4) k_batch_persistent(BatchArgs A) {
+// MINB: resident blocks per SM the register budget is cut for (4: 64
+// registers a thread; 5: 48, as the per-round kernel).
+template <int METRIC, int MINB>
+__global__ void __launch_bounds__(kThreads, MINB) k_batch_persistent(BatchArgs A) {
   if (*reinterpret_cast<volatile int*>(&A.bar->err) != 0) return;
   if (A.move || A.mark) {
     for (int sb = blockIdx.x; sb < A.n_sblk; sb += gridDim.x) move_mark_block(A, sb);
@@ -302,7 +303,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_batch_persistent(BatchArgs A) {
   if (!grid_sync(A, false)) return;
   for (int r = 0; r < A.rounds; ++r) {
     const int nt = A.round_tiles[r];
-    // maps are rewritten between barriers of this launch: read them at L2
+    // maps are rewritten between barriers of this launch: coherent loads
     for (int t = blockIdx.x; t < nt; t += gridDim.x) round_tile<METRIC, true>(A, r, t);
     if (!grid_sync(A, false)) return;
   }
@@ -475,9 +476,11 @@ inline int launch_rounds(const HostPlan& p, const BatchArgs& A, int metric, cuda
   return vd_cuda_check(cudaGetLastError(), "batch launch");
 }
 
-inline BatchArgs make_args(int rows_per_thread, Barrier* bar, long long timeout_ns, int test_skip_arrive) {
+inline BatchArgs make_args(int rows_per_thread, Barrier* bar, long long timeout_ns, int test_skip_arrive,
+                           int coh_byte) {
   BatchArgs A;
   std::memset(&A, 0, sizeof(A));
+  A.coh_byte = coh_byte;
   A.rows_per_thread = rows_per_thread;
   A.bar = bar;
   A.timeout_ns = timeout_ns;

@@ -67,7 +67,7 @@ __device__ __forceinline__ long long pack_key(int key, int c) {
 template <int METRIC, bool COH = false>
 __device__ __forceinline__ long long cand(int c, const int2* __restrict__ table, int m2x, int m2y, int x,
                                           int y) {
-  const int2 e = COH ? __ldcg(&table[c]) : __ldg(&table[c]);
+  const int2 e = COH ? __ldca(&table[c]) : __ldg(&table[c]);
   return pack_key(table_key<METRIC>(e, c, m2x, m2y, x, y), c);
 }
 
@@ -92,24 +92,30 @@ __device__ __forceinline__ void consider(int c, const int2* __restrict__ seeds, 
 }
 
 // Label-map and seed-table loads.  Separate launches use the read-only
-// (non-coherent L1) path; a persistent launch that rewrites maps and tables
-// between grid barriers must read them at L2 (ld.global.cg): the read-only
-// path is only defined for data that no thread writes during the launch.
+// (non-coherent) path, ld.global.nc.  A persistent launch rewrites maps and
+// tables between its grid barriers, and the read-only path is only defined
+// for data that no thread writes during the launch, so it uses ordinary
+// loads (ld.global.ca, cached in L1) instead: its grid barrier is a release
+// (every thread's stores, the block barrier, then a gpu-scope fence and the
+// atomic arrival) matched by an acquire (the spin read of the generation
+// word, a gpu-scope fence, then the block barrier), so under the PTX memory
+// model every load after the barrier observes every store made before it --
+// an L1 line cached in an earlier round included.
 template <bool COHERENT>
 __device__ __forceinline__ int4 map4(const int32_t* p) {
-  if (COHERENT) return __ldcg(reinterpret_cast<const int4*>(p));
+  if (COHERENT) return __ldca(reinterpret_cast<const int4*>(p));
   return __ldg(reinterpret_cast<const int4*>(p));
 }
 
 template <bool COHERENT>
 __device__ __forceinline__ int map1(const int32_t* p) {
-  if (COHERENT) return __ldcg(p);
+  if (COHERENT) return __ldca(p);
   return __ldg(p);
 }
 
 template <bool COHERENT>
 __device__ __forceinline__ int2 map2(const int32_t* p) {
-  if (COHERENT) return __ldcg(reinterpret_cast<const int2*>(p));
+  if (COHERENT) return __ldca(reinterpret_cast<const int2*>(p));
   return __ldg(reinterpret_cast<const int2*>(p));
 }
 
@@ -180,7 +186,7 @@ struct Quad {
   __device__ __forceinline__ Quad(const PassArgs& a, int x0_, int y_)
       : m2x(-2 * x0_), m2y(-2 * y_), x0(x0_), y(y_), table(a.table) {}
   __device__ __forceinline__ int2 pos(int c) const {
-    const int2 e = COH ? __ldcg(&table[c]) : __ldg(&table[c]);
+    const int2 e = COH ? __ldca(&table[c]) : __ldg(&table[c]);
     const int sx = e.x & 0xFFFF;
     const int sy = static_cast<int>(static_cast<unsigned int>(e.x) >> 16);
     // the sentinel (c = -1) reads {0, INT32_MAX}: its Euclidean key is
@@ -219,7 +225,7 @@ struct Quad32 {
   __device__ __forceinline__ Quad32(const PassArgs& a, int x0_, int y_)
       : x0(x0_), y(y_), cap(a.cap), mul(a.mul), ptable(a.ptable) {}
   __device__ __forceinline__ int2 pos(int c) const {
-    const uint32_t e = COH ? __ldcg(&ptable[c]) : __ldg(&ptable[c]);
+    const uint32_t e = COH ? __ldca(&ptable[c]) : __ldg(&ptable[c]);
     const uint32_t dy = static_cast<uint32_t>(static_cast<int>(e >> 16) - y);
     return make_int2(static_cast<int>(e & 0xFFFFu), static_cast<int>(dy * dy));
   }
@@ -256,7 +262,7 @@ struct Quad32M {
   __device__ __forceinline__ Quad32M(const PassArgs& a, int x0_, int y_)
       : x0(x0_), y(y_), cap(a.cap), mul(a.mul), ptable(a.ptable) {}
   __device__ __forceinline__ int2 pos(int c) const {
-    const uint32_t e = COH ? __ldcg(&ptable[c]) : __ldg(&ptable[c]);
+    const uint32_t e = COH ? __ldca(&ptable[c]) : __ldg(&ptable[c]);
     const int ady = c < 0 ? kManhattanFarY : abs(static_cast<int>(e >> 16) - y);
     return make_int2(static_cast<int>(e & 0xFFFFu), ady);
   }
@@ -308,7 +314,7 @@ struct Quad8 {
         mul(a.bmul),  // 2^16
         ptable(a.ptable) {}
   __device__ __forceinline__ int2 pos(int c) const {
-    const uint32_t e = COH ? __ldcg(&ptable[c]) : __ldg(&ptable[c]);
+    const uint32_t e = COH ? __ldca(&ptable[c]) : __ldg(&ptable[c]);
     return make_int2(static_cast<int>(e), 0);
   }
   __device__ __forceinline__ uint32_t key(int i, int2 p, int c) const {
@@ -573,7 +579,7 @@ __device__ __forceinline__ void pass_quad_byte(const PassArgs& a, int x0, int y)
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
     const uint32_t j = (q.b[i] + 1u) & mask;
-    const uint32_t e = COH ? __ldcg(&arena[j]) : __ldg(&arena[j]);
+    const uint32_t e = COH ? __ldca(&arena[j]) : __ldg(&arena[j]);
     // (dx + h) | (dy + h) << 16 has no bit at or above 2h in either half
     // exactly when dx, dy lie in [-h, h)
     bad |= (e + kw - static_cast<uint32_t>(i)) & wmask;

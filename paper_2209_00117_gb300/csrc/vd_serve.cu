@@ -131,7 +131,7 @@ int admit(vd_server* s) {
     s->pending.swap(keep);
     if (act.empty()) continue;
     vdb::HostPlan p = vdb::make_plan(s->sims, act, 0, s->rows_per_thread);
-    vdb::BatchArgs A = vdb::make_args(s->rows_per_thread, s->bar, 0, 0);
+    vdb::BatchArgs A = vdb::make_args(s->rows_per_thread, s->bar, 0, 0, 1);
     A.sched = 0;
     A.mark = 1;
     A.move = 1;
@@ -250,7 +250,7 @@ extern "C" int32_t vd_server_add_sim(vd_server* s, int32_t w, int32_t h, int32_t
   std::vector<vdb::SimDesc> one(s->sims);
   one[slot] = d;
   vdb::HostPlan p = vdb::make_plan(one, std::vector<int>{slot}, 1, s->rows_per_thread);
-  vdb::BatchArgs A = vdb::make_args(s->rows_per_thread, s->bar, 0, 0);
+  vdb::BatchArgs A = vdb::make_args(s->rows_per_thread, s->bar, 0, 0, 1);
   A.sched = 1;
   if (!rc) rc = vdb::plan_upload(s->admin_slot, p, s->d_sims, st, &A);
   if (!rc) rc = vdb::launch_rounds(p, A, s->metric, st, &s->launches);

@@ -368,6 +368,8 @@ BOPT_USE_GRAPHS = 4
 BOPT_BARRIER_TIMEOUT_US = 5
 BOPT_TEST_SKIP_ARRIVE = 6
 BOPT_CLAMPED_KEYS = 7
+BOPT_PERSISTENT_BYTE_KEYS = 8
+BOPT_PERSISTENT_MIN_BLOCKS = 9
 
 
 class VoronoiBatch:
@@ -466,9 +468,9 @@ class VoronoiBatch:
     def autotune(self, steps: int, max_disp: int, rng_seed: int = 0):
         """(best candidate index, ms per step of every candidate)."""
         best = ctypes.c_int32(-1)
-        ms = np.zeros(16, np.float64)
+        ms = np.zeros(32, np.float64)
         n = N.check(self._lib.vd_batch_autotune(self._h, int(steps), int(max_disp), int(rng_seed) & (2**64 - 1),
-                                                ctypes.byref(best), ms.ctypes.data, 16))
+                                                ctypes.byref(best), ms.ctypes.data, 32))
         return best.value, ms[:n].tolist()
 
     def work(self):

@@ -44,9 +44,10 @@ def _alone_rng(vd, shape, xy, sim_index, steps, D, rng_seed, metric=0):
     return out
 
 
-@pytest.mark.parametrize("mode,graphs,rpt,bps", [(0, 0, 1, 0), (0, 1, 1, 0), (0, 1, 2, 0), (1, 0, 1, 0), (1, 0, 4, 0),
-                                                (1, 0, 1, 2), (1, 0, 2, 3)])
-def test_batch_equals_alone_rng(vd, mode, graphs, rpt, bps):
+@pytest.mark.parametrize("mode,graphs,rpt,bps,pbyte,minb", [(0, 0, 1, 0, 1, 4), (0, 1, 1, 0, 1, 4), (0, 1, 2, 0, 1, 4),
+                                                             (1, 0, 1, 0, 1, 4), (1, 0, 4, 0, 1, 4), (1, 0, 1, 2, 1, 4),
+                                                             (1, 0, 2, 3, 1, 4), (1, 0, 1, 0, 0, 4), (1, 0, 2, 0, 1, 5)])
+def test_batch_equals_alone_rng(vd, mode, graphs, rpt, bps, pbyte, minb):
     """Every launch shape the batch autotuner tries (per-round or persistent,
     rows per thread, persistent blocks per SM) gives each simulation exactly
     its alone run."""
@@ -60,6 +61,8 @@ def test_batch_equals_alone_rng(vd, mode, graphs, rpt, bps):
     b.set_option(vd.BOPT_USE_GRAPHS, graphs)
     b.set_option(vd.BOPT_ROWS_PER_THREAD, rpt)
     b.set_option(vd.BOPT_BLOCKS_PER_SM, bps)
+    b.set_option(vd.BOPT_PERSISTENT_BYTE_KEYS, pbyte)
+    b.set_option(vd.BOPT_PERSISTENT_MIN_BLOCKS, minb)
     b.set_seeds(np.concatenate(xys))
     b.jfa()
     b.configure(d_max=D)
