@@ -376,10 +376,12 @@ __device__ __forceinline__ void fold4(Q& q, const int4& L) {
 // Labels at columns x0 + dx .. x0 + dx + 3 of one row for |dx| = k, a multiple
 // of 4 (one aligned 16-byte load); columns outside [0, pitch) read as -1 and
 // the row padding [w, pitch) holds -1 already.
-template <bool COH>
+// IN: the quad's block lies inside the map with all its neighbours (no test).
+template <bool COH, bool IN = false>
 __device__ __forceinline__ int4 load_side(const int32_t* __restrict__ row, int x0, int dx, int pitch,
                                           const int4& fill) {
   const int xs = x0 + dx;
+  if (IN) return map4<COH>(row + xs);
   return (xs >= 0 && xs < pitch) ? map4<COH>(row + xs) : fill;
 }
 
@@ -397,7 +399,7 @@ __device__ __forceinline__ int4 load_scalar4(const int32_t* __restrict__ row, in
 // For k = 1 and k = 2 the side labels of neighbouring pixels overlap the
 // row's own vector: only the 2 (k = 1) or 4 (k = 2) labels outside it are
 // gathered, and the 8 side candidates reuse `mp` for the rest.
-template <int KSEL, bool COH, class Q>
+template <int KSEL, bool COH, bool IN = false, class Q>
 __device__ __forceinline__ void fold_sides(Q& q, const int32_t* __restrict__ row, const int4& mid,
                                            const int2 (&mp)[4], const PassArgs& a) {
   const int x0 = q.x0;
@@ -405,15 +407,15 @@ __device__ __forceinline__ void fold_sides(Q& q, const int32_t* __restrict__ row
   // label at the pixel, which that pixel scores anyway
   const int4 fill = Q::kFillOwn ? mid : make_int4(-1, -1, -1, -1);
   if (KSEL == 0) {
-    const int4 L = load_side<COH>(row, x0, -a.k, a.pitch, fill);
-    const int4 R = load_side<COH>(row, x0, a.k, a.pitch, fill);
+    const int4 L = load_side<COH, IN>(row, x0, -a.k, a.pitch, fill);
+    const int4 R = load_side<COH, IN>(row, x0, a.k, a.pitch, fill);
     fold4(q, L);
     group_fence();
     fold4(q, R);
   } else if (KSEL == 1) {
     // left of pixel i: column x0 + i - 1; right: x0 + i + 1
-    const int l = (x0 >= 4) ? map1<COH>(row + x0 - 1) : fill.x;
-    const int r = (x0 + 4 < a.pitch) ? map1<COH>(row + x0 + 4) : fill.w;
+    const int l = (IN || x0 >= 4) ? map1<COH>(row + x0 - 1) : fill.x;
+    const int r = (IN || x0 + 4 < a.pitch) ? map1<COH>(row + x0 + 4) : fill.w;
     const int2 pl = q.pos(l);
     const int2 pr = q.pos(r);
     q.fold(0, pl, l);
@@ -426,8 +428,8 @@ __device__ __forceinline__ void fold_sides(Q& q, const int32_t* __restrict__ row
     q.fold(3, pr, r);
   } else if (KSEL == 2) {
     // left of pixel i: column x0 + i - 2; right: x0 + i + 2
-    const int2 l = (x0 >= 4) ? map2<COH>(row + x0 - 2) : make_int2(fill.x, fill.y);
-    const int2 r = (x0 + 4 < a.pitch) ? map2<COH>(row + x0 + 4) : make_int2(fill.z, fill.w);
+    const int2 l = (IN || x0 >= 4) ? map2<COH>(row + x0 - 2) : make_int2(fill.x, fill.y);
+    const int2 r = (IN || x0 + 4 < a.pitch) ? map2<COH>(row + x0 + 4) : make_int2(fill.z, fill.w);
     const int2 pl0 = q.pos(l.x);
     const int2 pl1 = q.pos(l.y);
     const int2 pr0 = q.pos(r.x);
@@ -455,14 +457,14 @@ __device__ __forceinline__ void fold_sides(Q& q, const int32_t* __restrict__ row
 // folds in the neighbour offsets one source row at a time (16-byte label
 // loads, seed gathers and minimums).  Candidate order does not matter: every
 // key form is a total order.
-template <int NB, int KSEL, bool COH, class Q>
+template <int NB, int KSEL, bool COH, bool IN = false, class Q>
 __device__ __forceinline__ void fold_all(Q& q, const PassArgs& a, int x0, int y) {
   const int64_t pitch = a.pitch;
   const int32_t* crow = a.src + y * pitch;
   const int4 own = map4<COH>(crow + x0);
   // the first up-row vector is in flight while the own labels are scored
-  const bool up_ok = y - a.k >= 0;
-  const bool dn_ok = y + a.k < a.h;
+  const bool up_ok = IN || y - a.k >= 0;
+  const bool dn_ok = IN || y + a.k < a.h;
   const int32_t* urow = a.src + (y - a.k) * pitch;
   const int32_t* drow = a.src + (y + a.k) * pitch;
   const int4 neg = make_int4(-1, -1, -1, -1);
@@ -472,85 +474,87 @@ __device__ __forceinline__ void fold_all(Q& q, const PassArgs& a, int x0, int y)
   init4(q, own, p);
   group_fence();
   // centre row: (-k, 0), (+k, 0)
-  fold_sides<KSEL, COH>(q, crow, own, p, a);
+  fold_sides<KSEL, COH, IN>(q, crow, own, p, a);
   // up row: (0, -k) and, for Moore, (-k, -k), (+k, -k); then the down row
   if (up_ok) {
     const int4 dm = dn_ok ? map4<COH>(drow + x0) : neg;
     gather4(q, um, p);
     fold4(q, um, p);
     group_fence();
-    if (NB == kMoore) fold_sides<KSEL, COH>(q, urow, um, p, a);
+    if (NB == kMoore) fold_sides<KSEL, COH, IN>(q, urow, um, p, a);
     if (dn_ok) {
       gather4(q, dm, p);
       fold4(q, dm, p);
       group_fence();
-      if (NB == kMoore) fold_sides<KSEL, COH>(q, drow, dm, p, a);
+      if (NB == kMoore) fold_sides<KSEL, COH, IN>(q, drow, dm, p, a);
     }
   } else if (dn_ok) {
     const int4 dm = map4<COH>(drow + x0);
     gather4(q, dm, p);
     fold4(q, dm, p);
     group_fence();
-    if (NB == kMoore) fold_sides<KSEL, COH>(q, drow, dm, p, a);
+    if (NB == kMoore) fold_sides<KSEL, COH, IN>(q, drow, dm, p, a);
   }
 }
 
+template <bool IN = false>
 __device__ __forceinline__ void store_quad(const PassArgs& a, int x0, int y, int l0, int l1, int l2, int l3) {
   int4 out;
-  out.x = (x0 < a.w) ? l0 : -1;
-  out.y = (x0 + 1 < a.w) ? l1 : -1;
-  out.z = (x0 + 2 < a.w) ? l2 : -1;
-  out.w = (x0 + 3 < a.w) ? l3 : -1;
+  out.x = (IN || x0 < a.w) ? l0 : -1;
+  out.y = (IN || x0 + 1 < a.w) ? l1 : -1;
+  out.z = (IN || x0 + 2 < a.w) ? l2 : -1;
+  out.w = (IN || x0 + 3 < a.w) ? l3 : -1;
   *reinterpret_cast<int4*>(a.dst + static_cast<int64_t>(y) * a.pitch + x0) = out;
 }
 
 __device__ __forceinline__ int low_label(long long b) { return static_cast<int>(static_cast<unsigned int>(b)); }
 
 // Exact form (any metric).
-template <int NB, int METRIC, int KSEL, bool COH = false, bool DEDUP = false>
+template <int NB, int METRIC, int KSEL, bool COH = false, bool DEDUP = false, bool IN = false>
 __device__ __forceinline__ void pass_quad(const PassArgs& a, int x0, int y) {
   Quad<METRIC, COH, DEDUP> q(a, x0, y);
-  fold_all<NB, KSEL, COH>(q, a, x0, y);
-  store_quad(a, x0, y, low_label(q.b[0]), low_label(q.b[1]), low_label(q.b[2]), low_label(q.b[3]));
+  fold_all<NB, KSEL, COH, IN>(q, a, x0, y);
+  store_quad<IN>(a, x0, y, low_label(q.b[0]), low_label(q.b[1]), low_label(q.b[2]), low_label(q.b[3]));
 }
 
 // 32-bit forms.  Euclidean, and Manhattan with MCAP (more than 2^15 labels):
 // clamped, falling back to the exact form for a quad whose best distance
 // reaches the cap (or that saw only empty labels).  Manhattan without MCAP:
 // exact as is (lb <= 15); an all-empty pixel stays -1.
-template <int NB, int KSEL, bool COH = false, int METRIC = kEuclid, bool DEDUP = false, bool MCAP = false>
+template <int NB, int KSEL, bool COH = false, int METRIC = kEuclid, bool DEDUP = false, bool MCAP = false,
+          bool IN = false>
 __device__ __forceinline__ void pass_quad_clamped(const PassArgs& a, int x0, int y) {
   const uint32_t mask = a.mul - 1u;
   if (METRIC == kManhattan && MCAP) {
     Quad32M<COH, DEDUP, true> q(a, x0, y);
-    fold_all<NB, KSEL, COH>(q, a, x0, y);
+    fold_all<NB, KSEL, COH, IN>(q, a, x0, y);
     const uint32_t lim = (a.cap - 1u) * a.mul;
     if (max(max(q.b[0], q.b[1]), max(q.b[2], q.b[3])) >= lim) {
-      pass_quad<NB, kManhattan, KSEL, COH, DEDUP>(a, x0, y);
+      pass_quad<NB, kManhattan, KSEL, COH, DEDUP, IN>(a, x0, y);
       return;
     }
-    store_quad(a, x0, y, static_cast<int>(q.b[0] & mask), static_cast<int>(q.b[1] & mask),
+    store_quad<IN>(a, x0, y, static_cast<int>(q.b[0] & mask), static_cast<int>(q.b[1] & mask),
                static_cast<int>(q.b[2] & mask), static_cast<int>(q.b[3] & mask));
     return;
   }
   if (METRIC == kManhattan) {
     Quad32M<COH, DEDUP> q(a, x0, y);
-    fold_all<NB, KSEL, COH>(q, a, x0, y);
+    fold_all<NB, KSEL, COH, IN>(q, a, x0, y);
     const uint32_t lim = (kManhattanMax + 1u) * a.mul;
-    store_quad(a, x0, y, q.b[0] >= lim ? -1 : static_cast<int>(q.b[0] & mask),
+    store_quad<IN>(a, x0, y, q.b[0] >= lim ? -1 : static_cast<int>(q.b[0] & mask),
                q.b[1] >= lim ? -1 : static_cast<int>(q.b[1] & mask),
                q.b[2] >= lim ? -1 : static_cast<int>(q.b[2] & mask),
                q.b[3] >= lim ? -1 : static_cast<int>(q.b[3] & mask));
     return;
   }
   Quad32<COH, DEDUP> q(a, x0, y);
-  fold_all<NB, KSEL, COH>(q, a, x0, y);
+  fold_all<NB, KSEL, COH, IN>(q, a, x0, y);
   const uint32_t lim = (a.cap - 1u) * a.mul;
   if (max(max(q.b[0], q.b[1]), max(q.b[2], q.b[3])) >= lim) {
-    pass_quad<NB, kEuclid, KSEL, COH, DEDUP>(a, x0, y);
+    pass_quad<NB, kEuclid, KSEL, COH, DEDUP, IN>(a, x0, y);
     return;
   }
-  store_quad(a, x0, y, static_cast<int>(q.b[0] & mask), static_cast<int>(q.b[1] & mask),
+  store_quad<IN>(a, x0, y, static_cast<int>(q.b[0] & mask), static_cast<int>(q.b[1] & mask),
              static_cast<int>(q.b[2] & mask), static_cast<int>(q.b[3] & mask));
 }
 
@@ -563,10 +567,10 @@ __device__ __noinline__ void byte_fallback(const PassArgs a, int x0, int y) {
 
 // Byte-offset form (Euclidean): the fold, then the winner check described at
 // Quad8; a quad that fails it is recomputed with the clamped form.
-template <int NB, int KSEL, bool COH = false, bool DEDUP = false, bool WIDE = false>
+template <int NB, int KSEL, bool COH = false, bool DEDUP = false, bool WIDE = false, bool IN = false>
 __device__ __forceinline__ void pass_quad_byte(const PassArgs& a, int x0, int y) {
   Quad8<COH, DEDUP, !WIDE && KSEL != 0> q(a, x0, y);
-  fold_all<NB, KSEL, COH>(q, a, x0, y);
+  fold_all<NB, KSEL, COH, IN>(q, a, x0, y);
   // packed positions with the far position first: the label field plus one,
   // masked, indexes it (all ones, an empty label, wraps to the far position)
   const uint32_t* __restrict__ arena = a.ptable - 1;
@@ -589,8 +593,8 @@ __device__ __forceinline__ void pass_quad_byte(const PassArgs& a, int x0, int y)
     byte_fallback<NB, KSEL, COH, DEDUP>(a, x0, y);
     return;
   }
-  store_quad(a, x0, y, static_cast<int>(q.b[0] & mask), static_cast<int>(q.b[1] & mask),
-             static_cast<int>(q.b[2] & mask), static_cast<int>(q.b[3] & mask));
+  store_quad<IN>(a, x0, y, static_cast<int>(q.b[0] & mask), static_cast<int>(q.b[1] & mask),
+                 static_cast<int>(q.b[2] & mask), static_cast<int>(q.b[3] & mask));
 }
 
 // Pass launch shape: 128-thread blocks (64 quads x 2 rows on wide maps), 10
@@ -620,8 +624,22 @@ __global__ void __launch_bounds__(kPassThreads, KEY >= 3 ? VD_BYTE_MIN_BLOCKS : 
   const int x0 = 4 * static_cast<int>(blockIdx.x * blockDim.x + threadIdx.x);
   int rb = blockIdx.y;
   if (a.band_m > 1) rb = (blockIdx.y % a.band_t) * a.band_m + blockIdx.y / a.band_t;
-  const int y = a.y0 + rb * static_cast<int>(blockDim.y) + static_cast<int>(threadIdx.y);
+  const int yb = a.y0 + rb * static_cast<int>(blockDim.y);
+  const int y = yb + static_cast<int>(threadIdx.y);
   if (x0 >= a.pitch || y >= a.y_end) return;
+  // a block whose pixels lie in the map, away from its edges by k in both
+  // directions, reads every neighbour inside the map: no range tests (the
+  // test is uniform across the block, so the two paths never diverge a warp)
+  const int xb = 4 * static_cast<int>(blockIdx.x * blockDim.x);
+  const bool in = KSEL <= 2 && xb - a.k >= 0 && xb + 4 * static_cast<int>(blockDim.x) + a.k <= a.w &&
+                  yb - a.k >= 0 && yb + static_cast<int>(blockDim.y) + a.k <= a.h &&
+                  yb + static_cast<int>(blockDim.y) <= a.y_end;
+  if (in) {
+    if (KEY == 3 || KEY == 4) pass_quad_byte<NB, KSEL, false, DEDUP, KEY == 4, true>(a, x0, y);
+    else if (KEY != 0) pass_quad_clamped<NB, KSEL, false, METRIC, DEDUP, KEY == 2, true>(a, x0, y);
+    else pass_quad<NB, METRIC, KSEL, false, DEDUP, true>(a, x0, y);
+    return;
+  }
   if (KEY == 3 || KEY == 4) pass_quad_byte<NB, KSEL, false, DEDUP, KEY == 4>(a, x0, y);
   else if (KEY != 0) pass_quad_clamped<NB, KSEL, false, METRIC, DEDUP, KEY == 2>(a, x0, y);
   else pass_quad<NB, METRIC, KSEL, false, DEDUP>(a, x0, y);
