@@ -586,6 +586,15 @@ int vd_server_set_max_batch(vd_server* server, int32_t max_batch);
                                     never depend on it */
 #define VD_OPT_PASS_TILE 16      /* block tile of the jump pass: 128 threads as 64 quads (256 pixels) x 2
                                     rows (default), 32 x 4 or 128 x 1.  Results never depend on it */
+#define VD_OPT_SMEM_TILE_MAX_K 17 /* byte-key passes with k = 1, 2 or a multiple of 4 up to this value
+                                    (0 = never (default), 1, 2, 4, 8, 16) run over a shared-memory tile:
+                                    each block of 256 x 16 pixels stages its tile and a k-pixel halo
+                                    as (label, seed position) pairs, one table read per staged pixel,
+                                    then reads every candidate from shared memory.  It measured
+                                    slower than the plain pass with large seed tables (the tile
+                                    takes most of L1) and about even with small ones, so it is
+                                    opt-in.  Results never depend on it */
+#define VD_OPT_SMEM_TILE_ROWS 18 /* rows of that tile: 16 (default, 1024-thread blocks) or 8 (512) */
 int vd_set_option(vd_ctx* ctx, int32_t option, int64_t value);
 
 /*
@@ -601,9 +610,11 @@ int vd_set_option(vd_ctx* ctx, int32_t option, int64_t value);
  * gather de-duplication (VD_OPT_DEDUP_GATHERS -1, 0, 1), the sparse form
  * (VD_OPT_SPARSE_PASS -1, 0, 1), the register-blocked form
  * (VD_OPT_BLOCKED_PASS -1, 1) and, when on, its blocks per SM
- * (VD_OPT_BLOCKED_MIN_BLOCKS 8, 6), and the shared-memory fusion depth of
- * small steps (VD_OPT_FUSE_MAX_K 0, 2, 4).  The fastest setting stays in
- * force.  chosen (may be NULL) receives 6 values in that order; ms_per_step
+ * (VD_OPT_BLOCKED_MIN_BLOCKS 8, 6), the shared-memory fusion depth of
+ * small steps (VD_OPT_FUSE_MAX_K 0, 2, 4), the shared-memory tiled form
+ * (VD_OPT_SMEM_TILE_MAX_K 0, 2, 8) and, when on, its rows
+ * (VD_OPT_SMEM_TILE_ROWS 16, 8).  The fastest setting stays in force.
+ * chosen (may be NULL) receives 8 values in that order; ms_per_step
  * (at least cap entries, may be NULL with cap = 0) the time of each candidate
  * measured, in order.  Allocates and frees one map-sized snapshot; synchronises
  * the stream.  Returns the number of candidates measured, or a VD_E* code

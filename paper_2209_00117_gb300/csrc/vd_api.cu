@@ -253,7 +253,7 @@ bool use_byte_key(int byte_option, int32_t metric, int32_t w, int32_t h, int32_t
 int launch_pass(const MapView& m, const int32_t* src, int32_t* dst, int32_t k, int32_t nb,
                 int32_t metric, int64_t band_min_k, bool clamp, cudaStream_t st, bool pdl, bool dedup,
                 bool byte_key, int blocked, int key_pack, int blk_min_blocks, bool sparse, int32_t y0,
-                int32_t y1, int pass_bx) {
+                int32_t y1, int pass_bx, int tile_max_k, int tile_rows) {
   if (y1 < 0) y1 = m.h;
   const bool rows_only = y0 != 0 || y1 != m.h;
   vdk::PassArgs a;
@@ -311,6 +311,14 @@ int launch_pass(const MapView& m, const int32_t* src, int32_t* dst, int32_t k, i
   // a pass over a row range (one band of a split map) always takes the plain kernel
   if (!rows_only && sparse && ksel <= 2)
     return launch_pass_sparse(a, grid, block, nb, metric, key, ksel, dedup, st, pdl);
+  // the shared-memory tiled form: opt-in (tile_max_k > 0).  It stages one
+  // table read per tile pixel instead of one per candidate, but its tile takes
+  // most of the SM's L1, so with large tables (2^18 seeds: 1 MB) the staging
+  // reads go to L2 behind a block barrier: on the GB300, 8192^2 with 2^18
+  // seeds, k = 2 234 -> 333 us and k = 8 274 -> 435 us; with 2^14 seeds
+  // (64 KB table) k <= 2 about even
+  if (!rows_only && tile_max_k > 0 && tile_applies(k, key, tile_max_k))
+    return launch_pass_tile(a, nb, key, tile_rows, st, pdl);
   // the register-blocked form: opt-in (blocked == 1).  It loads and gathers
   // each vector once for up to four quads, but needs 64 registers a thread
   // (half the resident warps) and measured slower than the plain pass on the
@@ -443,7 +451,8 @@ int run_passes(const MapView& m, int32_t* const buf[2], int* cur, const int32_t*
                        use_dedup(t.dedup, m.w, m.h, m.n, djfa_frame),
                        use_byte_key(t.byte_key, metric, m.w, m.h, m.n, ks[l.first], djfa_frame), t.blocked,
                        t.key_pack, t.blk_min_blocks,
-                       use_sparse(t.sparse, m.w, m.h, m.n, ks[l.first]), 0, -1, t.pass_bx);
+                       use_sparse(t.sparse, m.w, m.h, m.n, ks[l.first]), 0, -1, t.pass_bx, t.tile_max_k,
+                       t.tile_rows);
     } else {
       rc = launch_fused(m, src, dst, ks + l.first, nbs + l.first, l.n, metric, t.tile_x, t.tile_y, st);
     }
@@ -1283,7 +1292,8 @@ extern "C" int vd_pass(vd_ctx* c, int32_t k, int32_t nb, int32_t metric) {
                                   c->stream, false, vdi::use_dedup(c->tune.dedup, c->w, c->h, c->n, false),
                                   vdi::use_byte_key(c->tune.byte_key, metric, c->w, c->h, c->n, k, false),
                                   c->tune.blocked, c->tune.key_pack, c->tune.blk_min_blocks,
-                                  vdi::use_sparse(c->tune.sparse, c->w, c->h, c->n, k), 0, -1, c->tune.pass_bx);
+                                  vdi::use_sparse(c->tune.sparse, c->w, c->h, c->n, k), 0, -1, c->tune.pass_bx,
+                                  c->tune.tile_max_k, c->tune.tile_rows);
   if (rc) return rc;
   ++c->launches;
   c->cur ^= 1;
@@ -1393,10 +1403,13 @@ extern "C" int vd_autotune(vd_ctx* c, int32_t d_max, int32_t max_disp, int32_t v
       {&vdi::Tuning::blocked, {-1, 1}},            // register-blocked byte-key form
       {&vdi::Tuning::blk_min_blocks, {8, 6}},      // its blocks per SM
       {&vdi::Tuning::fuse_max_k, {0, 2, 4}},       // shared-memory fusion depth of small steps
+      {&vdi::Tuning::tile_max_k, {0, 2, 8}},       // shared-memory tiled byte-key passes
+      {&vdi::Tuning::tile_rows, {16, 8}},          // and that tile's rows
   };
   for (const Dim& d : dims) {
     if (rc) break;
     if (d.field == &vdi::Tuning::blk_min_blocks && best.blocked != 1) continue;  // no effect
+    if (d.field == &vdi::Tuning::tile_rows && best.tile_max_k == 0) continue;      // no effect
     const int start = best.*(d.field);
     for (int v : d.values) {
       if (rc) break;
@@ -1431,6 +1444,8 @@ extern "C" int vd_autotune(vd_ctx* c, int32_t d_max, int32_t max_disp, int32_t v
     chosen[3] = best.blocked;
     chosen[4] = best.blk_min_blocks;
     chosen[5] = best.fuse_max_k;
+    chosen[6] = best.tile_max_k;
+    chosen[7] = best.tile_rows;
   }
   return measured;
 }
@@ -1710,6 +1725,15 @@ extern "C" int vd_set_option(vd_ctx* c, int32_t option, int64_t value) {
       if (value != 32 && value != 64 && value != 128) return vd_fail(VD_EINVAL, "pass tile must be 32, 64 or 128");
       t.pass_bx = static_cast<int>(value);
       break;
+    case VD_OPT_SMEM_TILE_MAX_K:
+      if (value != 0 && value != 1 && value != 2 && value != 4 && value != 8 && value != 16)
+        return vd_fail(VD_EINVAL, "shared-memory tile max k must be 0, 1, 2, 4, 8 or 16");
+      t.tile_max_k = static_cast<int>(value);
+      break;
+    case VD_OPT_SMEM_TILE_ROWS:
+      if (value != 8 && value != 16) return vd_fail(VD_EINVAL, "shared-memory tile rows must be 8 or 16");
+      t.tile_rows = static_cast<int>(value);
+      break;
     default:
       return vd_fail(VD_EINVAL, "unknown option %d", option);
   }
@@ -1740,6 +1764,8 @@ extern "C" int vd_get_option(const vd_ctx* c, int32_t option, int64_t* value) {
     case VD_OPT_SPARSE_PASS: *value = c->tune.sparse; break;
     case VD_OPT_JFA_POSITION_MAP: *value = c->tune.pos_map; break;
     case VD_OPT_PASS_TILE: *value = c->tune.pass_bx; break;
+    case VD_OPT_SMEM_TILE_MAX_K: *value = c->tune.tile_max_k; break;
+    case VD_OPT_SMEM_TILE_ROWS: *value = c->tune.tile_rows; break;
     default: return vd_fail(VD_EINVAL, "unknown option %d", option);
   }
   return VD_OK;

@@ -606,6 +606,7 @@ def test_byte_offset_keys(vd, orc, dedup, w, h, s):
         sim.set_labels(lab)
         sim.jump_pass(k, M, E)
         np.testing.assert_array_equal(sim.labels(), orc.jump_pass(w, h, xy, lab, k, M, E), err_msg=f"k={k}")
+    sim.set_labels(lab)  # the dJFA chain starts from the JFA frame, like the oracle's
     disp = inputs.displacements(s, 2, 2, seed=s)
     for t in range(2):
         sim.move(disp[t])
@@ -844,3 +845,70 @@ def test_pass_tiles(vd, orc, tile):
         sim.djfa_step(d_max=2)
         np.testing.assert_array_equal(sim.labels(), orc.djfa_step(w, h, orc.move(w, h, xy, d), lab, d_max=2))
         sim.close()
+
+
+@pytest.mark.parametrize("max_k,rows", [(8, 16), (16, 16), (16, 8)])
+@pytest.mark.parametrize("w,h,s", [(37, 29, 12), (300, 211, 500), (517, 263, 65535), (640, 480, 65536),
+                                   (1000, 700, 1 << 18)])
+def test_smem_tile_pass(vd, orc, max_k, rows, w, h, s):
+    """The byte-key pass over a shared-memory tile (256 x 16 or 256 x 8 pixels staged
+    with a k-pixel halo as (label, seed position) pairs) against the oracle:
+    k = 1, 2 and multiples of 4 up to 16 (12 included), both neighbourhoods,
+    maps of random labels with and without empty ones (the far position
+    staged outside the map and the empty label make winners fail the check:
+    the recomputation path), ragged widths and heights, the narrow and wide
+    byte forms, then a JFA frame and dJFA steps."""
+    g = np.random.default_rng(s + w + max_k)
+    xy = inputs.uniform_seeds(w, h, s, seed=s + 17)
+    sim = _sim(vd, w, h, xy, byte_keys=1, smem_tile_max_k=max_k, smem_tile_rows=rows)
+    for lo in (-1, 0):
+        src = g.integers(lo, s, size=(h, w), dtype=np.int32)
+        for k in [1, 2, 4, 8, 12, 16]:
+            for nb in [M, VN]:
+                sim.set_labels(src)
+                sim.jump_pass(k, nb, E)
+                got = sim.labels()
+                want = orc.jump_pass(w, h, xy, src, k, nb, E)
+                assert np.array_equal(got, want), (k, nb, lo, int((got != want).sum()))
+    sim.jfa()
+    lab = orc.jfa(w, h, xy)
+    np.testing.assert_array_equal(sim.labels(), lab)
+    for k in [8, 4, 2, 1]:
+        sim.set_labels(lab)
+        sim.jump_pass(k, M, E)
+        np.testing.assert_array_equal(sim.labels(), orc.jump_pass(w, h, xy, lab, k, M, E), err_msg=f"k={k}")
+    sim.set_labels(lab)  # the dJFA chain starts from the JFA frame, like the oracle's
+    disp = inputs.displacements(s, 3, 2, seed=s)
+    for t in range(2):
+        sim.move(disp[t])
+        xy = orc.move(w, h, xy, disp[t])
+        sim.djfa_step(d_max=3)
+        lab = orc.djfa_step(w, h, xy, lab, d_max=3)
+        np.testing.assert_array_equal(sim.labels(), lab, err_msg=f"step {t}")
+    sim.close()
+
+
+@pytest.mark.parametrize("s,D", [(1 << 18, 4), (1 << 14, 4)])
+def test_smem_tile_auto_matches_plain_at_full_size(vd, orc, s, D):
+    """8192 x 8192 sweep points with the tiled pass on (steps up to 8) and
+    off: three graph-replayed dJFA steps give the same maps, the first equal
+    to the oracle."""
+    w = h = 8192
+    xy = inputs.uniform_seeds(w, h, s, seed=19)
+    disp = inputs.displacements(s, D, 3, seed=19)
+    a = _sim(vd, w, h, xy, use_graphs=1, smem_tile_max_k=8)
+    b = _sim(vd, w, h, xy, use_graphs=1, smem_tile_max_k=0)
+    a.jfa()
+    b.jfa()
+    lab = orc.jfa(w, h, xy)
+    for t in range(3):
+        for sim in (a, b):
+            sim.step(disp[t], d_max=D)
+        la = a.labels()
+        np.testing.assert_array_equal(la, b.labels(), err_msg=f"step {t}")
+        if t == 0:
+            xy = orc.move(w, h, xy, disp[t])
+            lab = orc.djfa_step(w, h, xy, lab, d_max=D)
+            np.testing.assert_array_equal(la, lab)
+    a.close()
+    b.close()
