@@ -253,7 +253,7 @@ bool use_byte_key(int byte_option, int32_t metric, int32_t w, int32_t h, int32_t
 int launch_pass(const MapView& m, const int32_t* src, int32_t* dst, int32_t k, int32_t nb,
                 int32_t metric, int64_t band_min_k, bool clamp, cudaStream_t st, bool pdl, bool dedup,
                 bool byte_key, int blocked, int key_pack, int blk_min_blocks, bool sparse, int32_t y0,
-                int32_t y1, int pass_bx, int tile_max_k, int tile_rows) {
+                int32_t y1, int pass_bx, int tile_max_k, int tile_rows, int pk_m, int pk_mode) {
   if (y1 < 0) y1 = m.h;
   const bool rows_only = y0 != 0 || y1 != m.h;
   vdk::PassArgs a;
@@ -308,6 +308,12 @@ int launch_pass(const MapView& m, const int32_t* src, int32_t* dst, int32_t k, i
     else if (a.cap != 0) key = 1;
   }
   if (byte_key && metric == VD_METRIC_EUCLID && a.cap != 0 && a.bwin_bias != 0) key = m.n < 65536 ? 3 : 4;
+  // the position-tagged passes of a dJFA frame (chosen by run_passes)
+  if (pk_m) {
+    if (rows_only || ksel > 2 || (pk_mode == 0 && key != (pk_m == 8 ? 3 : 4)))
+      return vd_fail(VD_EINVAL, "packed pass: step %d, key form %d, layout %d", k, key, pk_m);
+    return launch_pass_pk(a, grid, block, nb, pk_m, ksel, pk_mode, dedup, st, pdl);
+  }
   // a pass over a row range (one band of a split map) always takes the plain kernel
   if (!rows_only && sparse && ksel <= 2)
     return launch_pass_sparse(a, grid, block, nb, metric, key, ksel, dedup, st, pdl);
@@ -440,6 +446,15 @@ int run_passes(const MapView& m, int32_t* const buf[2], int* cur, const int32_t*
                int64_t* launches, Profiler* prof, bool djfa_frame) {
   const std::vector<Launch> plan = plan_passes(ks, nbs, n, t.fuse_max_k, t.max_halo);
   const int64_t px = static_cast<int64_t>(m.w) * m.h;
+  // the frame's last passes on position-tagged words: [pk_first, n), at least
+  // two of them (the first reads the plain map, the last writes it), never
+  // with shared-memory fusion
+  int pk_first = n;
+  const int pk_m = t.fuse_max_k <= 0 ? pk_bits(m.n) : 0;
+  if (pk_m) {
+    while (pk_first > 0 && use_packed(t, metric, m.w, m.h, m.n, ks[pk_first - 1], djfa_frame)) --pk_first;
+    if (n - pk_first < 2) pk_first = n;
+  }
   for (const Launch& l : plan) {
     const int32_t* src = buf[*cur];
     int32_t* dst = buf[*cur ^ 1];
@@ -452,7 +467,8 @@ int run_passes(const MapView& m, int32_t* const buf[2], int* cur, const int32_t*
                        use_byte_key(t.byte_key, metric, m.w, m.h, m.n, ks[l.first], djfa_frame), t.blocked,
                        t.key_pack, t.blk_min_blocks,
                        use_sparse(t.sparse, m.w, m.h, m.n, ks[l.first]), 0, -1, t.pass_bx, t.tile_max_k,
-                       t.tile_rows);
+                       t.tile_rows, l.first >= pk_first ? pk_m : 0,
+                       l.first == pk_first ? 0 : (l.first == n - 1 ? 2 : 1));
     } else {
       rc = launch_fused(m, src, dst, ks + l.first, nbs + l.first, l.n, metric, t.tile_x, t.tile_y, st);
     }
@@ -462,6 +478,20 @@ int run_passes(const MapView& m, int32_t* const buf[2], int* cur, const int32_t*
     *cur ^= 1;
   }
   return VD_OK;
+}
+
+bool use_packed(const Tuning& t, int32_t metric, int32_t w, int32_t h, int32_t n, int32_t k, bool djfa_frame) {
+  if (t.packed == 0 || !djfa_frame) return false;
+  const int lay = pk_bits(n);
+  if (lay == 0 || !(k == 1 || k == 2 || k % 4 == 0)) return false;
+  if (!use_byte_key(t.byte_key, metric, w, h, n, k, djfa_frame)) return false;
+  if (t.packed == 1) return true;
+  // auto: the byte-offset key's bounds (mean cell radius at most 40 pixels
+  // per 128 of window, k at most twice the window) with the layout's window
+  const double hw = static_cast<double>(1 << (lay - 1));
+  if (k > 2 * hw) return false;
+  const double r_max = 40.0 * hw / 128.0;
+  return static_cast<double>(w) * h <= 3.141592653589793 * r_max * r_max * n;
 }
 
 bool use_dedup(int dedup_option, int32_t w, int32_t h, int32_t n, bool djfa_frame) {
@@ -1734,6 +1764,10 @@ extern "C" int vd_set_option(vd_ctx* c, int32_t option, int64_t value) {
       if (value != 8 && value != 16) return vd_fail(VD_EINVAL, "shared-memory tile rows must be 8 or 16");
       t.tile_rows = static_cast<int>(value);
       break;
+    case VD_OPT_PACKED_MAP:
+      if (value < -1 || value > 1) return vd_fail(VD_EINVAL, "packed map must be -1, 0 or 1");
+      t.packed = static_cast<int>(value);
+      break;
     default:
       return vd_fail(VD_EINVAL, "unknown option %d", option);
   }
@@ -1766,6 +1800,7 @@ extern "C" int vd_get_option(const vd_ctx* c, int32_t option, int64_t* value) {
     case VD_OPT_PASS_TILE: *value = c->tune.pass_bx; break;
     case VD_OPT_SMEM_TILE_MAX_K: *value = c->tune.tile_max_k; break;
     case VD_OPT_SMEM_TILE_ROWS: *value = c->tune.tile_rows; break;
+    case VD_OPT_PACKED_MAP: *value = c->tune.packed; break;
     default: return vd_fail(VD_EINVAL, "unknown option %d", option);
   }
   return VD_OK;

@@ -49,6 +49,7 @@ struct Tuning {
   int pass_bx = 64;   // pass block tile: quads per row (32, 64, 128) x 128 / that many rows
   int tile_max_k = 0;  // byte-key passes with k <= this over a shared-memory tile (0 = never)
   int tile_rows = 16;  // rows of that tile (8 or 16)
+  int packed = -1;     // dJFA frames' last byte-key passes on position-tagged words: -1 auto, 0, 1
 };
 
 // Event pairs bracketing kernel launches (profiling mode).  Records are kept
@@ -91,7 +92,7 @@ int launch_pass(const MapView& m, const int32_t* src, int32_t* dst, int32_t k, i
                 int32_t metric, int64_t band_min_k, bool clamp, cudaStream_t st, bool pdl = false,
                 bool dedup = false, bool byte_key = false, int blocked = 0, int key_pack = 0,
                 int blk_min_blocks = 8, bool sparse = false, int32_t y0 = 0, int32_t y1 = -1,
-                int pass_bx = 64, int tile_max_k = 0, int tile_rows = 16);
+                int pass_bx = 64, int tile_max_k = 0, int tile_rows = 16, int pk_m = 0, int pk_mode = 0);
 // Whether a pass with step k runs in the sparse form (auto: k at most 1/32 of
 // the mean cell side).
 bool use_sparse(int sparse_option, int32_t w, int32_t h, int32_t n, int32_t k);
@@ -134,6 +135,14 @@ int launch_pass_sparse(const vdk::PassArgs& a, dim3 grid, dim3 block, int32_t nb
 // multiple of 4 up to 16, key forms 3 and 4, at most tile_max_k.
 bool tile_applies(int32_t k, int key, int max_k);
 int launch_pass_tile(const vdk::PassArgs& a, int32_t nb, int key, int rows, cudaStream_t st, bool pdl);
+// The position-tagged dJFA passes (vd_pass_pk.cuh): the word layout M for n
+// seeds (8, 7 or 6; 0 where none holds the labels), and one pass with step
+// k = 1, 2 or k % 4 == 0 (ksel 1, 2, 0) of layout m: mode 0 plain map in,
+// words out; 1 words in and out; 2 words in, plain labels out.
+int pk_bits(int32_t n);
+bool use_packed(const Tuning& t, int32_t metric, int32_t w, int32_t h, int32_t n, int32_t k, bool djfa_frame);
+int launch_pass_pk(const vdk::PassArgs& a, dim3 grid, dim3 block, int32_t nb, int m, int ksel, int mode,
+                   bool dedup, cudaStream_t st, bool pdl);
 // The position map of JFA frames (vd_pass_pos.cu): per pixel (label, x | y << 16).
 int launch_fill_pos(int2* map, int64_t elems, cudaStream_t st, bool pdl);
 int launch_stamp_pos(const MapView& m, int2* map, cudaStream_t st, bool pdl);

@@ -33,6 +33,7 @@ OPT_JFA_POSITION_MAP = 15
 OPT_PASS_TILE = 16
 OPT_SMEM_TILE_MAX_K = 17
 OPT_SMEM_TILE_ROWS = 18
+OPT_PACKED_MAP = 19
 
 KERNEL_KINDS = ("pass", "fused", "stamp", "move", "fill")
 

@@ -912,3 +912,67 @@ def test_smem_tile_auto_matches_plain_at_full_size(vd, orc, s, D):
             np.testing.assert_array_equal(la, lab)
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("w,h,s", [(37, 29, 12), (300, 211, 500), (517, 263, 32767), (1000, 70, 40000),
+                                   (640, 480, 65536), (700, 500, 131071), (1000, 700, 131072),
+                                   (1024, 700, 1 << 18)])
+def test_packed_map_frames(vd, orc, w, h, s):
+    """dJFA frames whose byte-key passes run on position-tagged words (forced
+    on) against the oracle, for each word layout: up to 32767 seeds (8-bit
+    position fields), 2^16 .. 2^17 - 1 (7-bit), 2^17 .. 2^18 (6-bit, where the
+    last seed's label code is also the empty code); 40000 seeds fit no layout
+    and keep the plain passes.  Frames after the JFA frame with moves, extra
+    passes and no Von Neumann waves, then frames stamped onto random maps with
+    and without empty labels: nearly every quad there fails the winner check
+    and is recomputed, and empty pixels cross the packed passes.  Ragged
+    widths and heights put the map border inside blocks."""
+    g = np.random.default_rng(s + w)
+    xy = inputs.uniform_seeds(w, h, s, seed=s + 29)
+    sim = _sim(vd, w, h, xy, byte_keys=1, packed_map=1)
+    sim.jfa()
+    lab = orc.jfa(w, h, xy)
+    np.testing.assert_array_equal(sim.labels(), lab)
+    disp = inputs.displacements(s, 5, 3, seed=s + 1)
+    for t, (D, vn, extra) in enumerate([(5, 2, 0), (2, 0, 1), (1, 2, 2)]):
+        sim.move(disp[t])
+        xy = orc.move(w, h, xy, disp[t])
+        sim.djfa_step(d_max=D, vn_waves=vn, extra=extra)
+        lab = orc.djfa_step(w, h, xy, lab, d_max=D, vn_waves=vn, extra=extra)
+        got = sim.labels()
+        assert np.array_equal(got, lab), (t, int((got != lab).sum()))
+    for lo in (-1, 0):
+        src = g.integers(lo, s, size=(h, w), dtype=np.int32)
+        for D in (1, 4):
+            sim.set_labels(src)
+            sim.djfa_step(d_max=D)
+            got = sim.labels()
+            want = orc.djfa_step(w, h, xy, src, d_max=D)
+            assert np.array_equal(got, want), (lo, D, int((got != want).sum()))
+    sim.close()
+
+
+@pytest.mark.parametrize("s,D", [(1 << 18, 4), (1 << 16, 4), (1 << 14, 4)])
+def test_packed_auto_matches_plain_at_full_size(vd, orc, s, D):
+    """8192 x 8192 sweep points with the position-tagged passes (auto) and
+    without: three graph-replayed dJFA steps give the same maps, the first
+    equal to the oracle."""
+    w = h = 8192
+    xy = inputs.uniform_seeds(w, h, s, seed=23)
+    disp = inputs.displacements(s, D, 3, seed=23)
+    a = _sim(vd, w, h, xy, use_graphs=1)
+    b = _sim(vd, w, h, xy, use_graphs=1, packed_map=0)
+    a.jfa()
+    b.jfa()
+    lab = orc.jfa(w, h, xy)
+    for t in range(3):
+        for sim in (a, b):
+            sim.step(disp[t], d_max=D)
+        la = a.labels()
+        np.testing.assert_array_equal(la, b.labels(), err_msg=f"step {t}")
+        if t == 0:
+            xy = orc.move(w, h, xy, disp[t])
+            lab = orc.djfa_step(w, h, xy, lab, d_max=D)
+            np.testing.assert_array_equal(la, lab)
+    a.close()
+    b.close()
