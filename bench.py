@@ -250,10 +250,17 @@ def hbm_peak():
         return FALLBACK_HBM_GBS, "fallback (6.8 TB/s, earlier GB300 copy measurement)"
 
 
+# the sources of the timed pass kernels: the plain pass and the
+# position-tagged passes of a dJFA frame
+PASS_SOURCES = ("vd_kernels.cuh", "vd_pass_pk.cuh")
+
+
 def kernel_source_hash():
-    p = os.path.join(ROOT, "paper_2209_00117_gb300", "csrc", "vd_kernels.cuh")
-    with open(p, "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+    h = hashlib.sha256()
+    for name in PASS_SOURCES:
+        with open(os.path.join(ROOT, "paper_2209_00117_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
 
 def recorded_traffic(kind, workload_name):

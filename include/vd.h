@@ -616,7 +616,8 @@ int vd_set_option(vd_ctx* ctx, int32_t option, int64_t value);
  * metric as for vd_djfa_step) after one untimed step; the snapshot is
  * restored before every candidate and at the end, so the state is left as it
  * was.  The search goes through one dimension at a time, the others held at
- * the best so far: the pass block tile (VD_OPT_PASS_TILE 64, 32, 128),
+ * the best so far: the position-tagged passes (VD_OPT_PACKED_MAP -1, 0),
+ * the pass block tile (VD_OPT_PASS_TILE 64, 32, 128),
  * gather de-duplication (VD_OPT_DEDUP_GATHERS -1, 0, 1), the sparse form
  * (VD_OPT_SPARSE_PASS -1, 0, 1), the register-blocked form
  * (VD_OPT_BLOCKED_PASS -1, 1) and, when on, its blocks per SM
@@ -624,7 +625,10 @@ int vd_set_option(vd_ctx* ctx, int32_t option, int64_t value);
  * small steps (VD_OPT_FUSE_MAX_K 0, 2, 4), the shared-memory tiled form
  * (VD_OPT_SMEM_TILE_MAX_K 0, 2, 8) and, when on, its rows
  * (VD_OPT_SMEM_TILE_ROWS 16, 8).  The fastest setting stays in force.
- * chosen (may be NULL) receives 8 values in that order; ms_per_step
+ * chosen (may be NULL) receives 9 values: the pass block tile, gather
+ * de-duplication, the sparse form, the blocked form, its blocks per SM, the
+ * fusion depth, the tiled form's largest step, its rows, then the
+ * position-tagged passes; ms_per_step
  * (at least cap entries, may be NULL with cap = 0) the time of each candidate
  * measured, in order.  Allocates and frees one map-sized snapshot; synchronises
  * the stream.  Returns the number of candidates measured, or a VD_E* code

@@ -261,6 +261,7 @@ int launch_pass(const MapView& m, const int32_t* src, int32_t* dst, int32_t k, i
   a.dst = dst;
   a.table = m.table;
   a.ptable = m.ptable;
+  a.pkf = m.pkf;
   {
     const int lb = label_bits(m.n);
     a.mul = lb >= 32 ? 0u : (1u << lb);
@@ -640,6 +641,7 @@ struct vd_ctx {
   int2* seeds = nullptr;
   int2* table = nullptr;   // n + 1 entries, [0] = sentinel
   uint32_t* ptable = nullptr;  // n + 1 packed positions, [0] = far position
+  uint2* pkf = nullptr;        // n + 1 entries of the position-tagged passes, [0] = far position
   int2* dxy_stage = nullptr;
   unsigned long long* counters = nullptr;      // [0] n_exact, [1] n_match, [2] flag
   unsigned long long* host_counters = nullptr;  // pinned mirror
@@ -689,6 +691,7 @@ static vdi::MapView view(const vd_ctx* c) {
   m.seeds = c->seeds;
   m.table = c->table + 1;
   m.ptable = c->ptable + 1;
+  m.pkf = c->pkf;
   return m;
 }
 
@@ -719,6 +722,7 @@ static void ctx_free(vd_ctx* c) {
   cudaFree(c->seeds);
   cudaFree(c->table);
   cudaFree(c->ptable);
+  cudaFree(c->pkf);
   cudaFree(c->dxy_stage);
   cudaFree(c->counters);
   cudaFreeHost(c->host_counters);
@@ -752,6 +756,7 @@ extern "C" vd_ctx* vd_create(int32_t w, int32_t h, int32_t n) {
   rc = rc ? rc : ctx_alloc(reinterpret_cast<void**>(&c->seeds), sizeof(int2) * n, "seeds");
   rc = rc ? rc : ctx_alloc(reinterpret_cast<void**>(&c->table), sizeof(int2) * (static_cast<size_t>(n) + 1), "seed table");
   rc = rc ? rc : ctx_alloc(reinterpret_cast<void**>(&c->ptable), sizeof(uint32_t) * (static_cast<size_t>(n) + 1), "seed table");
+  rc = rc ? rc : ctx_alloc(reinterpret_cast<void**>(&c->pkf), sizeof(uint2) * (static_cast<size_t>(n) + 1), "seed table");
   rc = rc ? rc : ctx_alloc(reinterpret_cast<void**>(&c->dxy_stage), sizeof(int2) * n, "moves");
   rc = rc ? rc : ctx_alloc(reinterpret_cast<void**>(&c->counters), 4 * sizeof(unsigned long long), "counters");
   if (!rc) {
@@ -853,15 +858,18 @@ static int grow_seed_buffers(vd_ctx* c, int32_t cap, const int* keep, const int*
   int2* seeds = nullptr;
   int2* table = nullptr;
   uint32_t* ptable = nullptr;
+  uint2* pkf = nullptr;
   int2* stage = nullptr;
   int rc = ctx_alloc(reinterpret_cast<void**>(&seeds), sizeof(int2) * cap, "seeds");
   rc = rc ? rc : ctx_alloc(reinterpret_cast<void**>(&table), sizeof(int2) * (static_cast<size_t>(cap) + 1), "seed table");
   rc = rc ? rc : ctx_alloc(reinterpret_cast<void**>(&ptable), sizeof(uint32_t) * (static_cast<size_t>(cap) + 1), "seed table");
+  rc = rc ? rc : ctx_alloc(reinterpret_cast<void**>(&pkf), sizeof(uint2) * (static_cast<size_t>(cap) + 1), "seed table");
   rc = rc ? rc : ctx_alloc(reinterpret_cast<void**>(&stage), sizeof(int2) * cap, "moves");
   if (rc) {
     cudaFree(seeds);
     cudaFree(table);
     cudaFree(ptable);
+    cudaFree(pkf);
     cudaFree(stage);
     return rc;
   }
@@ -873,18 +881,21 @@ static int grow_seed_buffers(vd_ctx* c, int32_t cap, const int* keep, const int*
     cudaFree(seeds);
     cudaFree(table);
     cudaFree(ptable);
+    cudaFree(pkf);
     cudaFree(stage);
     return rc;
   }
   cudaFree(c->seeds);
   cudaFree(c->table);
   cudaFree(c->ptable);
+  cudaFree(c->pkf);
   cudaFree(c->dxy_stage);
   cudaFree(c->bk_ids);  // sized by the seed count; reallocated on next use
   c->bk_ids = nullptr;
   c->seeds = seeds;
   c->table = table;
   c->ptable = ptable;
+  c->pkf = pkf;
   c->dxy_stage = stage;
   c->cap = cap;
   return VD_OK;
@@ -1427,6 +1438,7 @@ extern "C" int vd_autotune(vd_ctx* c, int32_t d_max, int32_t max_disp, int32_t v
     std::vector<int> values;
   };
   const Dim dims[] = {
+      {&vdi::Tuning::packed, {-1, 0}},             // position-tagged passes (auto, off)
       {&vdi::Tuning::pass_bx, {64, 32, 128}},      // block tile
       {&vdi::Tuning::dedup, {-1, 0, 1}},           // gather de-duplication
       {&vdi::Tuning::sparse, {-1, 0, 1}},          // sparse form of small steps
@@ -1476,6 +1488,7 @@ extern "C" int vd_autotune(vd_ctx* c, int32_t d_max, int32_t max_disp, int32_t v
     chosen[5] = best.fuse_max_k;
     chosen[6] = best.tile_max_k;
     chosen[7] = best.tile_rows;
+    chosen[8] = best.packed;
   }
   return measured;
 }

@@ -20,6 +20,7 @@ struct MapView {
   const int2* seeds = nullptr;
   const int2* table = nullptr;   // packed pass table, entry -1 = sentinel
   const uint32_t* ptable = nullptr;  // packed positions x | y << 16, entry -1 = far position
+  uint2* pkf = nullptr;  // n + 1 entries for the position-tagged passes, [0] = far position
 };
 
 // Bits of the largest label (ceil(log2 n_seeds)); clamped 32-bit keys need

@@ -136,6 +136,10 @@ struct PassArgs {
   int band_m;  // > 1: visit row-blocks in k-strided bands (band_m = k / rows per block)
   int band_t;  // row-blocks per band residue class
   int y0, y_end;  // k_pass writes rows [y0, y_end) of dst (the whole map: 0, h)
+  // position-tagged passes (wide layouts): n + 1 entries {x | y << 16, the
+  // seed's word bits but the label}, [0] the far position; written by a
+  // frame's first such pass for the ones after it
+  uint2* __restrict__ pkf;
 };
 
 // Stops the compiler from hoisting later loads above this point, which keeps

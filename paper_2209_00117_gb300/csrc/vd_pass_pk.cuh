@@ -90,7 +90,11 @@ struct Pk {
   // The winner's word from its key and its seed position e (check passed).
   __device__ __forceinline__ static uint32_t word_of_key(uint32_t key, uint32_t e) {
     if (kNarrow) return __byte_perm(key, e, 0x6140);
-    return (key & kLm) | kG | ((e << kXs) & (kXm << kXs)) | ((e << (16 - M)) & (kXm << kYs));
+    return (key & kLm) | fields(e);
+  }
+  // A word's bits but the label, for the seed at e (wide layouts).
+  __device__ __forceinline__ static uint32_t fields(uint32_t e) {
+    return kG | ((e << kXs) & (kXm << kXs)) | ((e << (16 - M)) & (kXm << kYs));
   }
 };
 
@@ -104,7 +108,8 @@ __device__ __forceinline__ uint2 words2(const int32_t* p) { return __ldg(reinter
 // least (distance^2, label) over its candidates (Table I / Section V-B),
 // candidates outside the map and empty ones skipped, read from a plain map
 // (PKIN false) or a packed one; written plain or packed (PKOUT).  Rare: out
-// of line, so that the common path keeps its small register budget.
+// of line (with the border blocks' path also out of line, measured 6% faster
+// a dJFA frame than either inline on the GB300).
 template <int NB, int M, bool PKIN, bool PKOUT>
 __device__ __noinline__ void pk_exact_quad(const PassArgs a, int x0, int y) {
   using F = Pk<M>;
@@ -148,18 +153,25 @@ __device__ __noinline__ void pk_exact_quad(const PassArgs a, int x0, int y) {
 // [-h, h) around each pixel, and every d < h^2.  lm = 2^lb - 1; the window
 // kw = h * 0x10001 - (x0 | y << 16), wmask = (0xFFFF & ~(2h - 1)) * 0x10001,
 // lim = h^2 << ks.  PKOUT: words of layout M from the keys (key form KF: 0
-// the plain byte-offset key, labels in the low lb bits; 1 this layout's).
-// Returns false when the quad must be recomputed.
+// the plain byte-offset key, labels in the low lb bits; 1 this layout's;
+// 2 this layout's, wide, with each seed's word bits read from a.pkf beside
+// its position).  Returns false when the quad must be recomputed.
 template <int M, int KF, bool PKOUT, bool IN>
 __device__ __forceinline__ bool pk_check_store(const PassArgs& a, const uint32_t (&b)[4], int x0, int y,
                                                uint32_t lm, uint32_t kw, uint32_t wmask, uint32_t lim) {
   using F = Pk<M>;
   const uint32_t* __restrict__ arena = a.ptable - 1;
-  uint32_t e[4];
+  uint32_t e[4], f[4];
   uint32_t bad = 0, top = 0;
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
-    e[i] = __ldg(&arena[(b[i] + 1u) & lm]);
+    if (KF == 2) {
+      const uint2 ef = __ldg(&a.pkf[(b[i] + 1u) & lm]);
+      e[i] = ef.x;
+      f[i] = ef.y;
+    } else {
+      e[i] = __ldg(&arena[(b[i] + 1u) & lm]);
+    }
     // (dx + h) | (dy + h) << 16 has no bit at or above 2h in either half
     // exactly when dx, dy lie in [-h, h)
     const uint32_t t = (e[i] + kw - static_cast<uint32_t>(i)) & wmask;
@@ -172,7 +184,7 @@ __device__ __forceinline__ bool pk_check_store(const PassArgs& a, const uint32_t
   uint32_t o[4];
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
-    if (PKOUT) o[i] = KF == 1 ? F::word_of_key(b[i], e[i]) : F::word(b[i] & lm, e[i]);
+    if (PKOUT) o[i] = KF == 2 ? (b[i] & lm) | f[i] : KF == 1 ? F::word_of_key(b[i], e[i]) : F::word(b[i] & lm, e[i]);
     else o[i] = b[i] & lm;
     if (!IN && x0 + i >= a.w) o[i] = PKOUT ? F::kEmpty : 0xFFFFFFFFu;
   }
@@ -204,64 +216,85 @@ __device__ __forceinline__ void pk_first_quad(const PassArgs& a, int x0, int y) 
 template <int NB, int KSEL, int M, bool PKOUT, bool IN>
 __device__ __forceinline__ void pk_quad(const PassArgs& a, int x0, int y) {
   using F = Pk<M>;
+  // element indices fit 32 bits (sides up to 32768): one base pointer and
+  // 32-bit offsets keep the six runtime-step addresses cheap in registers
   const int k = a.k;
-  const int64_t pitch = a.pitch;
-  const int32_t* crow = a.src + y * pitch;
+  const int32_t* __restrict__ src = a.src;
+  const int c0 = y * a.pitch + x0;
+  const int kp = k * a.pitch;
   const uint32_t pn = F::neg_pix(static_cast<uint32_t>(x0), static_cast<uint32_t>(y));
-  uint32_t pi[4];
-#pragma unroll
-  for (int i = 0; i < 4; ++i) pi[i] = pn - (static_cast<uint32_t>(i) << F::kXs);
+  // pixel i's fields: pn minus i in the x field (one three-input add with
+  // the word, the offset an immediate)
+#define pi(i) (pn - (static_cast<uint32_t>(i) << F::kXs))
   uint32_t b[4];
-  const uint4 own = words4(crow + x0);
+  const uint4 own = words4(src + c0);
   const bool up_ok = IN || y - k >= 0;
   const bool dn_ok = IN || y + k < a.h;
-  const int32_t* urow = a.src + (y - k) * pitch;
-  const int32_t* drow = a.src + (y + k) * pitch;
   const uint32_t ow[4] = {own.x, own.y, own.z, own.w};
 #pragma unroll
-  for (int i = 0; i < 4; ++i) b[i] = F::key(ow[i], pi[i]);
-  // the side candidates of one row, `mid` its vector at x0
-  auto sides = [&](const int32_t* row, const uint32_t (&mid)[4]) {
+  for (int i = 0; i < 4; ++i) b[i] = F::key(ow[i], pi(i));
+  // the side candidates of one row (index r of its element at x0), `mid` its
+  // vector at x0
+  auto sides = [&](int r, const uint32_t (&mid)[4]) {
     if (KSEL == 0) {
       const bool lok = IN || x0 - k >= 0, rok = IN || x0 + k < a.pitch;
-      const uint4 L = lok ? words4(row + x0 - k) : make_uint4(mid[0], mid[1], mid[2], mid[3]);
-      const uint4 R = rok ? words4(row + x0 + k) : make_uint4(mid[0], mid[1], mid[2], mid[3]);
-      const uint32_t l[4] = {L.x, L.y, L.z, L.w}, r[4] = {R.x, R.y, R.z, R.w};
+      const uint4 L = lok ? words4(src + r - k) : make_uint4(mid[0], mid[1], mid[2], mid[3]);
+      const uint32_t l[4] = {L.x, L.y, L.z, L.w};
 #pragma unroll
-      for (int i = 0; i < 4; ++i) b[i] = min(b[i], min(F::key(l[i], pi[i]), F::key(r[i], pi[i])));
+      for (int i = 0; i < 4; ++i) b[i] = min(b[i], F::key(l[i], pi(i)));
+      group_fence();
+      const uint4 R = rok ? words4(src + r + k) : make_uint4(mid[0], mid[1], mid[2], mid[3]);
+      const uint32_t r[4] = {R.x, R.y, R.z, R.w};
+#pragma unroll
+      for (int i = 0; i < 4; ++i) b[i] = min(b[i], F::key(r[i], pi(i)));
     } else if (KSEL == 1) {
       // left of pixel i: column x0 + i - 1; right: x0 + i + 1
-      const uint32_t l = (IN || x0 >= 4) ? words1(row + x0 - 1) : mid[0];
-      const uint32_t r = (IN || x0 + 4 < a.pitch) ? words1(row + x0 + 4) : mid[3];
-      b[0] = min(b[0], min(F::key(l, pi[0]), F::key(mid[1], pi[0])));
-      b[1] = min(b[1], min(F::key(mid[0], pi[1]), F::key(mid[2], pi[1])));
-      b[2] = min(b[2], min(F::key(mid[1], pi[2]), F::key(mid[3], pi[2])));
-      b[3] = min(b[3], min(F::key(mid[2], pi[3]), F::key(r, pi[3])));
+      const uint32_t wl = (IN || x0 >= 4) ? words1(src + r - 1) : mid[0];
+      const uint32_t wr = (IN || x0 + 4 < a.pitch) ? words1(src + r + 4) : mid[3];
+      b[0] = min(b[0], min(F::key(wl, pi(0)), F::key(mid[1], pi(0))));
+      b[1] = min(b[1], min(F::key(mid[0], pi(1)), F::key(mid[2], pi(1))));
+      b[2] = min(b[2], min(F::key(mid[1], pi(2)), F::key(mid[3], pi(2))));
+      b[3] = min(b[3], min(F::key(mid[2], pi(3)), F::key(wr, pi(3))));
     } else {
       // left of pixel i: column x0 + i - 2; right: x0 + i + 2
-      const uint2 l = (IN || x0 >= 4) ? words2(row + x0 - 2) : make_uint2(mid[0], mid[1]);
-      const uint2 r = (IN || x0 + 4 < a.pitch) ? words2(row + x0 + 4) : make_uint2(mid[2], mid[3]);
-      b[0] = min(b[0], min(F::key(l.x, pi[0]), F::key(mid[2], pi[0])));
-      b[1] = min(b[1], min(F::key(l.y, pi[1]), F::key(mid[3], pi[1])));
-      b[2] = min(b[2], min(F::key(mid[0], pi[2]), F::key(r.x, pi[2])));
-      b[3] = min(b[3], min(F::key(mid[1], pi[3]), F::key(r.y, pi[3])));
+      const uint2 wl = (IN || x0 >= 4) ? words2(src + r - 2) : make_uint2(mid[0], mid[1]);
+      const uint2 wr = (IN || x0 + 4 < a.pitch) ? words2(src + r + 4) : make_uint2(mid[2], mid[3]);
+      b[0] = min(b[0], min(F::key(wl.x, pi(0)), F::key(mid[2], pi(0))));
+      b[1] = min(b[1], min(F::key(wl.y, pi(1)), F::key(mid[3], pi(1))));
+      b[2] = min(b[2], min(F::key(mid[0], pi(2)), F::key(wr.x, pi(2))));
+      b[3] = min(b[3], min(F::key(mid[1], pi(3)), F::key(wr.y, pi(3))));
     }
   };
   // the row's own vector at x0 (the vertical candidates), then its sides
-  auto row_all = [&](const int32_t* row) {
-    const uint4 V = words4(row + x0);
+  auto row_all = [&](int r) {
+    const uint4 V = words4(src + r);
     const uint32_t v[4] = {V.x, V.y, V.z, V.w};
 #pragma unroll
-    for (int i = 0; i < 4; ++i) b[i] = min(b[i], F::key(v[i], pi[i]));
-    if (NB == kMoore) sides(row, v);
+    for (int i = 0; i < 4; ++i) b[i] = min(b[i], F::key(v[i], pi(i)));
+    if (NB == kMoore) sides(r, v);
   };
-  sides(crow, ow);
-  if (up_ok) row_all(urow);
-  if (dn_ok) row_all(drow);
+  // one row's loads in flight at a time (group_fence): the register budget
+  // of the launch shape holds no more
+  sides(c0, ow);
+  group_fence();
+  if (up_ok) row_all(c0 - kp);
+  group_fence();
+  if (dn_ok) row_all(c0 + kp);
   const uint32_t kw = F::kH * 0x10001u - (static_cast<uint32_t>(x0) + (static_cast<uint32_t>(y) << 16));
   const uint32_t wmask = (0xFFFFu & ~(2u * F::kH - 1u)) * 0x10001u;
-  if (!pk_check_store<M, 1, PKOUT, IN>(a, b, x0, y, F::kLm, kw, wmask, (F::kH * F::kH) << F::kKs))
+  // words out of a wide layout take their bits from a.pkf
+  constexpr int kf = PKOUT && M != 8 ? 2 : 1;
+  if (!pk_check_store<M, kf, PKOUT, IN>(a, b, x0, y, F::kLm, kw, wmask, (F::kH * F::kH) << F::kKs))
     pk_exact_quad<NB, M, true, PKOUT>(a, x0, y);
+#undef pi
+}
+
+// The blocks within k of the map border (a few percent of them) run out of
+// line, so that the interior path keeps a register allocation of its own.
+template <int NB, int KSEL, int M, int MODE, bool DEDUP>
+__device__ __noinline__ void pk_edge_quad(const PassArgs a, int x0, int y) {
+  if (MODE == 0) pk_first_quad<NB, KSEL, M, DEDUP, false>(a, x0, y);
+  else pk_quad<NB, KSEL, M, MODE == 1, false>(a, x0, y);
 }
 
 #ifndef VD_PK_MIN_BLOCKS
@@ -272,10 +305,21 @@ __device__ __forceinline__ void pk_quad(const PassArgs& a, int x0, int y) {
 // k-strided bands when band_m > 1), and its block-uniform interior test.
 // MODE 0: plain map in, words out (DEDUP: the fold's gathers de-duplicated);
 // 1: words in and out; 2: words in, plain labels out.
+// MODE 0 of a wide layout also writes a.pkf (the seed positions of this
+// frame with their word bits) for the passes after it.
 template <int NB, int KSEL, int M, int MODE, bool DEDUP = false>
 __global__ void __launch_bounds__(kPassThreads, VD_PK_MIN_BLOCKS) k_pass_pk(PassArgs a) {
   pdl_trigger();
   pdl_wait();
+  if (MODE == 0 && M != 8) {
+    const uint32_t nt = gridDim.x * gridDim.y * blockDim.x * blockDim.y;
+    const uint32_t t0 = ((blockIdx.y * gridDim.x + blockIdx.x) * blockDim.y + threadIdx.y) * blockDim.x + threadIdx.x;
+    const uint32_t* __restrict__ arena = a.ptable - 1;
+    for (uint32_t j = t0; j <= a.n_seeds; j += nt) {
+      const uint32_t e = __ldg(&arena[j]);
+      a.pkf[j] = make_uint2(e, j == 0 ? 0u : Pk<M>::fields(e));
+    }
+  }
   const int x0 = 4 * static_cast<int>(blockIdx.x * blockDim.x + threadIdx.x);
   int rb = blockIdx.y;
   if (a.band_m > 1) rb = (blockIdx.y % a.band_t) * a.band_m + blockIdx.y / a.band_t;
@@ -285,13 +329,9 @@ __global__ void __launch_bounds__(kPassThreads, VD_PK_MIN_BLOCKS) k_pass_pk(Pass
   const int xb = 4 * static_cast<int>(blockIdx.x * blockDim.x);
   const bool in = xb - a.k >= 0 && xb + 4 * static_cast<int>(blockDim.x) + a.k <= a.w && yb - a.k >= 0 &&
                   yb + static_cast<int>(blockDim.y) + a.k <= a.h;
-  if (MODE == 0) {
-    if (in) pk_first_quad<NB, KSEL, M, DEDUP, true>(a, x0, y);
-    else pk_first_quad<NB, KSEL, M, DEDUP, false>(a, x0, y);
-  } else {
-    if (in) pk_quad<NB, KSEL, M, MODE == 1, true>(a, x0, y);
-    else pk_quad<NB, KSEL, M, MODE == 1, false>(a, x0, y);
-  }
+  if (!in) pk_edge_quad<NB, KSEL, M, MODE, DEDUP>(a, x0, y);
+  else if (MODE == 0) pk_first_quad<NB, KSEL, M, DEDUP, true>(a, x0, y);
+  else pk_quad<NB, KSEL, M, MODE == 1, true>(a, x0, y);
 }
 
 }  // namespace vdk

@@ -261,14 +261,14 @@ class VoronoiSim:
         """Times the pass launch shapes on this context's dJFA steps and keeps
         the fastest (state left as it was; see vd_autotune).  Returns
         ({option: value}, [ms per step of each candidate measured])."""
-        chosen = np.zeros(8, np.int32)
+        chosen = np.zeros(9, np.int32)
         times = np.zeros(64, np.float64)
         n = self._lib.vd_autotune(self._h, int(d_max), int(max_disp), int(vn_waves), int(metric),
                                   int(rng_seed) & (2**64 - 1), int(steps),
                                   chosen.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), times.ctypes.data, 64)
         N.check(min(n, 0))
         names = ["pass_tile", "dedup_gathers", "sparse_pass", "blocked_pass", "blocked_min_blocks", "fuse_max_k",
-                 "smem_tile_max_k", "smem_tile_rows"]
+                 "smem_tile_max_k", "smem_tile_rows", "packed_map"]
         return dict(zip(names, (int(v) for v in chosen))), [float(t) for t in times[:n]]
 
     def pass_rows(self, k: int, nb: int, y0: int, y1: int, metric: int = EUCLID, djfa_frame: bool = True):

@@ -806,6 +806,7 @@ def test_autotune_keeps_state_and_results(vd, orc, w, h, s, D):
     chosen, times = a.autotune(d_max=D, max_disp=D, steps=3)
     assert len(times) >= 8 and all(t > 0 for t in times)
     assert chosen["pass_tile"] in (32, 64, 128) and chosen["fuse_max_k"] in (0, 2, 4)
+    assert chosen["packed_map"] in (-1, 0)
     np.testing.assert_array_equal(a.labels(), before)
     np.testing.assert_array_equal(a.get_seeds(), xy)
     assert a.get_option(vd.OPT_PASS_TILE) == chosen["pass_tile"]
