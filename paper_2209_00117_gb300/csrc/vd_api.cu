@@ -523,7 +523,11 @@ int launch_stamp(const MapView& m, int32_t* labels, bool mark, cudaStream_t st, 
     ++*launches;
   }
   // the minimum half follows the mark half or a fill: it may start while that drains
-  const cudaError_t e = launch_k(vdk::k_stamp_min, dim3(blocks), dim3(256), st, pdl, labels, m.pitch, m.seeds, m.n);
+  // (and, for the wide position-tagged layouts, the frame's seed entries of
+  // those passes)
+  const int pkm = pk_bits(m.n) == 8 ? 0 : pk_bits(m.n);
+  const cudaError_t e = launch_k(vdk::k_stamp_min, dim3(blocks), dim3(256), st, pdl, labels, m.pitch, m.seeds, m.n,
+                                 pkm ? m.pkf : nullptr, m.ptable - 1, pkm);
   if (e != cudaSuccess) return vd_cuda_check(e, "stamp launch");
   ++*launches;
   return vd_cuda_check(cudaGetLastError(), "stamp launch");

@@ -137,9 +137,9 @@ struct PassArgs {
   int band_t;  // row-blocks per band residue class
   int y0, y_end;  // k_pass writes rows [y0, y_end) of dst (the whole map: 0, h)
   // position-tagged passes (wide layouts): n + 1 entries {x | y << 16, the
-  // seed's word bits but the label}, [0] the far position; written by a
-  // frame's first such pass for the ones after it
-  uint2* __restrict__ pkf;
+  // seed's word bits but the label}, [0] the far position; written by the
+  // frame's stamp (k_stamp_min)
+  const uint2* __restrict__ pkf;
 };
 
 // Stops the compiler from hoisting later loads above this point, which keeps
@@ -848,8 +848,13 @@ static __global__ void k_stamp_mark(int32_t* __restrict__ labels, int pitch, con
 
 // Stamp, second half: the lowest index standing on the pixel wins.  As
 // unsigned, -1 is the largest value, so this also stamps an emptied map.
+// With pk_m = 6 or 7 it also writes the frame's entries of the
+// position-tagged passes' seed table (pkf: n + 1 entries {x | y << 16, the
+// seed's word bits but the label}, [0] the far position; parena: the packed
+// positions with the far one first): the stamp runs right before every dJFA
+// frame's passes, after the move.
 static __global__ void k_stamp_min(int32_t* __restrict__ labels, int pitch, const int2* __restrict__ seeds,
-                            int n) {
+                            int n, uint2* __restrict__ pkf, const uint32_t* __restrict__ parena, int pk_m) {
   pdl_trigger();
   pdl_wait();
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -857,6 +862,15 @@ static __global__ void k_stamp_min(int32_t* __restrict__ labels, int pitch, cons
   const int2 p = seeds[k];
   atomicMin(reinterpret_cast<unsigned int*>(labels + static_cast<int64_t>(p.y) * pitch + p.x),
             static_cast<unsigned int>(k));
+  if (pk_m) {
+    // the word bits of layout pk_m (wide): bit 24 set, x mod 2^m at
+    // [24 - m, 24), y mod 2^m at [32 - m, 32)
+    const uint32_t xm = (1u << pk_m) - 1u;
+    const uint32_t f = (1u << 24) | ((static_cast<uint32_t>(p.x) & xm) << (24 - pk_m)) |
+                       ((static_cast<uint32_t>(p.y) & xm) << (32 - pk_m));
+    pkf[k + 1] = make_uint2(pack_pos(p.x, p.y), f);
+    if (k == 0) pkf[0] = make_uint2(parena[0], 0u);
+  }
 }
 
 static __global__ void k_fill(int4* __restrict__ p, int64_t n4, int v) {

@@ -154,8 +154,9 @@ __device__ __noinline__ void pk_exact_quad(const PassArgs a, int x0, int y) {
 // kw = h * 0x10001 - (x0 | y << 16), wmask = (0xFFFF & ~(2h - 1)) * 0x10001,
 // lim = h^2 << ks.  PKOUT: words of layout M from the keys (key form KF: 0
 // the plain byte-offset key, labels in the low lb bits; 1 this layout's;
-// 2 this layout's, wide, with each seed's word bits read from a.pkf beside
-// its position).  Returns false when the quad must be recomputed.
+// 2 either, labels in the low lb bits, with each seed's word bits of a wide
+// layout read from a.pkf beside its position, as the frame's stamp wrote
+// them).  Returns false when the quad must be recomputed.
 template <int M, int KF, bool PKOUT, bool IN>
 __device__ __forceinline__ bool pk_check_store(const PassArgs& a, const uint32_t (&b)[4], int x0, int y,
                                                uint32_t lm, uint32_t kw, uint32_t wmask, uint32_t lim) {
@@ -184,7 +185,13 @@ __device__ __forceinline__ bool pk_check_store(const PassArgs& a, const uint32_t
   uint32_t o[4];
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
-    if (PKOUT) o[i] = KF == 2 ? (b[i] & lm) | f[i] : KF == 1 ? F::word_of_key(b[i], e[i]) : F::word(b[i] & lm, e[i]);
+    // (the plain narrow key's label bytes are bytes 0 and 1, the second
+    // below 0x80: one byte permute and the guard bit)
+    if (PKOUT)
+      o[i] = KF == 2   ? (b[i] & lm) | f[i]
+             : KF == 1 ? F::word_of_key(b[i], e[i])
+             : M == 8  ? __byte_perm(b[i], e[i], 0x6140) | F::kG
+                       : F::word(b[i] & lm, e[i]);
     else o[i] = b[i] & lm;
     if (!IN && x0 + i >= a.w) o[i] = PKOUT ? F::kEmpty : 0xFFFFFFFFu;
   }
@@ -205,7 +212,8 @@ __device__ __forceinline__ void pk_first_quad(const PassArgs& a, int x0, int y) 
   const uint32_t kw = (kWide ? a.bwin_bias : h * 0x10001u) -
                       (static_cast<uint32_t>(x0) + (static_cast<uint32_t>(y) << 16));
   const uint32_t lim = kWide ? a.blim : (h * h) << 16;
-  if (!pk_check_store<M, 0, true, IN>(a, q.b, x0, y, lm, kw, wmask, lim))
+  // words of a wide layout take their bits from a.pkf
+  if (!pk_check_store<M, kWide ? 2 : 0, true, IN>(a, q.b, x0, y, lm, kw, wmask, lim))
     pk_exact_quad<NB, M, false, true>(a, x0, y);
 }
 
@@ -305,21 +313,10 @@ __device__ __noinline__ void pk_edge_quad(const PassArgs a, int x0, int y) {
 // k-strided bands when band_m > 1), and its block-uniform interior test.
 // MODE 0: plain map in, words out (DEDUP: the fold's gathers de-duplicated);
 // 1: words in and out; 2: words in, plain labels out.
-// MODE 0 of a wide layout also writes a.pkf (the seed positions of this
-// frame with their word bits) for the passes after it.
 template <int NB, int KSEL, int M, int MODE, bool DEDUP = false>
 __global__ void __launch_bounds__(kPassThreads, VD_PK_MIN_BLOCKS) k_pass_pk(PassArgs a) {
   pdl_trigger();
   pdl_wait();
-  if (MODE == 0 && M != 8) {
-    const uint32_t nt = gridDim.x * gridDim.y * blockDim.x * blockDim.y;
-    const uint32_t t0 = ((blockIdx.y * gridDim.x + blockIdx.x) * blockDim.y + threadIdx.y) * blockDim.x + threadIdx.x;
-    const uint32_t* __restrict__ arena = a.ptable - 1;
-    for (uint32_t j = t0; j <= a.n_seeds; j += nt) {
-      const uint32_t e = __ldg(&arena[j]);
-      a.pkf[j] = make_uint2(e, j == 0 ? 0u : Pk<M>::fields(e));
-    }
-  }
   const int x0 = 4 * static_cast<int>(blockIdx.x * blockDim.x + threadIdx.x);
   int rb = blockIdx.y;
   if (a.band_m > 1) rb = (blockIdx.y % a.band_t) * a.band_m + blockIdx.y / a.band_t;
