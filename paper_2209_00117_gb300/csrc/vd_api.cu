@@ -285,7 +285,7 @@ int launch_pass(const MapView& m, const int32_t* src, int32_t* dst, int32_t k, i
   const int quads = m.pitch / 4;
   const int tile = (pass_bx == 32 || pass_bx == 128) ? pass_bx : 64;
   const int bx = quads < tile ? quads : tile;
-  const int by = vdk::kPassThreads / bx;
+  const int by = (pk_m ? pk_threads(nb, pk_mode) : vdk::kPassThreads) / bx;
   const int nrb = (y1 - y0 + by - 1) / by;
   dim3 block(bx, by);
   dim3 grid((quads + bx - 1) / bx, nrb);

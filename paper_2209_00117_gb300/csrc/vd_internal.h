@@ -14,6 +14,13 @@ int vd_cuda_check(cudaError_t e, const char* what);
 
 namespace vdi {
 
+// Threads per block of a position-tagged pass (vd_pass_pk.cuh): 256 for the
+// Von Neumann passes on words, whose short-lived 128-thread blocks kept only
+// 61% of the warp slots filled (8192^2, 2^18 seeds, k = 16: 141 -> 129 us);
+// 128 for the rest (the first pass 200 -> 206 us and the Moore passes
+// 1-2 us slower at 256).
+constexpr int pk_threads(int nb, int mode) { return mode != 0 && nb == 1 ? 256 : 128; }
+
 // What a jump pass needs to know about one map.
 struct MapView {
   int32_t w = 0, h = 0, pitch = 0, n = 0;

@@ -107,12 +107,23 @@ __device__ __forceinline__ uint2 words2(const int32_t* p) { return __ldg(reinter
 // The exact recomputation of one quad (x0 .. x0 + 3, y): for each pixel the
 // least (distance^2, label) over its candidates (Table I / Section V-B),
 // candidates outside the map and empty ones skipped, read from a plain map
-// (PKIN false) or a packed one; written plain or packed (PKOUT).  Rare: out
-// of line (with the border blocks' path also out of line, measured 6% faster
-// a dJFA frame than either inline on the GB300).
+// (PKIN false) or a packed one; written plain or packed (PKOUT).  Per pixel
+// all candidate words are loaded at once, then all their seed positions, so
+// that a quad costs two memory round trips a pixel rather than two a
+// candidate: with 2^18 seeds on 8192^2 about 1.5% of the first pass's quads
+// land here (a seed beyond the +-32 window of a k = 32 neighbour aliasing
+// to a short offset), enough warps that a serial recomputation held their
+// blocks and dominated that pass.  Out of line (with the border blocks'
+// path also out of line, measured 6% faster a dJFA frame than either inline
+// on the GB300).
 template <int NB, int M, bool PKIN, bool PKOUT>
 __device__ __noinline__ void pk_exact_quad(const PassArgs a, int x0, int y) {
   using F = Pk<M>;
+  constexpr int kN = NB == kMoore ? 9 : 5;
+  // candidate offsets in units of k: the pixel, its four axis neighbours,
+  // then (Moore) the four diagonal ones
+  constexpr int kOx[9] = {0, -1, 1, 0, 0, -1, 1, -1, 1};
+  constexpr int kOy[9] = {0, 0, 0, -1, 1, -1, -1, 1, 1};
   uint32_t out[4];
 #pragma unroll 1
   for (int i = 0; i < 4; ++i) {
@@ -121,27 +132,34 @@ __device__ __noinline__ void pk_exact_quad(const PassArgs a, int x0, int y) {
       out[i] = PKOUT ? F::kEmpty : 0xFFFFFFFFu;
       continue;
     }
+    int lab[kN];
+#pragma unroll
+    for (int c = 0; c < kN; ++c) {
+      const int qx = x + kOx[c] * a.k, qy = y + kOy[c] * a.k;
+      const bool in = qx >= 0 && qx < a.w && qy >= 0 && qy < a.h;
+      const uint32_t wv = in ? static_cast<uint32_t>(__ldg(a.src + static_cast<int64_t>(qy) * a.pitch + qx))
+                             : 0xFFFFFFFFu;
+      lab[c] = !in ? -1 : PKIN ? F::label(wv) : static_cast<int>(wv);
+    }
+    uint32_t e[kN];
+#pragma unroll
+    for (int c = 0; c < kN; ++c) e[c] = lab[c] >= 0 ? __ldg(&a.ptable[lab[c]]) : 0u;
     unsigned long long best = ~0ull;
-#pragma unroll 1
-    for (int dy = -1; dy <= 1; ++dy) {
-#pragma unroll 1
-      for (int dx = -1; dx <= 1; ++dx) {
-        if (NB == kVonNeumann && dx != 0 && dy != 0) continue;
-        const int qx = x + dx * a.k, qy = y + dy * a.k;
-        if (qx < 0 || qx >= a.w || qy < 0 || qy >= a.h) continue;
-        const uint32_t wv = static_cast<uint32_t>(a.src[static_cast<int64_t>(qy) * a.pitch + qx]);
-        const int l = PKIN ? F::label(wv) : static_cast<int>(wv);
-        if (l < 0) continue;
-        const uint32_t e = static_cast<uint32_t>(a.table[l].x);
-        const int sx = static_cast<int>(e & 0xFFFFu) - x;
-        const int sy = static_cast<int>(e >> 16) - y;
-        const uint32_t d = static_cast<uint32_t>(sx * sx) + static_cast<uint32_t>(sy * sy);
-        const unsigned long long kk = (static_cast<unsigned long long>(d) << 32) | static_cast<uint32_t>(l);
-        best = kk < best ? kk : best;
+    uint32_t eb = 0;
+#pragma unroll
+    for (int c = 0; c < kN; ++c) {
+      if (lab[c] < 0) continue;
+      const int sx = static_cast<int>(e[c] & 0xFFFFu) - x;
+      const int sy = static_cast<int>(e[c] >> 16) - y;
+      const uint32_t d = static_cast<uint32_t>(sx * sx) + static_cast<uint32_t>(sy * sy);
+      const unsigned long long kk = (static_cast<unsigned long long>(d) << 32) | static_cast<uint32_t>(lab[c]);
+      if (kk < best) {
+        best = kk;
+        eb = e[c];
       }
     }
     const int l = best == ~0ull ? -1 : static_cast<int>(static_cast<uint32_t>(best));
-    if (PKOUT) out[i] = l < 0 ? F::kEmpty : F::word(static_cast<uint32_t>(l), static_cast<uint32_t>(a.table[l].x));
+    if (PKOUT) out[i] = l < 0 ? F::kEmpty : F::word(static_cast<uint32_t>(l), eb);
     else out[i] = static_cast<uint32_t>(l);
   }
   *reinterpret_cast<uint4*>(a.dst + static_cast<int64_t>(y) * a.pitch + x0) = make_uint4(out[0], out[1], out[2], out[3]);
@@ -309,12 +327,14 @@ __device__ __noinline__ void pk_edge_quad(const PassArgs a, int x0, int y) {
 #define VD_PK_MIN_BLOCKS 16
 #endif
 
+
 // The launch shape and row order of k_pass (128-thread blocks, row-blocks in
 // k-strided bands when band_m > 1), and its block-uniform interior test.
 // MODE 0: plain map in, words out (DEDUP: the fold's gathers de-duplicated);
 // 1: words in and out; 2: words in, plain labels out.
 template <int NB, int KSEL, int M, int MODE, bool DEDUP = false>
-__global__ void __launch_bounds__(kPassThreads, VD_PK_MIN_BLOCKS) k_pass_pk(PassArgs a) {
+__global__ void __launch_bounds__(vdi::pk_threads(NB, MODE), VD_PK_MIN_BLOCKS * 128 / vdi::pk_threads(NB, MODE))
+    k_pass_pk(PassArgs a) {
   pdl_trigger();
   pdl_wait();
   const int x0 = 4 * static_cast<int>(blockIdx.x * blockDim.x + threadIdx.x);
