@@ -273,8 +273,10 @@ def recorded_traffic(kind, workload_name):
     with open(p) as f:
         for line in f:
             t = line.split()
-            if len(t) >= 4 and not line.startswith("#") and t[0] == kind and t[1] == workload_name:
-                return float(t[2]) if t[3] == cur else None
+            # lines taken on earlier kernel source stay as history; the one
+            # whose hash matches the current source counts
+            if len(t) >= 4 and not line.startswith("#") and t[0] == kind and t[1] == workload_name and t[3] == cur:
+                return float(t[2])
     return None
 
 
