@@ -429,6 +429,13 @@ int vd_batch_step_subset(vd_batch* batch, const int32_t* sims, int32_t n, int32_
                                         on it */
 #define VD_BOPT_PERSISTENT_MIN_BLOCKS 9 /* persistent mode: register budget of the kernel, 4 (default, 64
                                         registers a thread) or 5 (48) resident 256-thread blocks per SM */
+#define VD_BOPT_PACKED_MAP 10        /* launch per round: -1 (default) = a simulation's dJFA frame runs its
+                                        last passes (at least two, k = 1, 2 or a multiple of 4 up to
+                                        128) on position-tagged words, as VD_OPT_PACKED_MAP does for
+                                        one simulation, where it has up to 32767 seeds and mean cells
+                                        of radius at most 40 pixels; 0 = never.  Takes effect at the
+                                        next vd_batch_configure.  The persistent mode runs every pass
+                                        on labels.  Results never depend on it */
 int vd_batch_set_option(vd_batch* batch, int32_t option, int64_t value);
 int vd_batch_get_option(const vd_batch* batch, int32_t option, int64_t* value);
 

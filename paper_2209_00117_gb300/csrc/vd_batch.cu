@@ -51,11 +51,13 @@ struct vd_batch {
   int clamp = -1;  // clamped 32-bit keys: -1 auto, 0 never, 1 whenever usable
   int persistent_byte = 1;  // persistent launch: byte-offset keys where the auto rules pick them
   int persistent_min_blocks = 4;  // persistent launch: register budget for 4 (64 registers) or 5 (48) blocks per SM
+  int packed = -1;  // launch per round: dJFA frames' last passes on position-tagged words (-1 auto, 0 never)
   int64_t launches = 0;
   // cached full-batch dJFA plan + graph
   int full_plan_valid = 0;
   cudaGraphExec_t full_graph = nullptr;
   int full_graph_given = -1;
+  int64_t full_graph_launches = 0;  // kernel launches one replay of it makes
   int32_t last_max_disp = -1;
   uint64_t last_rng_seed = 0;
   int sm_count = 0;
@@ -224,7 +226,7 @@ extern "C" vd_batch* vd_batch_create(int32_t n_sims, const int32_t* w, const int
     toff += s.n + 1;
     // JFA schedule (index 1); the dJFA one is filled by vd_batch_configure
     s.n_pass[1] = vdi::fill_schedule(vdi::jfa_first_step(s.w, s.h), 0, 0, s.ks[1], s.nbs[1], vdb::kMaxPasses);
-    vdb::set_clamp(s, 1, VD_METRIC_EUCLID, b->clamp);
+    vdb::set_clamp(s, 1, VD_METRIC_EUCLID, b->clamp, b->packed);
   }
   int rc = upload_sims(b);
   for (int i = 0; !rc && i < n_sims; ++i)
@@ -362,7 +364,7 @@ extern "C" int vd_batch_configure(vd_batch* b, int32_t d_max, int32_t vn_waves, 
   for (vdb::SimDesc& s : b->sims) {
     s.n_pass[0] = vdi::fill_schedule(vdi::djfa_first_step(s.w, s.h, s.n, d_max), vn_waves, extra, s.ks[0], s.nbs[0],
                                      vdb::kMaxPasses);
-    vdb::set_clamp(s, 0, metric, b->clamp);
+    vdb::set_clamp(s, 0, metric, b->clamp, b->packed);
   }
   b->d_max = d_max;
   b->vn_waves = vn_waves;
@@ -385,7 +387,7 @@ extern "C" int vd_batch_jfa(vd_batch* b, int32_t metric) {
   int rc = vd_batch_synchronize(b);
   if (!rc) rc = pull_state(b);
   if (rc) return rc;
-  for (vdb::SimDesc& s : b->sims) vdb::set_clamp(s, 1, metric, b->clamp);
+  for (vdb::SimDesc& s : b->sims) vdb::set_clamp(s, 1, metric, b->clamp, b->packed);
   rc = upload_sims(b);
   if (rc) return rc;
   // frame 0 of every simulation: empty both buffers' current map, stamp, JFA passes
@@ -427,7 +429,7 @@ static int batch_step(vd_batch* b, const std::vector<int>& act, bool given, int3
     // RNG parameters, which are per-launch: only replay when they match
     int rc = vd_cuda_check(cudaGraphLaunch(b->full_graph, b->stream), "graph launch");
     if (rc) return rc;
-    b->launches += 3 + p.rounds;
+    b->launches += b->full_graph_launches;
     return VD_OK;
   }
   int rc = upload_plan(b, p, &A);
@@ -439,6 +441,7 @@ static int batch_step(vd_batch* b, const std::vector<int>& act, bool given, int3
   const int64_t l0 = b->launches;
   const int lrc = launch_plan(b, p, A);
   const cudaError_t ee = cudaStreamEndCapture(b->stream, &g);
+  const int64_t captured = b->launches - l0;
   b->launches = l0;
   if (lrc) {
     if (g) cudaGraphDestroy(g);
@@ -453,9 +456,10 @@ static int batch_step(vd_batch* b, const std::vector<int>& act, bool given, int3
   drop_graph(b);
   b->full_graph = ex;
   b->full_graph_given = static_cast<int>(given);
+  b->full_graph_launches = captured;
   rc = vd_cuda_check(cudaGraphLaunch(ex, b->stream), "graph launch");
   if (rc) return rc;
-  b->launches += 3 + p.rounds;
+  b->launches += captured;
   return VD_OK;
 }
 
@@ -532,6 +536,11 @@ extern "C" int vd_batch_set_option(vd_batch* b, int32_t option, int64_t value) {
       if (value != 4 && value != 5) return vd_fail(VD_EINVAL, "persistent blocks per SM must be 4 or 5");
       b->persistent_min_blocks = static_cast<int>(value);
       break;
+    case VD_BOPT_PACKED_MAP:
+      if (value != -1 && value != 0) return vd_fail(VD_EINVAL, "packed map must be -1 (auto) or 0 (never)");
+      b->packed = static_cast<int>(value);
+      // takes effect at the next vd_batch_configure
+      break;
     default:
       return vd_fail(VD_EINVAL, "unknown batch option %d", option);
   }
@@ -552,6 +561,7 @@ extern "C" int vd_batch_get_option(const vd_batch* b, int32_t option, int64_t* v
     case VD_BOPT_CLAMPED_KEYS: *value = b->clamp; break;
     case VD_BOPT_PERSISTENT_BYTE_KEYS: *value = b->persistent_byte; break;
     case VD_BOPT_PERSISTENT_MIN_BLOCKS: *value = b->persistent_min_blocks; break;
+    case VD_BOPT_PACKED_MAP: *value = b->packed; break;
     default: return vd_fail(VD_EINVAL, "unknown batch option %d", option);
   }
   return VD_OK;

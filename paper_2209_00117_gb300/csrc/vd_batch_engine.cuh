@@ -19,6 +19,7 @@
 #include "vd.h"
 #include "vd_internal.h"
 #include "vd_kernels.cuh"
+#include "vd_pass_pk.cuh"
 
 namespace vdb {
 
@@ -36,6 +37,7 @@ struct SimDesc {
   uint32_t clampmask[2];   // bit r: pass r of the schedule uses clamped keys
   uint32_t bytemask[2];    // bit r: pass r uses the byte-offset key (its fallback: the clamped one)
   int dedup[2];            // 1: the schedule's passes de-duplicate repeated table gathers
+  int pk_first[2];         // passes [pk_first, n_pass) run on position-tagged words (n_pass: none)
   int seed_off;
   int cur;
   long long step;      // moves drawn so far (the RNG step of the next move)
@@ -210,7 +212,54 @@ __device__ __forceinline__ void tile_quad8(const vdk::PassArgs& a, int x0, int y
   }
 }
 
-template <int METRIC, bool COH>
+// A thread's quads of one tile on position-tagged words (the narrow layout,
+// up to 32767 seeds, as the single-simulation passes of vd_pass_pk.cuh):
+// rows ybase, ybase + 4, ... (n_rows of them).  MODE 0: the frame's first
+// such pass (labels in, words out); 1 words to words; 2 the last (words in,
+// labels out).  `in`: the tile and every neighbour at offset k lie inside
+// the map (no range tests; tiles at the border take the out-of-line path).
+// One function per combination, out of line, so that each keeps a register
+// allocation of its own inside the dispatching kernel.
+template <int NB, int KS, int MODE, bool DEDUP>
+__device__ __noinline__ void pk_tile_rows(const vdk::PassArgs a, int x0, int ybase, int n_rows, bool in) {
+  for (int i = 0; i < n_rows; ++i) {
+    const int y = ybase + 4 * i;
+    if (x0 >= a.pitch || y >= a.h) continue;
+    if (!in) vdk::pk_edge_quad<NB, KS, 8, MODE, DEDUP>(a, x0, y);
+    else if (MODE == 0) vdk::pk_first_quad<NB, KS, 8, DEDUP, true>(a, x0, y);
+    else vdk::pk_quad<NB, KS, 8, MODE == 1, true>(a, x0, y);
+  }
+}
+
+template <int NB, int KS>
+__device__ __forceinline__ void pk_tile_nb(const vdk::PassArgs& a, int x0, int ybase, int n_rows, int mode,
+                                           bool dedup, bool in) {
+  if (mode == 0) {
+    if (dedup) pk_tile_rows<NB, KS, 0, true>(a, x0, ybase, n_rows, in);
+    else pk_tile_rows<NB, KS, 0, false>(a, x0, ybase, n_rows, in);
+  } else if (mode == 1) {
+    pk_tile_rows<NB, KS, 1, false>(a, x0, ybase, n_rows, in);
+  } else {
+    pk_tile_rows<NB, KS, 2, false>(a, x0, ybase, n_rows, in);
+  }
+}
+
+__device__ __forceinline__ void pk_tile(const vdk::PassArgs& a, int x0, int ybase, int n_rows, int nb, int ksel,
+                                        int mode, bool dedup, bool in) {
+  switch (nb * 4 + ksel) {
+    case 0: pk_tile_nb<vdk::kMoore, 0>(a, x0, ybase, n_rows, mode, dedup, in); break;
+    case 1: pk_tile_nb<vdk::kMoore, 1>(a, x0, ybase, n_rows, mode, dedup, in); break;
+    case 2: pk_tile_nb<vdk::kMoore, 2>(a, x0, ybase, n_rows, mode, dedup, in); break;
+    case 4: pk_tile_nb<vdk::kVonNeumann, 0>(a, x0, ybase, n_rows, mode, dedup, in); break;
+    case 5: pk_tile_nb<vdk::kVonNeumann, 1>(a, x0, ybase, n_rows, mode, dedup, in); break;
+    default: pk_tile_nb<vdk::kVonNeumann, 2>(a, x0, ybase, n_rows, mode, dedup, in); break;
+  }
+}
+
+// PK: the tile belongs to a simulation whose pass r runs on position-tagged
+// words (the first tiles of each round, launched apart so that the packed
+// code keeps its own register allocation); otherwise it runs on labels.
+template <int METRIC, bool COH, bool PK = false>
 __device__ __forceinline__ void round_tile(const BatchArgs& A, int r, int t) {
   // the entry holding tile t: the last one whose first tile is <= t
   int lo = A.round_off[r], hi = A.round_off[r + 1] - 1;
@@ -250,6 +299,17 @@ __device__ __forceinline__ void round_tile(const BatchArgs& A, int r, int t) {
   const bool dedup = sd->dedup[A.sched] != 0;
   const bool mcap = sd->mul > (1u << 15);
   const bool byte = (COH ? A.coh_byte : true) && METRIC == vdk::kEuclid && ((sd->bytemask[A.sched] >> r) & 1u);
+  // position-tagged words: launch per round only (the persistent kernel's
+  // loads after a grid barrier go through its coherent path, these do not;
+  // it runs every pass on labels, so each mode is consistent on its own)
+  if (PK) {
+    const int pkf = sd->pk_first[A.sched];
+    const int mode = r == pkf ? 0 : (r == sd->n_pass[A.sched] - 1 ? 2 : 1);
+    const int xb = 4 * tx * kQuadsX, yb = ty * rows;
+    const bool in = xb - k >= 0 && xb + 4 * kQuadsX + k <= a.w && yb - k >= 0 && yb + rows + k <= a.h;
+    pk_tile(a, x0, yb + static_cast<int>(threadIdx.x / kQuadsX), A.rows_per_thread, nb, ksel, mode, dedup, in);
+    return;
+  }
   for (int i = 0; i < A.rows_per_thread; ++i) {
     const int y = ty * rows + static_cast<int>(threadIdx.x / kQuadsX) + 4 * i;
     if (x0 >= a.pitch || y >= a.h) continue;
@@ -278,9 +338,16 @@ static __global__ void __launch_bounds__(kThreads) k_batch_move_mark(BatchArgs A
 
 static __global__ void __launch_bounds__(kThreads) k_batch_min(BatchArgs A) { stamp_min_block(A, blockIdx.x); }
 
+// Round r's tiles from t0 on (the ones on labels).
 template <int METRIC>
-__global__ void __launch_bounds__(kThreads, 5) k_batch_round(BatchArgs A, int r) {
-  round_tile<METRIC, false>(A, r, blockIdx.x);
+__global__ void __launch_bounds__(kThreads, 5) k_batch_round(BatchArgs A, int r, int t0) {
+  round_tile<METRIC, false>(A, r, t0 + static_cast<int>(blockIdx.x));
+}
+
+// Round r's first tiles: simulations whose pass r runs on position-tagged
+// words (Euclidean), at the 32 registers of the single-simulation passes.
+static __global__ void __launch_bounds__(kThreads, 8) k_batch_round_pk(BatchArgs A, int r) {
+  round_tile<vdk::kEuclid, false, true>(A, r, blockIdx.x);
 }
 
 static __global__ void k_batch_finish(BatchArgs A) {
@@ -318,6 +385,7 @@ struct HostPlan {
   std::vector<int> act;
   std::vector<int2> sblk;
   std::vector<int> round_tiles, round_off;
+  std::vector<int> pk_tiles;  // per round: its first tiles, of simulations on position-tagged words
   std::vector<int2> entries;
   int rounds = 0;
   int64_t pixel_passes = 0;
@@ -341,12 +409,16 @@ inline HostPlan make_plan(const std::vector<SimDesc>& sims, const std::vector<in
   p.round_off.push_back(0);
   for (int r = 0; r < p.rounds; ++r) {
     int t = 0;
-    for (int i : act) {
-      const SimDesc& s = sims[i];
-      if (s.n_pass[sched] > r) {
-        p.entries.push_back(make_int2(i, t));
-        t += tiles_of(s, rpt);
+    // simulations whose pass r runs on words first, then the rest
+    for (int on_words = 1; on_words >= 0; --on_words) {
+      for (int i : act) {
+        const SimDesc& s = sims[i];
+        if (s.n_pass[sched] > r && (s.pk_first[sched] <= r) == (on_words != 0)) {
+          p.entries.push_back(make_int2(i, t));
+          t += tiles_of(s, rpt);
+        }
       }
+      if (on_words) p.pk_tiles.push_back(t);
     }
     p.round_tiles.push_back(t);
     p.round_off.push_back(static_cast<int>(p.entries.size()));
@@ -359,7 +431,7 @@ inline HostPlan make_plan(const std::vector<SimDesc>& sims, const std::vector<in
 // schedule (sched 0 = dJFA, 1 = JFA) under `metric`.
 // Per-schedule key form (clamped 32-bit or exact, per pass) and gather
 // de-duplication (the single-simulation auto rules).
-inline void set_clamp(SimDesc& s, int sched, int32_t metric, int clamp_option) {
+inline void set_clamp(SimDesc& s, int sched, int32_t metric, int clamp_option, int packed_option = -1) {
   const int lb = vdi::label_bits(s.n);
   s.mul = lb >= 32 ? 0u : (1u << lb);
   s.cap = lb >= 4 ? static_cast<uint32_t>((uint64_t{1} << (32 - lb)) - 1) : 0u;
@@ -383,6 +455,19 @@ inline void set_clamp(SimDesc& s, int sched, int32_t metric, int clamp_option) {
     }
   }
   s.bytemask[sched] = bmask;
+  // Position-tagged words (launch-per-round mode): the dJFA frame's last
+  // passes with k = 1, 2 or a multiple of 4 up to 128, at least two of them,
+  // under the byte-offset key's mean-radius bound, up to 32767 seeds (the
+  // narrow layout, packed from the position table alone).  packed_option:
+  // -1 auto, 0 never.
+  int pkf = s.n_pass[sched];
+  if (sched == 0 && packed_option != 0 && metric == VD_METRIC_EUCLID && vdi::pk_bits(s.n) == 8 && lb >= 4 &&
+      small_cells) {
+    auto ok = [](int k) { return (k == 1 || k == 2 || k % 4 == 0) && k <= 128; };
+    while (pkf > 0 && ok(s.ks[sched][pkf - 1])) --pkf;
+    if (s.n_pass[sched] - pkf < 2) pkf = s.n_pass[sched];
+  }
+  s.pk_first[sched] = pkf;
 }
 
 // A pinned host staging buffer and a device buffer for one plan.
@@ -462,11 +547,16 @@ inline int launch_rounds(const HostPlan& p, const BatchArgs& A, int metric, cuda
     ++*launches;
   }
   for (int r = 0; r < p.rounds; ++r) {
-    if (p.round_tiles[r] == 0) continue;
+    const int pk = p.pk_tiles[r], rest = p.round_tiles[r] - pk;
+    if (pk > 0) {
+      k_batch_round_pk<<<pk, kThreads, 0, st>>>(A, r);
+      ++*launches;
+    }
+    if (rest <= 0) continue;
     if (metric == VD_METRIC_MANHATTAN)
-      k_batch_round<vdk::kManhattan><<<p.round_tiles[r], kThreads, 0, st>>>(A, r);
+      k_batch_round<vdk::kManhattan><<<rest, kThreads, 0, st>>>(A, r, pk);
     else
-      k_batch_round<vdk::kEuclid><<<p.round_tiles[r], kThreads, 0, st>>>(A, r);
+      k_batch_round<vdk::kEuclid><<<rest, kThreads, 0, st>>>(A, r, pk);
     ++*launches;
   }
   if (A.n_act > 0) {

@@ -374,6 +374,7 @@ BOPT_TEST_SKIP_ARRIVE = 6
 BOPT_CLAMPED_KEYS = 7
 BOPT_PERSISTENT_BYTE_KEYS = 8
 BOPT_PERSISTENT_MIN_BLOCKS = 9
+BOPT_PACKED_MAP = 10
 
 
 class VoronoiBatch:

@@ -44,13 +44,17 @@ def _alone_rng(vd, shape, xy, sim_index, steps, D, rng_seed, metric=0):
     return out
 
 
-@pytest.mark.parametrize("mode,graphs,rpt,bps,pbyte,minb", [(0, 0, 1, 0, 1, 4), (0, 1, 1, 0, 1, 4), (0, 1, 2, 0, 1, 4),
-                                                             (1, 0, 1, 0, 1, 4), (1, 0, 4, 0, 1, 4), (1, 0, 1, 2, 1, 4),
-                                                             (1, 0, 2, 3, 1, 4), (1, 0, 1, 0, 0, 4), (1, 0, 2, 0, 1, 5)])
-def test_batch_equals_alone_rng(vd, mode, graphs, rpt, bps, pbyte, minb):
+@pytest.mark.parametrize("mode,graphs,rpt,bps,pbyte,minb,packed", [
+    (0, 0, 1, 0, 1, 4, -1), (0, 1, 1, 0, 1, 4, -1), (0, 1, 2, 0, 1, 4, -1), (0, 1, 1, 0, 1, 4, 0),
+    (1, 0, 1, 0, 1, 4, -1), (1, 0, 4, 0, 1, 4, -1), (1, 0, 1, 2, 1, 4, -1), (1, 0, 2, 3, 1, 4, -1),
+    (1, 0, 1, 0, 0, 4, -1), (1, 0, 2, 0, 1, 5, -1)])
+def test_batch_equals_alone_rng(vd, mode, graphs, rpt, bps, pbyte, minb, packed):
     """Every launch shape the batch autotuner tries (per-round or persistent,
     rows per thread, persistent blocks per SM) gives each simulation exactly
-    its alone run."""
+    its alone run.  Per round, the simulations with up to 32767 seeds and
+    small cells run their dJFA frames' last passes on position-tagged words
+    (packed = -1), here against alone runs on plain passes (maps below the
+    single simulation's 2^21-pixel bound), and also with that off."""
     import torch
 
     D, steps, rng = 2, 3, 99
@@ -63,6 +67,8 @@ def test_batch_equals_alone_rng(vd, mode, graphs, rpt, bps, pbyte, minb):
     b.set_option(vd.BOPT_BLOCKS_PER_SM, bps)
     b.set_option(vd.BOPT_PERSISTENT_BYTE_KEYS, pbyte)
     b.set_option(vd.BOPT_PERSISTENT_MIN_BLOCKS, minb)
+    b.set_option(vd.BOPT_PACKED_MAP, packed)
+    assert b.get_option(vd.BOPT_PACKED_MAP) == packed
     b.set_seeds(np.concatenate(xys))
     b.jfa()
     b.configure(d_max=D)
