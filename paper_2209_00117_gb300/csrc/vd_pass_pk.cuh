@@ -26,7 +26,8 @@
 // masked out of the word and one multiply-add) or d * 2^16 + 2^15 + label
 // (narrow: one byte permute of the word and d).  Per candidate: a subtraction,
 // a mask, the dp4a, the key pack (wide: and the label mask) and a minimum; no
-// gather.  Every key lies below 2^31.
+// gather.  No key wraps: wide keys lie below 2^31, narrow ones hold d <= 2^15
+// in their upper 16 bits (keys compare as unsigned).
 //
 // Outside the window the fields alias and a key may be anything, and the
 // byte-offset pass's winner check applies unchanged: each pixel's winner is
