@@ -606,7 +606,7 @@ int vd_server_set_max_batch(vd_server* server, int32_t max_batch);
                                     a multiple of 4) take the byte-offset key run them on a
                                     position-tagged map: each 32-bit word holds the label and the
                                     low 6, 7 or 8 bits of its seed's x and y (up to 32767 seeds,
-                                    2^16 to 2^17 - 1, 2^17 to 2^18), so that a candidate is scored
+                                    32768 to 2^17 - 1, 2^17 to 2^18), so that a candidate is scored
                                     with no table gather; the first of those passes reads the plain
                                     map and the last writes it again.  -1 = auto (default: the
                                     byte-offset key's mean-radius and step bounds with the

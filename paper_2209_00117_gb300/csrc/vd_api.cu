@@ -311,7 +311,9 @@ int launch_pass(const MapView& m, const int32_t* src, int32_t* dst, int32_t k, i
   if (byte_key && metric == VD_METRIC_EUCLID && a.cap != 0 && a.bwin_bias != 0) key = m.n < 65536 ? 3 : 4;
   // the position-tagged passes of a dJFA frame (chosen by run_passes)
   if (pk_m) {
-    if (rows_only || ksel > 2 || (pk_mode == 0 && key != (pk_m == 8 ? 3 : 4)))
+    // the first pass folds with a byte-offset key (the narrow one for the
+    // 8-bit layout; either for the wide ones)
+    if (rows_only || ksel > 2 || (pk_mode == 0 && (key < 3 || (pk_m == 8 && key != 3))))
       return vd_fail(VD_EINVAL, "packed pass: step %d, key form %d, layout %d", k, key, pk_m);
     return launch_pass_pk(a, grid, block, nb, pk_m, ksel, pk_mode, dedup, st, pdl);
   }

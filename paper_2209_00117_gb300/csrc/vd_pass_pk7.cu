@@ -1,5 +1,5 @@
 // vd_pass_pk7.cu -- the position-tagged dJFA passes of layout M = 7
-// (2^16 to 2^17 - 1 seeds, window +-64); one translation unit per layout so that they compile in
+// (32768 to 2^17 - 1 seeds, window +-64); one translation unit per layout so that they compile in
 // parallel.
 #include "vd_pass_pk.cuh"
 

@@ -13,9 +13,11 @@ template int launch_pass_pk_m<8>(const vdk::PassArgs&, dim3, dim3, int32_t, int,
 
 int pk_bits(int32_t n) {
   // the label code 2^lb - 1 marks an empty pixel: below it for M = 7 and 8;
-  // M = 6 carries a separate empty bit and so takes up to 2^18 labels
+  // M = 6 carries a separate empty bit and so takes up to 2^18 labels.  (M = 7
+  // below 2^16 seeds: the frame's first pass folds with the narrow byte-offset
+  // key, whose 16-bit label field the word bits then follow.)
   if (n >= 1 && n <= 32767) return 8;
-  if (n >= 65536 && n <= 131071) return 7;
+  if (n >= 32768 && n <= 131071) return 7;
   if (n >= 131072 && n <= 262144) return 6;
   return 0;
 }

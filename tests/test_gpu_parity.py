@@ -921,9 +921,9 @@ def test_smem_tile_auto_matches_plain_at_full_size(vd, orc, s, D):
 def test_packed_map_frames(vd, orc, w, h, s):
     """dJFA frames whose byte-key passes run on position-tagged words (forced
     on) against the oracle, for each word layout: up to 32767 seeds (8-bit
-    position fields), 2^16 .. 2^17 - 1 (7-bit), 2^17 .. 2^18 (6-bit, where the
-    last seed's label code is also the empty code); 40000 seeds fit no layout
-    and keep the plain passes.  Frames after the JFA frame with moves, extra
+    position fields), 32768 .. 2^17 - 1 (7-bit; below 2^16 seeds, as 40000,
+    the frame's first pass folds with the narrow byte-offset key), 2^17 ..
+    2^18 (6-bit, where the last seed's label code is also the empty code).  Frames after the JFA frame with moves, extra
     passes and no Von Neumann waves, then frames stamped onto random maps with
     and without empty labels: nearly every quad there fails the winner check
     and is recomputed, and empty pixels cross the packed passes.  Ragged

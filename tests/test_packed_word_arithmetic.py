@@ -1,6 +1,6 @@
 """Host-side check of the position-tagged words' arithmetic (the dJFA passes
 of vd_pass_pk.cuh), written out with numpy integer operations for each word
-layout M (8: up to 32767 seeds; 7 and 6: the wide ones):
+layout M (8: up to 32767 seeds; 7: to 2^17 - 1; 6: to 2^18):
 
 * a pixel's key of a candidate word is exactly d * 2^ks (+ 2^15 for M = 8)
   + label whenever the candidate's seed lies in the window [-h, h)^2 around
