@@ -31,6 +31,7 @@ struct vd_batch {
   int2* seeds = nullptr;
   int2* tables = nullptr;
   uint32_t* ptables = nullptr;
+  uint2* pkfs = nullptr;  // seed entries of the wide position-tagged layouts, n + 1 per simulation
   int2* dxy_stage = nullptr;
   int64_t total_seeds = 0;
   int64_t total_pixels = 0;
@@ -123,6 +124,7 @@ void batch_free(vd_batch* b) {
   cudaFree(b->seeds);
   cudaFree(b->tables);
   cudaFree(b->ptables);
+  cudaFree(b->pkfs);
   cudaFree(b->dxy_stage);
   cudaFree(b->bar);
   cudaFree(b->flag);
@@ -197,6 +199,7 @@ extern "C" vd_batch* vd_batch_create(int32_t n_sims, const int32_t* w, const int
   if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&b->seeds), sizeof(int2) * seeds);
   if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&b->tables), sizeof(int2) * (seeds + n_sims));
   if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&b->ptables), sizeof(uint32_t) * (seeds + n_sims));
+  if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&b->pkfs), sizeof(uint2) * (seeds + n_sims));
   if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&b->dxy_stage), sizeof(int2) * seeds);
   if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&b->d_sims), sizeof(vdb::SimDesc) * n_sims);
   if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&b->bar), sizeof(vdb::Barrier));
@@ -223,6 +226,9 @@ extern "C" vd_batch* vd_batch_create(int32_t n_sims, const int32_t* w, const int
     s.seeds = b->seeds + s.seed_off;
     s.table = b->tables + toff;
     s.ptable = b->ptables + toff;
+    s.pkf = b->pkfs + toff;
+    s.pk_m = 0;
+    s.pk_first[0] = 0;
     toff += s.n + 1;
     // JFA schedule (index 1); the dJFA one is filled by vd_batch_configure
     s.n_pass[1] = vdi::fill_schedule(vdi::jfa_first_step(s.w, s.h), 0, 0, s.ks[1], s.nbs[1], vdb::kMaxPasses);

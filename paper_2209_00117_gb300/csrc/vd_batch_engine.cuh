@@ -19,7 +19,6 @@
 #include "vd.h"
 #include "vd_internal.h"
 #include "vd_kernels.cuh"
-#include "vd_pass_pk.cuh"
 
 namespace vdb {
 
@@ -38,6 +37,9 @@ struct SimDesc {
   uint32_t bytemask[2];    // bit r: pass r uses the byte-offset key (its fallback: the clamped one)
   int dedup[2];            // 1: the schedule's passes de-duplicate repeated table gathers
   int pk_first[2];         // passes [pk_first, n_pass) run on position-tagged words (n_pass: none)
+  int pk_m;                // their word layout (8, 7 or 6; 0: none), dJFA schedule
+  uint2* pkf;              // n + 1 seed entries of the wide layouts, [0] far; written by the stamp
+  uint32_t bmul, bwin_bias, bwin_mask, blim;  // byte-offset key of the first such pass (PassArgs fields)
   int seed_off;
   int cur;
   long long step;      // moves drawn so far (the RNG step of the next move)
@@ -164,6 +166,16 @@ __device__ __forceinline__ void stamp_min_block(const BatchArgs& A, int sb) {
   const int2 p = sd->seeds[k];
   atomicMin(reinterpret_cast<unsigned int*>(sd->map[sd->cur] + static_cast<int64_t>(p.y) * sd->pitch + p.x),
             static_cast<unsigned int>(k));
+  // the seed entries of a wide word layout (as k_stamp_min: bit 24 set, x and
+  // y modulo 2^m at [24 - m, 24) and [32 - m, 32)), for this step's passes
+  const int m = A.sched == 0 ? sd->pk_m : 0;
+  if (m == 6 || m == 7) {
+    const uint32_t xm = (1u << m) - 1u;
+    const uint32_t f = (1u << 24) | ((static_cast<uint32_t>(p.x) & xm) << (24 - m)) |
+                       ((static_cast<uint32_t>(p.y) & xm) << (32 - m));
+    sd->pkf[k + 1] = make_uint2(vdk::pack_pos(p.x, p.y), f);
+    if (k == 0) sd->pkf[0] = make_uint2(sd->ptable[0], 0u);
+  }
 }
 
 // One quad of a pass in a 32-bit key form, dispatched on the neighbourhood and step.
@@ -212,56 +224,14 @@ __device__ __forceinline__ void tile_quad8(const vdk::PassArgs& a, int x0, int y
   }
 }
 
-// A thread's quads of one tile on position-tagged words (the narrow layout,
-// up to 32767 seeds, as the single-simulation passes of vd_pass_pk.cuh):
-// rows ybase, ybase + 4, ... (n_rows of them).  MODE 0: the frame's first
-// such pass (labels in, words out); 1 words to words; 2 the last (words in,
-// labels out).  `in`: the tile and every neighbour at offset k lie inside
-// the map (no range tests; tiles at the border take the out-of-line path).
-// One function per combination, out of line, so that each keeps a register
-// allocation of its own inside the dispatching kernel.
-template <int NB, int KS, int MODE, bool DEDUP>
-__device__ __noinline__ void pk_tile_rows(const vdk::PassArgs a, int x0, int ybase, int n_rows, bool in) {
-  for (int i = 0; i < n_rows; ++i) {
-    const int y = ybase + 4 * i;
-    if (x0 >= a.pitch || y >= a.h) continue;
-    if (!in) vdk::pk_edge_quad<NB, KS, 8, MODE, DEDUP>(a, x0, y);
-    else if (MODE == 0) vdk::pk_first_quad<NB, KS, 8, DEDUP, true>(a, x0, y);
-    else vdk::pk_quad<NB, KS, 8, MODE == 1, true>(a, x0, y);
-  }
-}
+// Round r's tile t: its simulation and tile coordinates (the entry holding
+// tile t is the last one whose first tile is <= t).
+struct TileAt {
+  const SimDesc* sd;
+  int tx, ty;
+};
 
-template <int NB, int KS>
-__device__ __forceinline__ void pk_tile_nb(const vdk::PassArgs& a, int x0, int ybase, int n_rows, int mode,
-                                           bool dedup, bool in) {
-  if (mode == 0) {
-    if (dedup) pk_tile_rows<NB, KS, 0, true>(a, x0, ybase, n_rows, in);
-    else pk_tile_rows<NB, KS, 0, false>(a, x0, ybase, n_rows, in);
-  } else if (mode == 1) {
-    pk_tile_rows<NB, KS, 1, false>(a, x0, ybase, n_rows, in);
-  } else {
-    pk_tile_rows<NB, KS, 2, false>(a, x0, ybase, n_rows, in);
-  }
-}
-
-__device__ __forceinline__ void pk_tile(const vdk::PassArgs& a, int x0, int ybase, int n_rows, int nb, int ksel,
-                                        int mode, bool dedup, bool in) {
-  switch (nb * 4 + ksel) {
-    case 0: pk_tile_nb<vdk::kMoore, 0>(a, x0, ybase, n_rows, mode, dedup, in); break;
-    case 1: pk_tile_nb<vdk::kMoore, 1>(a, x0, ybase, n_rows, mode, dedup, in); break;
-    case 2: pk_tile_nb<vdk::kMoore, 2>(a, x0, ybase, n_rows, mode, dedup, in); break;
-    case 4: pk_tile_nb<vdk::kVonNeumann, 0>(a, x0, ybase, n_rows, mode, dedup, in); break;
-    case 5: pk_tile_nb<vdk::kVonNeumann, 1>(a, x0, ybase, n_rows, mode, dedup, in); break;
-    default: pk_tile_nb<vdk::kVonNeumann, 2>(a, x0, ybase, n_rows, mode, dedup, in); break;
-  }
-}
-
-// PK: the tile belongs to a simulation whose pass r runs on position-tagged
-// words (the first tiles of each round, launched apart so that the packed
-// code keeps its own register allocation); otherwise it runs on labels.
-template <int METRIC, bool COH, bool PK = false>
-__device__ __forceinline__ void round_tile(const BatchArgs& A, int r, int t) {
-  // the entry holding tile t: the last one whose first tile is <= t
+__device__ __forceinline__ TileAt tile_at(const BatchArgs& A, int r, int t) {
   int lo = A.round_off[r], hi = A.round_off[r + 1] - 1;
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
@@ -269,12 +239,17 @@ __device__ __forceinline__ void round_tile(const BatchArgs& A, int r, int t) {
     else hi = mid - 1;
   }
   const int2 e = A.entries[lo];
-  const SimDesc* sd = A.sims + e.x;
+  TileAt at;
+  at.sd = A.sims + e.x;
   const int lt = t - e.y;
-  const int tiles_x = (sd->pitch + 4 * kQuadsX - 1) / (4 * kQuadsX);
-  const int tx = lt % tiles_x, ty = lt / tiles_x;
-  const int k = sd->ks[A.sched][r];
-  const int nb = sd->nbs[A.sched][r];
+  const int tiles_x = (at.sd->pitch + 4 * kQuadsX - 1) / (4 * kQuadsX);
+  at.tx = lt % tiles_x;
+  at.ty = lt / tiles_x;
+  return at;
+}
+
+// The single-simulation pass arguments of simulation sd's pass r.
+__device__ __forceinline__ vdk::PassArgs round_args(const SimDesc* sd, int sched, int r) {
   vdk::PassArgs a;
   a.src = sd->map[(sd->cur + r) & 1];
   a.dst = sd->map[(sd->cur + r + 1) & 1];
@@ -282,36 +257,41 @@ __device__ __forceinline__ void round_tile(const BatchArgs& A, int r, int t) {
   a.ptable = sd->ptable + 1;
   a.cap = sd->cap;
   a.mul = sd->mul;
-  a.bmul = 1u << 16;
+  a.bmul = sd->bmul;
+  a.bwin_bias = sd->bwin_bias;
+  a.bwin_mask = sd->bwin_mask;
+  a.blim = sd->blim;
+  a.pkf = sd->pkf;
   a.n_seeds = static_cast<uint32_t>(sd->n);
   a.w = sd->w;
   a.h = sd->h;
   a.y0 = 0;
   a.y_end = sd->h;
   a.pitch = sd->pitch;
-  a.k = k;
+  a.k = sd->ks[sched][r];
   a.band_m = 1;
   a.band_t = 1;
-  const int x0 = 4 * (tx * kQuadsX + static_cast<int>(threadIdx.x % kQuadsX));
+  return a;
+}
+
+// A tile of a pass on labels.  (Tiles of passes on position-tagged words run
+// in k_batch_round_pk, vd_batch_pk.cuh.)
+template <int METRIC, bool COH>
+__device__ __forceinline__ void round_tile(const BatchArgs& A, int r, int t) {
+  const TileAt at = tile_at(A, r, t);
+  const SimDesc* sd = at.sd;
+  const vdk::PassArgs a = round_args(sd, A.sched, r);
+  const int k = a.k;
+  const int nb = sd->nbs[A.sched][r];
+  const int x0 = 4 * (at.tx * kQuadsX + static_cast<int>(threadIdx.x % kQuadsX));
   const int ksel = (k == 1) ? 1 : (k == 2 ? 2 : 0);
   const bool clamp = (sd->clampmask[A.sched] >> r) & 1u;
   const int rows = 4 * A.rows_per_thread;
   const bool dedup = sd->dedup[A.sched] != 0;
   const bool mcap = sd->mul > (1u << 15);
   const bool byte = (COH ? A.coh_byte : true) && METRIC == vdk::kEuclid && ((sd->bytemask[A.sched] >> r) & 1u);
-  // position-tagged words: launch per round only (the persistent kernel's
-  // loads after a grid barrier go through its coherent path, these do not;
-  // it runs every pass on labels, so each mode is consistent on its own)
-  if (PK) {
-    const int pkf = sd->pk_first[A.sched];
-    const int mode = r == pkf ? 0 : (r == sd->n_pass[A.sched] - 1 ? 2 : 1);
-    const int xb = 4 * tx * kQuadsX, yb = ty * rows;
-    const bool in = xb - k >= 0 && xb + 4 * kQuadsX + k <= a.w && yb - k >= 0 && yb + rows + k <= a.h;
-    pk_tile(a, x0, yb + static_cast<int>(threadIdx.x / kQuadsX), A.rows_per_thread, nb, ksel, mode, dedup, in);
-    return;
-  }
   for (int i = 0; i < A.rows_per_thread; ++i) {
-    const int y = ty * rows + static_cast<int>(threadIdx.x / kQuadsX) + 4 * i;
+    const int y = at.ty * rows + static_cast<int>(threadIdx.x / kQuadsX) + 4 * i;
     if (x0 >= a.pitch || y >= a.h) continue;
     if (byte) {
       if (dedup) tile_quad8<COH, true>(a, x0, y, nb, ksel);
@@ -344,11 +324,9 @@ __global__ void __launch_bounds__(kThreads, 5) k_batch_round(BatchArgs A, int r,
   round_tile<METRIC, false>(A, r, t0 + static_cast<int>(blockIdx.x));
 }
 
-// Round r's first tiles: simulations whose pass r runs on position-tagged
-// words (Euclidean), at the 32 registers of the single-simulation passes.
-static __global__ void __launch_bounds__(kThreads, 8) k_batch_round_pk(BatchArgs A, int r) {
-  round_tile<vdk::kEuclid, false, true>(A, r, blockIdx.x);
-}
+// Round r's tiles [t0, t0 + n_tiles), all of simulations whose pass r runs on
+// position-tagged words of layout m (8, 7, 6): vd_batch_pk<m>.cu.
+int launch_round_pk(int m, const BatchArgs& A, int r, int t0, int n_tiles, cudaStream_t st);
 
 static __global__ void k_batch_finish(BatchArgs A) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -385,7 +363,9 @@ struct HostPlan {
   std::vector<int> act;
   std::vector<int2> sblk;
   std::vector<int> round_tiles, round_off;
-  std::vector<int> pk_tiles;  // per round: its first tiles, of simulations on position-tagged words
+  // per word layout (8, 7, 6) and round: the round's first tiles, of
+  // simulations whose pass r runs on words of that layout, in that order
+  std::vector<int> pk_tiles[3];
   std::vector<int2> entries;
   int rounds = 0;
   int64_t pixel_passes = 0;
@@ -409,16 +389,19 @@ inline HostPlan make_plan(const std::vector<SimDesc>& sims, const std::vector<in
   p.round_off.push_back(0);
   for (int r = 0; r < p.rounds; ++r) {
     int t = 0;
-    // simulations whose pass r runs on words first, then the rest
-    for (int on_words = 1; on_words >= 0; --on_words) {
+    // simulations whose pass r runs on words of layout 8, 7, 6, then the rest
+    for (int g = 0; g < 4; ++g) {
+      const int t_g = t;
       for (int i : act) {
         const SimDesc& s = sims[i];
-        if (s.n_pass[sched] > r && (s.pk_first[sched] <= r) == (on_words != 0)) {
+        if (s.n_pass[sched] <= r) continue;
+        const bool words = s.pk_first[sched] <= r;
+        if (g < 3 ? (words && s.pk_m == 8 - g) : !words) {
           p.entries.push_back(make_int2(i, t));
           t += tiles_of(s, rpt);
         }
       }
-      if (on_words) p.pk_tiles.push_back(t);
+      if (g < 3) p.pk_tiles[g].push_back(t - t_g);
     }
     p.round_tiles.push_back(t);
     p.round_off.push_back(static_cast<int>(p.entries.size()));
@@ -456,16 +439,33 @@ inline void set_clamp(SimDesc& s, int sched, int32_t metric, int clamp_option, i
   }
   s.bytemask[sched] = bmask;
   // Position-tagged words (launch-per-round mode): the dJFA frame's last
-  // passes with k = 1, 2 or a multiple of 4 up to 128, at least two of them,
-  // under the byte-offset key's mean-radius bound, up to 32767 seeds (the
-  // narrow layout, packed from the position table alone).  packed_option:
-  // -1 auto, 0 never.
+  // passes with k = 1, 2 or a multiple of 4, at least two of them, at steps
+  // up to 128 and twice the layout's and the first pass's byte-key windows,
+  // under the byte-offset key's mean-radius bound taken at the layout's
+  // window, up to 2^18 seeds (word layouts 8, 7, 6 as a single simulation's;
+  // the wide ones read the 8-byte seed entries the stamp writes).  The
+  // frame's first such pass folds with the byte-offset key: its window and
+  // label field (narrow below 2^16 seeds) go to the descriptor.
+  // packed_option: -1 auto, 0 never.
   int pkf = s.n_pass[sched];
-  if (sched == 0 && packed_option != 0 && metric == VD_METRIC_EUCLID && vdi::pk_bits(s.n) == 8 && lb >= 4 &&
-      small_cells) {
-    auto ok = [](int k) { return (k == 1 || k == 2 || k % 4 == 0) && k <= 128; };
-    while (pkf > 0 && ok(s.ks[sched][pkf - 1])) --pkf;
-    if (s.n_pass[sched] - pkf < 2) pkf = s.n_pass[sched];
+  int blb = 16;
+  const int hb = vdi::byte_key_window(s.n, &blb);
+  s.bmul = blb >= 32 ? 0u : (1u << blb);
+  s.bwin_bias = static_cast<uint32_t>(hb) * 0x10001u;
+  s.bwin_mask = hb ? (0xFFFFu & ~(2u * hb - 1u)) * 0x10001u : 0xFFFFFFFFu;
+  s.blim = static_cast<uint32_t>(hb) * static_cast<uint32_t>(hb) * s.bmul;
+  if (sched == 0) {
+    s.pk_m = 0;
+    const int lay = vdi::pk_bits(s.n);
+    const int hp = lay ? 1 << (lay - 1) : 0;
+    const double r_max = 40.0 * hp / 128.0;
+    if (packed_option != 0 && metric == VD_METRIC_EUCLID && lay && lb >= 4 && hb >= 32 &&
+        static_cast<double>(s.w) * s.h <= 3.141592653589793 * r_max * r_max * s.n) {
+      auto ok = [&](int k) { return (k == 1 || k == 2 || k % 4 == 0) && k <= 128 && k <= 2 * hp && k <= 2 * hb; };
+      while (pkf > 0 && ok(s.ks[sched][pkf - 1])) --pkf;
+      if (s.n_pass[sched] - pkf < 2) pkf = s.n_pass[sched];
+      if (pkf < s.n_pass[sched]) s.pk_m = lay;
+    }
   }
   s.pk_first[sched] = pkf;
 }
@@ -547,16 +547,21 @@ inline int launch_rounds(const HostPlan& p, const BatchArgs& A, int metric, cuda
     ++*launches;
   }
   for (int r = 0; r < p.rounds; ++r) {
-    const int pk = p.pk_tiles[r], rest = p.round_tiles[r] - pk;
-    if (pk > 0) {
-      k_batch_round_pk<<<pk, kThreads, 0, st>>>(A, r);
+    int t0 = 0;
+    for (int g = 0; g < 3; ++g) {
+      const int n = p.pk_tiles[g][r];
+      if (n <= 0) continue;
+      const int rc = launch_round_pk(8 - g, A, r, t0, n, st);
+      if (rc) return rc;
       ++*launches;
+      t0 += n;
     }
+    const int rest = p.round_tiles[r] - t0;
     if (rest <= 0) continue;
     if (metric == VD_METRIC_MANHATTAN)
-      k_batch_round<vdk::kManhattan><<<rest, kThreads, 0, st>>>(A, r, pk);
+      k_batch_round<vdk::kManhattan><<<rest, kThreads, 0, st>>>(A, r, t0);
     else
-      k_batch_round<vdk::kEuclid><<<rest, kThreads, 0, st>>>(A, r, pk);
+      k_batch_round<vdk::kEuclid><<<rest, kThreads, 0, st>>>(A, r, t0);
     ++*launches;
   }
   if (A.n_act > 0) {

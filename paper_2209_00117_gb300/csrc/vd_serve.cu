@@ -70,7 +70,9 @@ double now_s(const vd_server* s) {
 
 int64_t sim_bytes(int w, int h, int n) {
   const int64_t pitch = (w + 31) / 32 * 32;
-  return 2 * pitch * h * 4 + static_cast<int64_t>(n) * 8 + (static_cast<int64_t>(n) + 1) * (8 + 4) + 256;
+  // maps, seeds, the pass table, the position table and the seed entries of
+  // the wide position-tagged layouts (8 bytes each, after an 8-byte alignment)
+  return 2 * pitch * h * 4 + static_cast<int64_t>(n) * 8 + (static_cast<int64_t>(n) + 1) * (8 + 4 + 8) + 8 + 256;
 }
 
 void server_free(vd_server* s) {
@@ -234,6 +236,10 @@ extern "C" int32_t vd_server_add_sim(vd_server* s, int32_t w, int32_t h, int32_t
   d.seeds = reinterpret_cast<int2*>(d.map[1] + map_elems);
   d.table = d.seeds + n;
   d.ptable = reinterpret_cast<uint32_t*>(d.table + (n + 1));
+  {
+    const uintptr_t end = reinterpret_cast<uintptr_t>(d.ptable + (n + 1));
+    d.pkf = reinterpret_cast<uint2*>((end + 7) & ~static_cast<uintptr_t>(7));
+  }
   d.cur = 0;
   d.step = 0;
   d.n_pass[0] = vdi::fill_schedule(vdi::djfa_first_step(w, h, n, s->d_max), s->vn_waves, 0, d.ks[0], d.nbs[0],

@@ -260,3 +260,34 @@ def test_batch_many_labels_equal_oracle(vd, orc, metric):
     for i in range(len(shapes)):
         np.testing.assert_array_equal(b.labels(i), labs[i], err_msg=f"sim {i} {shapes[i]}")
     b.close()
+
+
+@pytest.mark.parametrize("packed", [-1, 0])
+def test_batch_wide_layouts_equal_alone(vd, packed):
+    """Simulations whose seed counts take each position-tagged layout in the
+    per-round launches -- 8-bit (up to 32767 seeds), 7-bit with the narrow
+    first pass (40000), 7-bit with the wide one (100000), 6-bit (200000 and
+    2^18, where the last seed's code is also the empty code) -- batched with
+    small ones, give exactly their alone runs (maps below the single
+    simulation's 2^21-pixel bound, so those run plain passes), and so do
+    they with the position-tagged passes off."""
+    import torch
+
+    shapes = [(1024, 1024, 40000), (1024, 768, 100000), (1024, 1024, 200000), (1000, 1000, 1 << 18),
+              (512, 384, 2000), (37, 29, 5)]
+    D, steps, rng = 2, 3, 7
+    xys = _seeds(shapes, 40)
+    stream = torch.cuda.Stream()
+    b = vd.VoronoiBatch(shapes, stream=stream)
+    b.set_option(vd.BOPT_PACKED_MAP, packed)
+    b.set_seeds(np.concatenate(xys))
+    b.jfa()
+    b.configure(d_max=D)
+    for _ in range(steps):
+        b.step(None, max_disp=D, rng_seed=rng)
+    b.synchronize()
+    for i, shape in enumerate(shapes):
+        want_l, want_s = _alone_rng(vd, shape, xys[i], i, steps, D, rng)
+        np.testing.assert_array_equal(b.get_seeds(i), want_s)
+        np.testing.assert_array_equal(b.labels(i), want_l, err_msg=f"sim {i} {shape}")
+    b.close()
