@@ -271,9 +271,9 @@ __device__ __forceinline__ void pk_quad(const PassArgs& a, int x0, int y) {
       for (int i = 0; i < 4; ++i) b[i] = min(b[i], F::key(l[i], pi(i)));
       group_fence();
       const uint4 R = rok ? words4(src + r + k) : make_uint4(mid[0], mid[1], mid[2], mid[3]);
-      const uint32_t r[4] = {R.x, R.y, R.z, R.w};
+      const uint32_t rv[4] = {R.x, R.y, R.z, R.w};
 #pragma unroll
-      for (int i = 0; i < 4; ++i) b[i] = min(b[i], F::key(r[i], pi(i)));
+      for (int i = 0; i < 4; ++i) b[i] = min(b[i], F::key(rv[i], pi(i)));
     } else if (KSEL == 1) {
       // left of pixel i: column x0 + i - 1; right: x0 + i + 1
       const uint32_t wl = (IN || x0 >= 4) ? words1(src + r - 1) : mid[0];
@@ -328,9 +328,9 @@ __device__ __noinline__ void pk_edge_quad(const PassArgs a, int x0, int y) {
 #define VD_PK_MIN_BLOCKS 16
 #endif
 
-
-// The launch shape and row order of k_pass (128-thread blocks, row-blocks in
-// k-strided bands when band_m > 1), and its block-uniform interior test.
+// The row order of k_pass (row-blocks in k-strided bands when band_m > 1) and
+// its block-uniform interior test, in blocks of vdi::pk_threads threads (256
+// for the Von Neumann passes on words, 128 otherwise; 32 registers a thread).
 // MODE 0: plain map in, words out (DEDUP: the fold's gathers de-duplicated);
 // 1: words in and out; 2: words in, plain labels out.
 template <int NB, int KSEL, int M, int MODE, bool DEDUP = false>
