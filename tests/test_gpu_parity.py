@@ -977,3 +977,25 @@ def test_packed_auto_matches_plain_at_full_size(vd, orc, s, D):
             np.testing.assert_array_equal(la, lab)
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("w,h,s", [(32768, 8, 300), (8, 32768, 300), (32768, 40, 20000), (40, 32768, 140000)])
+def test_packed_map_maximum_sides(vd, orc, w, h, s):
+    """Position-tagged passes (forced on) on grids at the maximum side: x or y
+    up to 32767 taken modulo 2^M in the words, element indices up to 2^30,
+    the 8-, 7- and 6-bit layouts; dJFA steps after the JFA frame equal the
+    oracle."""
+    xy = inputs.uniform_seeds(w, h, s, seed=w + 3 * h)
+    disp = inputs.displacements(s, 4, 2, seed=2)
+    sim = _sim(vd, w, h, xy, byte_keys=1, packed_map=1)
+    sim.jfa()
+    lab = orc.jfa(w, h, xy)
+    np.testing.assert_array_equal(sim.labels(), lab)
+    for t in range(2):
+        sim.move(disp[t])
+        xy = orc.move(w, h, xy, disp[t])
+        sim.djfa_step(d_max=4)
+        lab = orc.djfa_step(w, h, xy, lab, d_max=4)
+        got = sim.labels()
+        assert np.array_equal(got, lab), (t, int((got != lab).sum()))
+    sim.close()
