@@ -274,8 +274,17 @@ int vd_get_labels_async(vd_ctx* ctx, int32_t* labels);
  * share the limit of two outstanding copies.
  */
 int vd_get_labels16_async(vd_ctx* ctx, uint16_t* labels);
-/* Waits until every vd_get_labels_async / vd_get_labels16_async copy of the
-   context has landed. */
+/*
+ * As vd_get_labels_async, into a dense w x h map of 24-bit labels, three
+ * little-endian bytes each (3/4 of the bytes to copy; labels the host can
+ * widen or use as they are): each label as it is, the empty label -1 as
+ * 0xFFFFFF.  `labels` holds 3 * w * h bytes.  Needs at most 16777215 seeds
+ * (VD_EINVAL otherwise).  Packed on the context's stream into one of the
+ * same two snapshot slots as the other asynchronous read-backs.
+ */
+int vd_get_labels24_async(vd_ctx* ctx, uint8_t* labels);
+/* Waits until every vd_get_labels_async / vd_get_labels16_async /
+   vd_get_labels24_async copy of the context has landed. */
 int vd_wait_labels(vd_ctx* ctx);
 
 /*

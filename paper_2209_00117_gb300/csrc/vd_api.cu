@@ -2046,6 +2046,72 @@ extern "C" int vd_get_labels16_async(vd_ctx* c, uint16_t* labels) {
   return VD_OK;
 }
 
+// Dense 24-bit copy of a label map (rows of w out of a pitched map): each
+// label as three little-endian bytes, the empty label -1 as 0xFFFFFF.  With w
+// a multiple of 4 a thread packs four labels of one row into three aligned
+// 32-bit words (dense byte offset 3 (y w + x) is then a multiple of 12);
+// otherwise it stores the three bytes of one label.
+static __global__ void k_narrow24x4(const int32_t* __restrict__ src, int pitch, int w, uint32_t* __restrict__ dst) {
+  const int x = 4 * static_cast<int>(blockIdx.x * blockDim.x + threadIdx.x);
+  const int64_t y = blockIdx.y;
+  if (x >= w) return;
+  const int4 l = *reinterpret_cast<const int4*>(src + y * pitch + x);
+  const uint32_t a = static_cast<uint32_t>(l.x) & 0xFFFFFFu, b = static_cast<uint32_t>(l.y) & 0xFFFFFFu;
+  const uint32_t c = static_cast<uint32_t>(l.z) & 0xFFFFFFu, d = static_cast<uint32_t>(l.w) & 0xFFFFFFu;
+  uint32_t* o = dst + 3 * ((y * w + x) / 4);
+  o[0] = a | (b << 24);
+  o[1] = (b >> 8) | (c << 16);
+  o[2] = (c >> 16) | (d << 8);
+}
+
+static __global__ void k_narrow24(const int32_t* __restrict__ src, int pitch, int w, uint8_t* __restrict__ dst) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t y = blockIdx.y;
+  if (x >= w) return;
+  const uint32_t v = static_cast<uint32_t>(src[y * pitch + x]);
+  uint8_t* o = dst + 3 * (y * w + x);
+  o[0] = static_cast<uint8_t>(v);
+  o[1] = static_cast<uint8_t>(v >> 8);
+  o[2] = static_cast<uint8_t>(v >> 16);
+}
+
+extern "C" int vd_get_labels24_async(vd_ctx* c, uint8_t* labels) {
+  VD_CHECK_CTX(c);
+  if (!labels) return vd_fail(VD_EINVAL, "null output");
+  if (c->n > 0xFFFFFF) return vd_fail(VD_EINVAL, "24-bit labels need at most 16777215 seeds (have %d)", c->n);
+  int rc = ensure_async(c);
+  if (rc) return rc;
+  const int i = c->snap_next;
+  c->snap_next ^= 1;
+  if (c->copy_pending[i]) {
+    // the slot's previous copy must have left the snapshot before it is reused
+    rc = vd_cuda_check(cudaEventSynchronize(c->copy_done[i]), "wait for read-back");
+    if (rc) return rc;
+    c->copy_pending[i] = false;
+  }
+  // pack the current map into the slot on the compute stream (later frames
+  // rewrite the map), then copy the dense 24-bit map out on the copy stream
+  if (c->w % 4 == 0) {
+    const dim3 grid((c->w / 4 + 255) / 256, c->h);
+    k_narrow24x4<<<grid, 256, 0, c->stream>>>(c->buf[c->cur], c->pitch, c->w, reinterpret_cast<uint32_t*>(c->snap[i]));
+  } else {
+    const dim3 grid((c->w + 255) / 256, c->h);
+    k_narrow24<<<grid, 256, 0, c->stream>>>(c->buf[c->cur], c->pitch, c->w, reinterpret_cast<uint8_t*>(c->snap[i]));
+  }
+  rc = vd_cuda_check(cudaGetLastError(), "pack labels");
+  if (!rc) rc = vd_cuda_check(cudaEventRecord(c->snap_ready[i], c->stream), "event");
+  if (!rc) rc = vd_cuda_check(cudaStreamWaitEvent(c->copy_stream, c->snap_ready[i], 0), "wait event");
+  const size_t bytes = 3 * static_cast<size_t>(c->w) * c->h;
+  if (!rc)
+    rc = vd_cuda_check(cudaMemcpyAsync(labels, c->snap[i], bytes, cudaMemcpyDeviceToHost, c->copy_stream),
+                       "copy labels out");
+  if (!rc) rc = vd_cuda_check(cudaEventRecord(c->copy_done[i], c->copy_stream), "event");
+  if (rc) return rc;
+  ++c->launches;
+  c->copy_pending[i] = true;
+  return VD_OK;
+}
+
 extern "C" int vd_wait_labels(vd_ctx* c) {
   VD_CHECK_CTX(c);
   for (int i = 0; i < 2; ++i) {

@@ -65,6 +65,14 @@ def _buf(a, n_elems: int | None = None, writable: bool = False):
     return a.ctypes.data, 0
 
 
+def widen24(packed, h: int, w: int) -> np.ndarray:
+    """int32 labels (h x w) from a 24-bit read-back (vd_get_labels24_async):
+    three little-endian bytes a label, 0xFFFFFF the empty label -1."""
+    b = np.asarray(packed, np.uint8).reshape(h * w, 3).astype(np.int32)
+    v = b[:, 0] | (b[:, 1] << 8) | (b[:, 2] << 16)
+    return np.where(v == 0xFFFFFF, -1, v).astype(np.int32).reshape(h, w)
+
+
 def _schedule(fn, *args):
     ks = np.zeros(MAX_PASSES, np.int32)
     nbs = np.zeros(MAX_PASSES, np.int32)
@@ -321,6 +329,26 @@ class VoronoiSim:
         if n != self.w * self.h:
             raise ValueError(f"expected {self.w * self.h} elements, got {n}")
         N.check(self._lib.vd_get_labels16_async(self._h, ptr))
+        return out
+
+    def labels24_async(self, out):
+        """As :meth:`labels_async` into a contiguous host uint8 array or tensor
+        of 3 * h * w bytes: each label as three little-endian bytes, the empty
+        label as 0xFFFFFF (at most 16777215 seeds); :func:`widen24` turns it
+        back into int32 labels."""
+        if _is_torch(out):
+            if str(out.dtype) != "torch.uint8" or not out.is_contiguous() or out.is_cuda:
+                raise TypeError("out must be a contiguous host uint8 tensor")
+            n, ptr = out.numel(), out.data_ptr()
+        else:
+            if not isinstance(out, np.ndarray) or out.dtype != np.uint8 or not out.flags.c_contiguous:
+                raise TypeError("out must be a C-contiguous uint8 numpy array")
+            if not out.flags.writeable:
+                raise ValueError("output array is read-only")
+            n, ptr = out.size, out.ctypes.data
+        if n != 3 * self.w * self.h:
+            raise ValueError(f"expected {3 * self.w * self.h} bytes, got {n}")
+        N.check(self._lib.vd_get_labels24_async(self._h, ptr))
         return out
 
     def wait_labels(self):

@@ -460,6 +460,63 @@ def test_async_label_readback_16bit(vd, w, h, s):
     b.close()
 
 
+@pytest.mark.parametrize("w,h,s", [(600, 400, 2500), (601, 403, 70000), (1024, 512, 1 << 18), (33, 5, 9)])
+def test_async_label_readback_24bit(vd, w, h, s):
+    """The 24-bit read-back: every frame's dense map (three little-endian bytes
+    a label), interleaved with 32-bit read-backs through the same two slots,
+    equals the synchronous int32 read: empty labels as 0xFFFFFF, widths a
+    multiple of 4 (four labels packed into three words) and not (byte
+    stores), seed counts beyond 16 bits."""
+    import torch
+
+    D = 2
+    xy = inputs.uniform_seeds(w, h, s, seed=17)
+    disp = inputs.displacements(s, D, 5, seed=17)
+    a = _sim(vd, w, h, xy)
+    b = _sim(vd, w, h, xy)
+    src = np.random.default_rng(s + 1).integers(-1, s, size=(h, w), dtype=np.int32)
+    a.set_labels(src)
+    b.set_labels(src)
+    o24 = [torch.empty(3 * h * w, dtype=torch.uint8).pin_memory() for _ in range(6)]
+    o32 = [torch.empty((h, w), dtype=torch.int32).pin_memory() for _ in range(6)]
+    want = []
+    for t in range(6):
+        if t:
+            for sim in (a, b):
+                sim.move(disp[t - 1])
+                sim.djfa_step(d_max=D)
+        a.labels24_async(o24[t])
+        a.labels_async(o32[t])
+        want.append(b.labels())
+    a.wait_labels()
+    for t in range(6):
+        raw = o24[t].numpy().reshape(h * w, 3).astype(np.int64)
+        packed = raw[:, 0] | (raw[:, 1] << 8) | (raw[:, 2] << 16)
+        exp = want[t].astype(np.int64).reshape(-1)
+        exp[exp == -1] = 0xFFFFFF
+        np.testing.assert_array_equal(packed, exp, err_msg=f"frame {t}")
+        np.testing.assert_array_equal(vd.widen24(o24[t].numpy(), h, w), want[t], err_msg=f"frame {t}")
+        np.testing.assert_array_equal(o32[t].numpy(), want[t], err_msg=f"frame {t}")
+    arr = np.empty(3 * h * w, np.uint8)
+    a.labels24_async(arr)
+    a.wait_labels()
+    np.testing.assert_array_equal(vd.widen24(arr, h, w), want[-1])
+    a.close()
+    b.close()
+
+
+def test_async_label_readback_24bit_refuses_large_counts(vd):
+    """From 2^24 seeds on a label no longer fits 24 bits: VD_EINVAL."""
+    from paper_2209_00117_gb300._native import VD_EINVAL, VDError
+
+    w, h, s = 64, 64, 1 << 24
+    sim = vd.VoronoiSim(w, h, s)
+    with pytest.raises(VDError) as ei:
+        sim.labels24_async(np.empty(3 * h * w, np.uint8))
+    assert ei.value.code == VD_EINVAL
+    sim.close()
+
+
 def test_async_label_readback_16bit_refuses_large_counts(vd):
     """From 65536 seeds on a label no longer fits 16 bits: VD_EINVAL."""
     from paper_2209_00117_gb300._native import VD_EINVAL, VDError
