@@ -341,13 +341,13 @@ int vd_exact(vd_ctx* ctx, int32_t* labels, int32_t* dist, int on_device, int32_t
  * that every GPU loading the library holds until the process exits.  The
  * bucket grid needs 64 + 2 * buckets + 1 + n_seeds ints, and the bucket side
  * is chosen so that there are at most two buckets per seed, so the need is at
- * most 66 + 5 * n_seeds ints: up to 200000 seeds always fit, on any grid.  Larger requests fail with VD_EINVAL and a message
- * naming the need, as do bad sizes, a bad metric and seeds outside the
- * grid.  No cudaMalloc, cudaFree or allocating library routine is called.
- * The first call on a device resolves the array's device address (with that
- * device current) and keeps it for the life of the process; make that first
- * call before any stream capture, and do not call cudaDeviceReset on a
- * device between calls (the kept address would be stale).  All calls
+ * most 66 + 5 * n_seeds ints: up to 200000 seeds always fit, on any grid.
+ * Larger requests fail with VD_EINVAL and a message naming the need, as do
+ * bad sizes, a bad metric and seeds outside the grid.  No cudaMalloc,
+ * cudaFree or allocating library routine is called.  Every call synchronises
+ * the stream for the seed check, so the call cannot be captured into a CUDA
+ * graph.  The array's device address is resolved on every call (with the
+ * seeds' device current), so it stays valid across a device reset.  All calls
  * share the one array, which keeps the previous call's contents (the parts
  * that must start at zero are cleared on every call): calls that overlap on
  * the GPU, on any stream, race.

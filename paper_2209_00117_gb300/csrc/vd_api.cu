@@ -9,7 +9,6 @@
 #include <cmath>
 #include <cstring>
 #include <map>
-#include <mutex>
 #include <string>
 #include <tuple>
 #include <vector>
@@ -1860,9 +1859,6 @@ static __device__ __align__(256) int g_noalloc_scratch[VD_NOALLOC_SCRATCH_INTS];
 namespace {
 
 constexpr int kNoallocHeaderInts = 64;
-constexpr int kNoallocMaxDevices = 64;
-std::mutex g_noalloc_mu;
-int* g_noalloc_ptr[kNoallocMaxDevices] = {};
 
 }  // namespace
 
@@ -1897,25 +1893,13 @@ extern "C" int vd_exact_noalloc(const int32_t* seeds_xy, int32_t n_seeds, int32_
                    n_seeds, w, h, static_cast<long long>(need), static_cast<long long>(cells),
                    VD_NOALLOC_SCRATCH_INTS);
 
-  int dev = 0;
-  int rc = vd_cuda_check(cudaGetDevice(&dev), "cudaGetDevice");
+  // the host-side name of the array is only a stand-in, the kernels need its
+  // device address: resolved on every call (cheap) for the current device's
+  // context, so no address outlives a device reset
+  void* p = nullptr;
+  int rc = vd_cuda_check(cudaGetSymbolAddress(&p, g_noalloc_scratch), "cudaGetSymbolAddress(scratch)");
   if (rc) return rc;
-  if (dev < 0 || dev >= kNoallocMaxDevices) return vd_fail(VD_EINVAL, "device %d beyond %d", dev, kNoallocMaxDevices);
-  int* base = nullptr;
-  {
-    // once per device, with that device current: the host-side name of the
-    // array is only a stand-in, the kernels need its device address.  The
-    // cached address belongs to the device's primary context: it is stale
-    // after cudaDeviceReset, so callers must not reset a device between calls
-    std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_ptr[dev]) {
-      void* p = nullptr;
-      rc = vd_cuda_check(cudaGetSymbolAddress(&p, g_noalloc_scratch), "cudaGetSymbolAddress(scratch)");
-      if (rc) return rc;
-      g_noalloc_ptr[dev] = static_cast<int*>(p);
-    }
-    base = g_noalloc_ptr[dev];
-  }
+  int* base = static_cast<int*>(p);
   unsigned long long* flag = reinterpret_cast<unsigned long long*>(base);
   int* count = base + kNoallocHeaderInts;
   int* start = count + cells;
