@@ -311,8 +311,10 @@ int launch_pass(const MapView& m, const int32_t* src, int32_t* dst, int32_t k, i
   // the position-tagged passes of a dJFA frame (chosen by run_passes)
   if (pk_m) {
     // the first pass folds with a byte-offset key (the narrow one for the
-    // 8-bit layout; either for the wide ones)
-    if (rows_only || ksel > 2 || (pk_mode == 0 && (key < 3 || (pk_m == 8 && key != 3))))
+    // 8-bit layout; either for the wide ones; the split layout's with the
+    // clamped key)
+    const bool first_ok = pk_m == 4 ? a.cap != 0 : key >= 3 && (pk_m != 8 || key == 3);
+    if (rows_only || ksel > 2 || metric != VD_METRIC_EUCLID || (pk_mode == 0 && !first_ok))
       return vd_fail(VD_EINVAL, "packed pass: step %d, key form %d, layout %d", k, key, pk_m);
     return launch_pass_pk(a, grid, block, nb, pk_m, ksel, pk_mode, dedup, st, pdl);
   }
@@ -454,7 +456,7 @@ int run_passes(const MapView& m, int32_t* const buf[2], int* cur, const int32_t*
   int pk_first = n;
   const int pk_m = t.fuse_max_k <= 0 ? pk_bits(m.n) : 0;
   if (pk_m) {
-    while (pk_first > 0 && use_packed(t, metric, m.w, m.h, m.n, ks[pk_first - 1], djfa_frame)) --pk_first;
+    while (pk_first > 0 && use_packed(t, metric, m.w, m.h, m.n, ks[pk_first - 1], ks[0], djfa_frame)) --pk_first;
     if (n - pk_first < 2) pk_first = n;
   }
   for (const Launch& l : plan) {
@@ -482,16 +484,30 @@ int run_passes(const MapView& m, int32_t* const buf[2], int* cur, const int32_t*
   return VD_OK;
 }
 
-bool use_packed(const Tuning& t, int32_t metric, int32_t w, int32_t h, int32_t n, int32_t k, bool djfa_frame) {
-  if (t.packed == 0 || !djfa_frame) return false;
+bool use_packed(const Tuning& t, int32_t metric, int32_t w, int32_t h, int32_t n, int32_t k, int32_t k_first,
+                bool djfa_frame) {
+  if (t.packed == 0 || !djfa_frame || metric != VD_METRIC_EUCLID) return false;
   const int lay = pk_bits(n);
   if (lay == 0 || !(k == 1 || k == 2 || k % 4 == 0)) return false;
-  if (!use_byte_key(t.byte_key, metric, w, h, n, k, djfa_frame)) return false;
+  // the split layout's first pass folds with the clamped key, the others'
+  // with the byte-offset key
+  if (!(lay == 4 ? use_clamp(t.clamp, metric, n, k, djfa_frame) : use_byte_key(t.byte_key, metric, w, h, n, k,
+                                                                               djfa_frame)))
+    return false;
   if (t.packed == 1) return true;
   // auto: the byte-offset key's bounds (mean cell radius at most 40 pixels
   // per 128 of window, k at most twice the window) with the layout's window
   const double hw = static_cast<double>(1 << (lay - 1));
   if (k > 2 * hw) return false;
+  // The split layout's +-8 window: after a frame's first step of 16 (moves
+  // of more than 8 pixels) the map is still that far off two passes later.
+  // Estimated on the CPU at 16 pixels a seed (1024^2, 2^16 seeds), the share
+  // of quads whose winner fails the check in the first pass on words: first
+  // step 8, that pass at k = 4: 0.05% (moves of 1), 0.65% (4); first step
+  // 16, at k = 8: 85%, at k = 4: 26%, at k = 2: 0.12%.  So words from
+  // k * first step <= 64 on, i.e. the words passes start two steps after a
+  // first step of 16 and right after one of 8
+  if (lay == 4 && static_cast<int64_t>(k) * k_first > 64) return false;
   const double r_max = 40.0 * hw / 128.0;
   return static_cast<double>(w) * h <= 3.141592653589793 * r_max * r_max * n;
 }

@@ -459,7 +459,7 @@ inline void set_clamp(SimDesc& s, int sched, int32_t metric, int clamp_option, i
     const int lay = vdi::pk_bits(s.n);
     const int hp = lay ? 1 << (lay - 1) : 0;
     const double r_max = 40.0 * hp / 128.0;
-    if (packed_option != 0 && metric == VD_METRIC_EUCLID && lay && lb >= 4 && hb >= 32 &&
+    if (packed_option != 0 && metric == VD_METRIC_EUCLID && lay >= 6 && lb >= 4 && hb >= 32 &&
         static_cast<double>(s.w) * s.h <= 3.141592653589793 * r_max * r_max * s.n) {
       auto ok = [&](int k) { return (k == 1 || k == 2 || k % 4 == 0) && k <= 128 && k <= 2 * hp && k <= 2 * hb; };
       while (pkf > 0 && ok(s.ks[sched][pkf - 1])) --pkf;

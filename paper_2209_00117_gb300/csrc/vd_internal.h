@@ -144,11 +144,13 @@ int launch_pass_sparse(const vdk::PassArgs& a, dim3 grid, dim3 block, int32_t nb
 bool tile_applies(int32_t k, int key, int max_k);
 int launch_pass_tile(const vdk::PassArgs& a, int32_t nb, int key, int rows, cudaStream_t st, bool pdl);
 // The position-tagged dJFA passes (vd_pass_pk.cuh): the word layout M for n
-// seeds (8, 7 or 6; 0 where none holds the labels), and one pass with step
+// seeds (8, 7, 6 or 4; 0 where none holds the labels), whether a frame whose
+// first step is k_first runs its pass of step k on words, and one pass with step
 // k = 1, 2 or k % 4 == 0 (ksel 1, 2, 0) of layout m: mode 0 plain map in,
 // words out; 1 words in and out; 2 words in, plain labels out.
 int pk_bits(int32_t n);
-bool use_packed(const Tuning& t, int32_t metric, int32_t w, int32_t h, int32_t n, int32_t k, bool djfa_frame);
+bool use_packed(const Tuning& t, int32_t metric, int32_t w, int32_t h, int32_t n, int32_t k, int32_t k_first,
+                bool djfa_frame);
 int launch_pass_pk(const vdk::PassArgs& a, dim3 grid, dim3 block, int32_t nb, int m, int ksel, int mode,
                    bool dedup, cudaStream_t st, bool pdl);
 // The position map of JFA frames (vd_pass_pos.cu): per pixel (label, x | y << 16).

@@ -848,11 +848,11 @@ static __global__ void k_stamp_mark(int32_t* __restrict__ labels, int pitch, con
 
 // Stamp, second half: the lowest index standing on the pixel wins.  As
 // unsigned, -1 is the largest value, so this also stamps an emptied map.
-// With pk_m = 6 or 7 it also writes the frame's entries of the
+// With pk_m = 6, 7 or 4 it also writes the frame's entries of the
 // position-tagged passes' seed table (pkf: n + 1 entries {x | y << 16, the
-// seed's word bits but the label}, [0] the far position; parena: the packed
-// positions with the far one first): the stamp runs right before every dJFA
-// frame's passes, after the move.
+// seed's word bits but the label's low bits}, [0] the far position; parena:
+// the packed positions with the far one first): the stamp runs right before
+// every dJFA frame's passes, after the move.
 static __global__ void k_stamp_min(int32_t* __restrict__ labels, int pitch, const int2* __restrict__ seeds,
                             int n, uint2* __restrict__ pkf, const uint32_t* __restrict__ parena, int pk_m) {
   pdl_trigger();
@@ -863,11 +863,15 @@ static __global__ void k_stamp_min(int32_t* __restrict__ labels, int pitch, cons
   atomicMin(reinterpret_cast<unsigned int*>(labels + static_cast<int64_t>(p.y) * pitch + p.x),
             static_cast<unsigned int>(k));
   if (pk_m) {
-    // the word bits of layout pk_m (wide): bit 24 set, x mod 2^m at
-    // [24 - m, 24), y mod 2^m at [32 - m, 32)
+    // the word bits of layout pk_m: wide, bit 24 set, x mod 2^m at
+    // [24 - m, 24), y mod 2^m at [32 - m, 32); split (m = 4), label bits
+    // 20-21 at [24, 26), bit 26 set, x mod 16 at [20, 24), y mod 16 at [28, 32)
     const uint32_t xm = (1u << pk_m) - 1u;
-    const uint32_t f = (1u << 24) | ((static_cast<uint32_t>(p.x) & xm) << (24 - pk_m)) |
-                       ((static_cast<uint32_t>(p.y) & xm) << (32 - pk_m));
+    const uint32_t f =
+        pk_m == 4 ? ((static_cast<uint32_t>(k) & 0x300000u) << 4) | (1u << 26) |
+                        ((static_cast<uint32_t>(p.x) & 15u) << 20) | ((static_cast<uint32_t>(p.y) & 15u) << 28)
+                  : (1u << 24) | ((static_cast<uint32_t>(p.x) & xm) << (24 - pk_m)) |
+                        ((static_cast<uint32_t>(p.y) & xm) << (32 - pk_m));
     pkf[k + 1] = make_uint2(pack_pos(p.x, p.y), f);
     if (k == 0) pkf[0] = make_uint2(parena[0], 0u);
   }

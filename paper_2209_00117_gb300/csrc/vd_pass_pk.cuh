@@ -15,6 +15,10 @@
 //   M = 8 ("narrow"):  bits [0, 8) label bits 0-7, [8, 16) x mod 256,
 //                      [16, 23) label bits 8-14, bit 23 set (guard),
 //                      [24, 32) y mod 256.
+//   M = 4 ("split"):   bits [0, 20) label bits 0-19, [20, 24) x mod 16,
+//                      [24, 26) label bits 20-21, bit 26 set (guard),
+//                      bit 27 marks an empty pixel, [28, 32) y mod 16
+//                      (up to 2^22 seeds).
 //
 // For a pixel whose own fields P sit in the same places, v = w - P holds
 // (x - x_p) mod 2^M and (y - y_p) mod 2^M at the top of their bytes: the guard
@@ -27,7 +31,11 @@
 // (narrow: one byte permute of the word and d).  Per candidate: a subtraction,
 // a mask, the dp4a, the key pack (wide: and the label mask) and a minimum; no
 // gather.  No key wraps: wide keys lie below 2^31, narrow ones hold d <= 2^15
-// in their upper 16 bits (keys compare as unsigned).
+// in their upper 16 bits (keys compare as unsigned).  The split layout's
+// label code (its label bits where the word holds them, an order-preserving
+// image of the label) spans 26 bits, which leaves 6 bits for d: its key is
+// min(d, 63) * 2^26 + code, one more minimum a candidate, and the winner
+// check accepts d < 63 only (a saturated key carries no distance).
 //
 // Outside the window the fields alias and a key may be anything, and the
 // byte-offset pass's winner check applies unchanged: each pixel's winner is
@@ -41,8 +49,9 @@
 // of the position table and so always takes the recomputation.
 //
 // A frame runs its first packed pass on the plain map (the byte-offset fold
-// with gathers) writing words, the passes after it word to word, and its last
-// pass writes plain labels again.
+// with gathers; for the split layout, whose labels leave the byte-offset key
+// too narrow a window, the clamped 32-bit fold) writing words, the passes
+// after it word to word, and its last pass writes plain labels again.
 #pragma once
 
 #include "vd.h"
@@ -54,39 +63,62 @@ namespace vdk {
 template <int M>
 struct Pk {
   static constexpr bool kNarrow = M == 8;
-  static constexpr int kLb = kNarrow ? 15 : 24 - M;  // label bits
-  static constexpr int kKs = kNarrow ? 16 : kLb;     // key = d * 2^kKs + ...
-  static constexpr uint32_t kLm = (1u << kLb) - 1u;  // label code mask; all ones: empty
-  static constexpr uint32_t kH = 1u << (M - 1);      // window: dx, dy in [-kH, kH)
+  static constexpr bool kSplit = M == 4;
+  static constexpr int kLb = kNarrow ? 15 : kSplit ? 26 : 24 - M;  // label code bits
+  static constexpr int kKs = kNarrow ? 16 : kLb;                    // key = d * 2^kKs + ...
+  // label code mask; all ones: empty
+  static constexpr uint32_t kLm = kSplit ? 0x030FFFFFu : (1u << kLb) - 1u;
+  static constexpr uint32_t kH = 1u << (M - 1);  // window: dx, dy in [-kH, kH)
   static constexpr uint32_t kXm = (1u << M) - 1u;
-  static constexpr int kXs = kNarrow ? 8 : kLb;  // x field shift
-  static constexpr int kYs = 32 - M;             // y field shift
+  static constexpr int kXs = kNarrow ? 8 : kSplit ? 20 : kLb;  // x field shift
+  static constexpr int kYs = 32 - M;                           // y field shift
   static constexpr uint32_t kFm = (kXm << kXs) | (kXm << kYs);
-  static constexpr uint32_t kG = kNarrow ? 0x00800000u : 0x01000000u;
-  static constexpr uint32_t kEf = M == 6 ? 0x02000000u : 0u;  // empty flag (M = 6)
+  static constexpr uint32_t kG = kNarrow ? 0x00800000u : kSplit ? 0x04000000u : 0x01000000u;
+  // empty flag (M = 6 and 4, whose all-ones code is also the last seed's)
+  static constexpr uint32_t kEf = M == 6 ? 0x02000000u : kSplit ? 0x08000000u : 0u;
   static constexpr uint32_t kEmpty = kNarrow ? (0xFFu | (0x7Fu << 16) | kG) : (kLm | kG | kEf);
+  // keys at or above this fail the winner check: d >= h^2 (split: d >= 63,
+  // the saturated keys)
+  static constexpr uint32_t kLim = kSplit ? 63u << kKs : (kH * kH) << kKs;
+  // the dp4a sum of the split layout is 256 d, saturated at 256 * 63
+  static constexpr uint32_t kSat = 63u * 256u;
 
   // The fields of pixel (x, y), negated: v = w + neg_pix(x, y).
   __device__ __forceinline__ static uint32_t neg_pix(uint32_t x, uint32_t y) {
     return 0u - (((x & kXm) << kXs) | ((y & kXm) << kYs));
   }
+  // The label a code (of a word or a key) names (split: its bits joined).
+  __device__ __forceinline__ static uint32_t code_label(uint32_t c) {
+    return kSplit ? ((c & 0xFFFFFu) | ((c >> 4) & 0x300000u)) : (c & kLm);
+  }
   // The label a word names, -1 for the empty word.
   __device__ __forceinline__ static int label(uint32_t w) {
-    if (M == 6) return (w & kEf) ? -1 : static_cast<int>(w & kLm);
+    if (kEf) return (w & kEf) ? -1 : static_cast<int>(code_label(w));
     const uint32_t c = kNarrow ? ((w & 0xFFu) | ((w >> 8) & 0x7F00u)) : (w & kLm);
     return c == kLm ? -1 : static_cast<int>(c);
+  }
+  // The label bits of label l where a word holds them.
+  __device__ __forceinline__ static uint32_t code(uint32_t l) {
+    return kSplit ? (l & 0xFFFFFu) | ((l & 0x300000u) << 4) : l;
   }
   // The word of label l >= 0 whose seed lies at e = x | y << 16.
   __device__ __forceinline__ static uint32_t word(uint32_t l, uint32_t e) {
     if (kNarrow) return (l & 0xFFu) | ((e & 0xFFu) << 8) | ((l & 0x7F00u) << 8) | kG | ((e >> 16) << 24);
-    return l | kG | ((e & kXm) << kXs) | (((e >> 16) & kXm) << kYs);
+    return code(l) | kG | ((e & kXm) << kXs) | (((e >> 16) & kXm) << kYs);
   }
   // Key of word w for the pixel with negated fields pn.
   __device__ __forceinline__ static uint32_t key(uint32_t w, uint32_t pn) {
     const uint32_t b = (w + pn) & kFm;
     const uint32_t d = static_cast<uint32_t>(__dp4a(static_cast<int>(b), static_cast<int>(b), 0));
     if (kNarrow) return __byte_perm(w, d, 0x5420);
+    if (kSplit) return min(d, kSat) * (1u << 18) + (w & kLm);
     return d * (1u << (8 + M)) + (w & kLm);
+  }
+  // The position-table index of a key's label (far entry first): (label + 1)
+  // modulo the code's range, so that the empty code lands on the far entry.
+  __device__ __forceinline__ static uint32_t index(uint32_t key) {
+    if (kSplit) return (code_label(key) + 1u) & 0x3FFFFFu;
+    return (key + 1u) & kLm;
   }
   // The winner's word from its key and its seed position e (check passed).
   __device__ __forceinline__ static uint32_t word_of_key(uint32_t key, uint32_t e) {
@@ -168,7 +200,8 @@ __device__ __noinline__ void pk_exact_quad(const PassArgs a, int x0, int y) {
 
 // The winner check and the store of one quad whose keys are d * 2^ks + code
 // (code = label, its low lb bits; all ones: empty): e = the position-table
-// entry at (code + 1) mod 2^lb with the far position first, in the window
+// entry at (code + 1) mod 2^lb (split layout: (label + 1) mod 2^22) with the
+// far position first, in the window
 // [-h, h) around each pixel, and every d < h^2.  lm = 2^lb - 1; the window
 // kw = h * 0x10001 - (x0 | y << 16), wmask = (0xFFFF & ~(2h - 1)) * 0x10001,
 // lim = h^2 << ks.  PKOUT: words of layout M from the keys (key form KF: 0
@@ -185,12 +218,14 @@ __device__ __forceinline__ bool pk_check_store(const PassArgs& a, const uint32_t
   uint32_t bad = 0, top = 0;
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
+    // (the split layout's code is not the label: its index joins the bits)
+    const uint32_t j = F::kSplit ? F::index(b[i]) : (b[i] + 1u) & lm;
     if (KF == 2) {
-      const uint2 ef = __ldg(&a.pkf[(b[i] + 1u) & lm]);
+      const uint2 ef = __ldg(&a.pkf[j]);
       e[i] = ef.x;
       f[i] = ef.y;
     } else {
-      e[i] = __ldg(&arena[(b[i] + 1u) & lm]);
+      e[i] = __ldg(&arena[j]);
     }
     // (dx + h) | (dy + h) << 16 has no bit at or above 2h in either half
     // exactly when dx, dy lie in [-h, h)
@@ -211,7 +246,7 @@ __device__ __forceinline__ bool pk_check_store(const PassArgs& a, const uint32_t
              : KF == 1 ? F::word_of_key(b[i], e[i])
              : M == 8  ? __byte_perm(b[i], e[i], 0x6140) | F::kG
                        : F::word(b[i] & lm, e[i]);
-    else o[i] = b[i] & lm;
+    else o[i] = F::kSplit ? F::code_label(b[i]) : b[i] & lm;
     if (!IN && x0 + i >= a.w) o[i] = PKOUT ? F::kEmpty : 0xFFFFFFFFu;
   }
   *reinterpret_cast<uint4*>(a.dst + static_cast<int64_t>(y) * a.pitch + x0) = make_uint4(o[0], o[1], o[2], o[3]);
@@ -234,6 +269,30 @@ __device__ __forceinline__ void pk_first_quad(const PassArgs& a, int x0, int y) 
   // words of a wide layout take their bits from a.pkf
   if (!pk_check_store<M, kWide ? 2 : 0, true, IN>(a, q.b, x0, y, lm, kw, wmask, lim))
     pk_exact_quad<NB, M, false, true>(a, x0, y);
+}
+
+// The split layout's first packed pass: the clamped 32-bit fold on the plain
+// map (as the plain pass: exact while every pixel's best lies below the cap),
+// then words from the labels and the seeds' word bits in a.pkf (which carry
+// the labels' upper bits); a quad whose best reaches the cap is recomputed.
+template <int NB, int KSEL, bool DEDUP, bool IN>
+__device__ __forceinline__ void pk_first_quad32(const PassArgs& a, int x0, int y) {
+  using F = Pk<4>;
+  Quad32<false, DEDUP> q(a, x0, y);
+  fold_all<NB, KSEL, false, IN>(q, a, x0, y);
+  if (max(max(q.b[0], q.b[1]), max(q.b[2], q.b[3])) >= (a.cap - 1u) * a.mul) {
+    pk_exact_quad<NB, 4, false, true>(a, x0, y);
+    return;
+  }
+  const uint32_t mask = a.mul - 1u;
+  uint32_t o[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const uint32_t l = q.b[i] & mask;
+    o[i] = (l & 0xFFFFFu) | __ldg(&a.pkf[l + 1u].y);
+    if (!IN && x0 + i >= a.w) o[i] = F::kEmpty;
+  }
+  *reinterpret_cast<uint4*>(a.dst + static_cast<int64_t>(y) * a.pitch + x0) = make_uint4(o[0], o[1], o[2], o[3]);
 }
 
 // One packed pass (words in) for the quad (x0 .. x0 + 3, y).  Candidate order
@@ -311,7 +370,7 @@ __device__ __forceinline__ void pk_quad(const PassArgs& a, int x0, int y) {
   const uint32_t wmask = (0xFFFFu & ~(2u * F::kH - 1u)) * 0x10001u;
   // words out of a wide layout take their bits from a.pkf
   constexpr int kf = PKOUT && M != 8 ? 2 : 1;
-  if (!pk_check_store<M, kf, PKOUT, IN>(a, b, x0, y, F::kLm, kw, wmask, (F::kH * F::kH) << F::kKs))
+  if (!pk_check_store<M, kf, PKOUT, IN>(a, b, x0, y, F::kLm, kw, wmask, F::kLim))
     pk_exact_quad<NB, M, true, PKOUT>(a, x0, y);
 #undef pi
 }
@@ -320,7 +379,8 @@ __device__ __forceinline__ void pk_quad(const PassArgs& a, int x0, int y) {
 // line, so that the interior path keeps a register allocation of its own.
 template <int NB, int KSEL, int M, int MODE, bool DEDUP>
 __device__ __noinline__ void pk_edge_quad(const PassArgs a, int x0, int y) {
-  if (MODE == 0) pk_first_quad<NB, KSEL, M, DEDUP, false>(a, x0, y);
+  if (MODE == 0 && M == 4) pk_first_quad32<NB, KSEL, DEDUP, false>(a, x0, y);
+  else if (MODE == 0) pk_first_quad<NB, KSEL, M, DEDUP, false>(a, x0, y);
   else pk_quad<NB, KSEL, M, MODE == 1, false>(a, x0, y);
 }
 
@@ -330,11 +390,14 @@ __device__ __noinline__ void pk_edge_quad(const PassArgs a, int x0, int y) {
 
 // The row order of k_pass (row-blocks in k-strided bands when band_m > 1) and
 // its block-uniform interior test, in blocks of vdi::pk_threads threads (256
-// for the Von Neumann passes on words, 128 otherwise; 32 registers a thread).
+// for the Von Neumann passes on words, 128 otherwise; 32 registers a thread,
+// the split layout's first pass the clamped plain pass's 48).
 // MODE 0: plain map in, words out (DEDUP: the fold's gathers de-duplicated);
 // 1: words in and out; 2: words in, plain labels out.
 template <int NB, int KSEL, int M, int MODE, bool DEDUP = false>
-__global__ void __launch_bounds__(vdi::pk_threads(NB, MODE), VD_PK_MIN_BLOCKS * 128 / vdi::pk_threads(NB, MODE))
+__global__ void __launch_bounds__(vdi::pk_threads(NB, MODE),
+                                  (MODE == 0 && M == 4 ? VD_PASS_MIN_BLOCKS : VD_PK_MIN_BLOCKS) * 128 /
+                                      vdi::pk_threads(NB, MODE))
     k_pass_pk(PassArgs a) {
   pdl_trigger();
   pdl_wait();
@@ -348,6 +411,7 @@ __global__ void __launch_bounds__(vdi::pk_threads(NB, MODE), VD_PK_MIN_BLOCKS * 
   const bool in = xb - a.k >= 0 && xb + 4 * static_cast<int>(blockDim.x) + a.k <= a.w && yb - a.k >= 0 &&
                   yb + static_cast<int>(blockDim.y) + a.k <= a.h;
   if (!in) pk_edge_quad<NB, KSEL, M, MODE, DEDUP>(a, x0, y);
+  else if (MODE == 0 && M == 4) pk_first_quad32<NB, KSEL, DEDUP, true>(a, x0, y);
   else if (MODE == 0) pk_first_quad<NB, KSEL, M, DEDUP, true>(a, x0, y);
   else pk_quad<NB, KSEL, M, MODE == 1, true>(a, x0, y);
 }

@@ -974,13 +974,15 @@ def test_smem_tile_auto_matches_plain_at_full_size(vd, orc, s, D):
 
 @pytest.mark.parametrize("w,h,s", [(37, 29, 12), (300, 211, 500), (517, 263, 32767), (1000, 70, 40000),
                                    (640, 480, 65536), (700, 500, 131071), (1000, 700, 131072),
-                                   (1024, 700, 1 << 18)])
+                                   (1024, 700, 1 << 18), (701, 499, (1 << 18) + 1), (1500, 900, 400000)])
 def test_packed_map_frames(vd, orc, w, h, s):
     """dJFA frames whose byte-key passes run on position-tagged words (forced
     on) against the oracle, for each word layout: up to 32767 seeds (8-bit
     position fields), 32768 .. 2^17 - 1 (7-bit; below 2^16 seeds, as 40000,
     the frame's first pass folds with the narrow byte-offset key), 2^17 ..
-    2^18 (6-bit, where the last seed's label code is also the empty code).  Frames after the JFA frame with moves, extra
+    2^18 (6-bit, where the last seed's label code is also the empty code),
+    above 2^18 (4-bit, the label split around the x field, distances
+    saturated, the frame's first pass on the clamped key).  Frames after the JFA frame with moves, extra
     passes and no Von Neumann waves, then frames stamped onto random maps with
     and without empty labels: nearly every quad there fails the winner check
     and is recomputed, and empty pixels cross the packed passes.  Ragged
@@ -1010,11 +1012,12 @@ def test_packed_map_frames(vd, orc, w, h, s):
     sim.close()
 
 
-@pytest.mark.parametrize("s,D", [(1 << 18, 4), (1 << 16, 4), (1 << 14, 4)])
+@pytest.mark.parametrize("s,D", [(1 << 18, 4), (1 << 16, 4), (1 << 14, 4), (1 << 22, 4), (1 << 22, 16)])
 def test_packed_auto_matches_plain_at_full_size(vd, orc, s, D):
     """8192 x 8192 sweep points with the position-tagged passes (auto) and
     without: three graph-replayed dJFA steps give the same maps, the first
-    equal to the oracle."""
+    equal to the oracle (2^22 seeds: the 4-bit layout, from the first pass
+    with moves of 4, from the third with moves of 16)."""
     w = h = 8192
     xy = inputs.uniform_seeds(w, h, s, seed=23)
     disp = inputs.displacements(s, D, 3, seed=23)
@@ -1036,12 +1039,13 @@ def test_packed_auto_matches_plain_at_full_size(vd, orc, s, D):
     b.close()
 
 
-@pytest.mark.parametrize("w,h,s", [(32768, 8, 300), (8, 32768, 300), (32768, 40, 20000), (40, 32768, 140000)])
+@pytest.mark.parametrize("w,h,s", [(32768, 8, 300), (8, 32768, 300), (32768, 40, 20000), (40, 32768, 140000),
+                                   (32768, 24, 300000)])
 def test_packed_map_maximum_sides(vd, orc, w, h, s):
     """Position-tagged passes (forced on) on grids at the maximum side: x or y
     up to 32767 taken modulo 2^M in the words, element indices up to 2^30,
-    the 8-, 7- and 6-bit layouts; dJFA steps after the JFA frame equal the
-    oracle."""
+    the 8-, 7-, 6- and 4-bit layouts; dJFA steps after the JFA frame equal
+    the oracle."""
     xy = inputs.uniform_seeds(w, h, s, seed=w + 3 * h)
     disp = inputs.displacements(s, 4, 2, seed=2)
     sim = _sim(vd, w, h, xy, byte_keys=1, packed_map=1)

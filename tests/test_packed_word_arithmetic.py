@@ -1,16 +1,20 @@
 """Host-side check of the position-tagged words' arithmetic (the dJFA passes
 of vd_pass_pk.cuh), written out with numpy integer operations for each word
-layout M (8: up to 32767 seeds; 7: to 2^17 - 1; 6: to 2^18):
+layout M (8: up to 32767 seeds; 7: to 2^17 - 1; 6: to 2^18; 4: to 2^22, the
+label split around the x field and distances saturated at 63):
 
 * a pixel's key of a candidate word is exactly d * 2^ks (+ 2^15 for M = 8)
-  + label whenever the candidate's seed lies in the window [-h, h)^2 around
-  the pixel (h = 2^(M-1)): the guard bit absorbs the borrow out of the x
-  field, the label bits see no borrow, and the masked field bytes read as
-  signed numbers are 2^(8-M) dx and 2^(8-M) dy;
+  + label code whenever the candidate's seed lies in the window [-h, h)^2
+  around the pixel (h = 2^(M-1)) (M = 4: min(d, 63)): the guard bit absorbs
+  the borrow out of the x field, the label bits below it see no borrow, and
+  the masked field bytes read as signed numbers are 2^(8-M) dx and
+  2^(8-M) dy;
 * for any seed, in the window or not, the key's low bits are the label code
   and the distance part does not wrap (wide keys stay below 2^31; narrow
-  ones hold d <= 2^15 in their upper 16 bits, compared as unsigned);
-* keys order in-window candidates as (d, label) does (the tie rule);
+  ones hold d <= 2^15 in their upper 16 bits, compared as unsigned; M = 4
+  keys stay below 63 * 2^26 + 2^26);
+* keys order in-window candidates as (d, label) does (the tie rule; with
+  M = 4 for d < 63, the distances the winner check accepts);
 * a word decodes to its label, the empty word to -1 (with M = 6 and 2^18
   seeds the last seed's code is also the empty code, told apart by the flag
   bit), and the winner check's table index (code + 1) mod 2^lb lands on the
@@ -31,16 +35,18 @@ class Layout:
     def __init__(self, m):
         self.m = m
         self.narrow = m == 8
-        self.lb = 15 if self.narrow else 24 - m
+        self.split = m == 4
+        self.lb = 15 if self.narrow else 26 if self.split else 24 - m
         self.ks = 16 if self.narrow else self.lb
-        self.lm = (1 << self.lb) - 1
+        # the key's label code: all the label bits where the word holds them
+        self.lm = 0x030FFFFF if self.split else (1 << self.lb) - 1
         self.h = 1 << (m - 1)
         self.xm = (1 << m) - 1
-        self.xs = 8 if self.narrow else self.lb
+        self.xs = 8 if self.narrow else 20 if self.split else self.lb
         self.ys = 32 - m
         self.fm = (self.xm << self.xs) | (self.xm << self.ys)
-        self.g = 0x00800000 if self.narrow else 0x01000000
-        self.ef = 0x02000000 if m == 6 else 0
+        self.g = 0x00800000 if self.narrow else 0x04000000 if self.split else 0x01000000
+        self.ef = 0x02000000 if m == 6 else 0x08000000 if self.split else 0
         self.empty = (0xFF | (0x7F << 16) | self.g) if self.narrow else (self.lm | self.g | self.ef)
 
     def neg_pix(self, x, y):
@@ -52,12 +58,21 @@ class Layout:
         if self.narrow:
             return ((l & U(0xFF)) | ((x & U(0xFF)) << U(8)) | ((l & U(0x7F00)) << U(8)) | U(self.g) |
                     ((y & U(0xFF)) << U(24)))
+        if self.split:
+            l = (l & U(0xFFFFF)) | ((l & U(0x300000)) << U(4))
         return l | U(self.g) | ((x & U(self.xm)) << U(self.xs)) | ((y & U(self.xm)) << U(self.ys))
+
+    def code_label(self, c):
+        """The label a key's (or word's) code names (M = 4: the split bits joined)."""
+        c = U(c)
+        if self.split:
+            return ((c & U(0xFFFFF)) | ((c >> U(4)) & U(0x300000))).astype(np.int64)
+        return (c & U(self.lm)).astype(np.int64)
 
     def label(self, w):
         w = U(w)
-        if self.m == 6:
-            return np.where((w & U(self.ef)) != 0, -1, (w & U(self.lm)).astype(np.int64))
+        if self.ef:
+            return np.where((w & U(self.ef)) != 0, -1, self.code_label(w))
         c = ((w & U(0xFF)) | ((w >> U(8)) & U(0x7F00))) if self.narrow else (w & U(self.lm))
         return np.where(c == U(self.lm), -1, c.astype(np.int64))
 
@@ -76,6 +91,9 @@ class Layout:
         if self.narrow:
             # byte permute 0x5420: bytes (w.b0, w.b2, d.b0, d.b1)
             return (U(w) & U(0xFF)) | (((U(w) >> U(16)) & U(0xFF)) << U(8)) | ((d & U(0xFFFF)) << U(16))
+        if self.split:
+            # 256 d, saturated at 63 * 256, times 2^18
+            return (np.minimum(d, U(63 * 256)) * U(1 << 18) + (U(w) & U(self.lm))) & M32
         return (d * U(1 << (8 + self.m)) + (U(w) & U(self.lm))) & M32
 
     def word_of_key(self, key, x, y):
@@ -88,10 +106,17 @@ class Layout:
              ((e << U(16 - self.m)) & U(self.xm << self.ys))) & M32
         return (key & U(self.lm)) | f
 
+    def index(self, key):
+        """The winner check's position-table index: (label + 1) mod 2^22 for
+        M = 4, (code + 1) mod 2^lb otherwise."""
+        if self.split:
+            return (U(self.code_label(key)) + U(1)) & U(0x3FFFFF)
+        return (U(key) + U(1)) & U(self.lm)
 
-LAYOUTS = [Layout(8), Layout(7), Layout(6)]
+
+LAYOUTS = [Layout(8), Layout(7), Layout(6), Layout(4)]
 # largest seed count each layout takes
-N_MAX = {8: 32767, 7: 131071, 6: 262144}
+N_MAX = {8: 32767, 7: 131071, 6: 262144, 4: 1 << 22}
 
 
 def _cases(rng, lay, n, near):
@@ -123,7 +148,11 @@ def test_keys_exact_inside_the_window(lay):
     w = lay.word(lab, sx, sy)
     k = lay.key(w, _pixel_pn(lay, x0, py, i))
     d = ((sx - px) ** 2 + (sy - py) ** 2).astype(np.uint64)
-    want = d * U(1 << lay.ks) + U(lab) + (U(1 << 15) if lay.narrow else U(0))
+    if lay.split:
+        want = np.minimum(d, U(63)) * U(1 << lay.ks) + (w & U(lay.lm))
+        assert (lay.code_label(w & U(lay.lm)) == lab).all()
+    else:
+        want = d * U(1 << lay.ks) + U(lab) + (U(1 << 15) if lay.narrow else U(0))
     assert inside.mean() > 0.9
     np.testing.assert_array_equal(k[inside], want[inside])
 
@@ -135,9 +164,11 @@ def test_key_low_bits_and_range_for_any_seed(lay):
     k = lay.key(lay.word(lab, sx, sy), _pixel_pn(lay, x0, py, i))
     if lay.narrow:
         assert (k < U(1 << 32)).all() and ((k >> U(16)) <= U(1 << 15)).all()
+    elif lay.split:
+        assert (k < U(1 << 32)).all() and ((k >> U(26)) <= U(63)).all()
     else:
         assert (k < U(1 << 31)).all()
-    np.testing.assert_array_equal((k & U(lay.lm)).astype(np.int64), lab)
+    np.testing.assert_array_equal(lay.code_label(k & U(lay.lm)), lab)
     # the empty word's key also names the empty code
     ke = lay.key(np.full(1000, lay.empty, np.uint64), _pixel_pn(lay, x0[:1000], py[:1000], i[:1000]))
     assert ((ke & U(lay.lm)) == U(lay.lm)).all() and (ke < U(1 << 32)).all()
@@ -158,6 +189,10 @@ def test_key_order_is_distance_then_label(lay):
     k2 = lay.key(lay.word(lab2, sx2, sy2), pn)
     d1 = (sx - px) ** 2 + (sy - py) ** 2
     d2 = (sx2 - px) ** 2 + (sy2 - py) ** 2
+    if lay.split:
+        # saturated distances tie at 63 (the check rejects such winners)
+        d1, d2 = np.minimum(d1, 63), np.minimum(d2, 63)
+        assert ((d1 < 63) & (d2 < 63) & ok).mean() > 0.5
     less = (d1 < d2) | ((d1 == d2) & (lab < lab2))
     np.testing.assert_array_equal((k1 < k2)[ok], less[ok])
 
@@ -173,11 +208,24 @@ def test_labels_empty_word_and_check_index(lay):
     if lay.m == 6:
         # 2^18 seeds: the last seed's code is the all-ones code, a real label
         assert int(lay.label(lay.word(np.array([N_MAX[6] - 1]), np.array([5]), np.array([9])))[0]) == N_MAX[6] - 1
+    if lay.split:
+        # 2^22 seeds: the last seed's code is the all-ones code, a real label
+        top = N_MAX[4] - 1
+        assert int(lay.label(lay.word(np.array([top]), np.array([5]), np.array([9])))[0]) == top
+        assert int(lay.code_label(U(lay.lm))) == top
     # the winner check indexes the position table (far entry first) with
-    # (code + 1) mod 2^lb: seeds land on their entry, the empty code on the far one
-    codes = np.concatenate([lab[lab < lay.lm], [lay.lm]]).astype(np.uint64)
-    idx = (codes + U(1)) & U(lay.lm)
-    np.testing.assert_array_equal(idx[:-1], codes[:-1] + U(1))
+    # (label + 1) mod 2^lb (M = 4: mod 2^22, the label joined from its split
+    # code): seeds land on their entry, the empty code on the far one
+    if lay.split:
+        live = lab[lab < N_MAX[4] - 1]
+        codes = np.concatenate([lay.word(live, 0, 0) & U(lay.lm), [U(lay.lm)]]).astype(np.uint64)
+        want = live + 1
+    else:
+        live = lab[lab < lay.lm]
+        codes = np.concatenate([live, [lay.lm]]).astype(np.uint64)
+        want = live + 1
+    idx = lay.index(codes)
+    np.testing.assert_array_equal(idx[:-1].astype(np.int64), want)
     assert int(idx[-1]) == 0
 
 
