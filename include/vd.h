@@ -612,14 +612,16 @@ int vd_server_set_max_batch(vd_server* server, int32_t max_batch);
                                     opt-in.  Results never depend on it */
 #define VD_OPT_SMEM_TILE_ROWS 18 /* rows of that tile: 16 (default, 1024-thread blocks) or 8 (512) */
 #define VD_OPT_PACKED_MAP 19     /* dJFA frames whose last passes (at least two, each with k = 1, 2 or
-                                    a multiple of 4) take the byte-offset key run them on a
+                                    a multiple of 4) take the byte-offset key (up to 2^18 seeds) or
+                                    the clamped key (2^18 + 1 to 2^22) run them on a
                                     position-tagged map: each 32-bit word holds the label and the
-                                    low 6, 7 or 8 bits of its seed's x and y (up to 32767 seeds,
-                                    32768 to 2^17 - 1, 2^17 to 2^18), so that a candidate is scored
-                                    with no table gather; the first of those passes reads the plain
-                                    map and the last writes it again.  -1 = auto (default: the
-                                    byte-offset key's mean-radius and step bounds with the
-                                    layout's window 2^(M-1)), 0 = never, 1 = whenever usable.
+                                    low 8, 7, 6 or 4 bits of its seed's x and y (up to 32767 seeds,
+                                    32768 to 2^17 - 1, 2^17 to 2^18, to 2^22), so that a candidate
+                                    is scored with no table gather; the first of those passes reads
+                                    the plain map and the last writes it again.  -1 = auto
+                                    (default: the byte-offset key's mean-radius and step bounds
+                                    with the layout's window 2^(M-1); with 4 bits also k times the
+                                    frame's first step at most 64), 0 = never, 1 = whenever usable.
                                     Results never depend on it */
 int vd_set_option(vd_ctx* ctx, int32_t option, int64_t value);
 
