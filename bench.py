@@ -60,9 +60,10 @@ def parse_args():
                     help="bounded CPU-oracle sample for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--e2e-labels", type=int, choices=[24, 32], default=24,
-                    help="end-to-end read-back: 24-bit labels (3 B a pixel, lossless up to 16777215 seeds; "
-                         "default) or the int32 map")
+    ap.add_argument("--e2e-labels", choices=["packed", "24", "32"], default="packed",
+                    help="end-to-end read-back: labels bit-packed at the fewest bits the seed count needs "
+                         "(default; 19 bits a pixel for 2^18 seeds), 24-bit labels (3 B a pixel, up to "
+                         "16777215 seeds) or the int32 map")
     ap.add_argument("--no-autotune", action="store_true",
                     help="skip vd_autotune (the pass launch-shape search) before the timed steps")
     ap.add_argument("--metric", choices=["euclid", "manhattan"], default="euclid",
@@ -531,10 +532,17 @@ def run_ours(args):
             apply_tuning(vd, ee, tuned["chosen"])
         ee.jfa(metric=metric)
         pin_disp = torch.from_numpy(disp_host).pin_memory()
-        # the map comes back as 24-bit labels where every label fits (the copy
-        # to the host is the bound of this leg: 3 bytes a pixel instead of 4)
-        bits = 24 if args.e2e_labels == 24 and s <= 0xFFFFFF else 32
-        if bits == 24:
+        # the map comes back bit-packed at the fewest bits the labels need (the
+        # copy to the host is the bound of this leg: 19 bits a pixel for 2^18
+        # seeds instead of 32), or as 24-bit labels, or as the int32 map
+        if args.e2e_labels == "packed":
+            bits = vd.label_bits(s)
+        else:
+            bits = 24 if args.e2e_labels == "24" and s <= 0xFFFFFF else 32
+        if args.e2e_labels == "packed":
+            pin_out = [torch.empty((px * bits + 7) // 8, dtype=torch.uint8).pin_memory() for _ in range(2)]
+            read_back = lambda out: ee.labels_packed_async(out, bits)  # noqa: E731
+        elif bits == 24:
             pin_out = [torch.empty(3 * h * w, dtype=torch.uint8).pin_memory() for _ in range(2)]
             read_back = ee.labels24_async
         else:
@@ -554,13 +562,16 @@ def run_ours(args):
         ee.wait_labels()
         barrier()
         te = max_over_ranks(pg, 1e3 * (time.perf_counter() - t_e2e), dev)
-        if bits == 24:
-            # the last step's map, widened on the host, equals the context's own
+        # the last step's map, widened on the host, equals the context's own
+        if args.e2e_labels == "packed":
+            assert np.array_equal(vd.unpack_labels(pin_out[(K - 1) % 2].numpy(), h, w, bits, rows_per_chunk=256),
+                                  ee.labels())
+        elif bits == 24:
             assert np.array_equal(vd.widen24(pin_out[(K - 1) % 2].numpy(), h, w), ee.labels())
         ee.close()
         e2e = {"value": whole_job_gpx(px * n_djfa, K, world, te), "unit": UNIT,
-               "h2d_bytes_per_step": int(s * 2 * 4), "d2h_bytes_per_step": int(px * bits // 8),
-               "ms_per_step": te / K, "labels": f"{bits}-bit",
+               "h2d_bytes_per_step": int(s * 2 * 4), "d2h_bytes_per_step": int((px * bits + 7) // 8),
+               "ms_per_step": te / K, "labels": f"{bits}-bit" + (" packed" if args.e2e_labels == "packed" else ""),
                "timing": "host wall clock around K steps (pinned displacements in, every step's whole label map "
                          f"read back as {bits}-bit labels, read-back overlapped with the next step)"}
 

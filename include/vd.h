@@ -283,8 +283,21 @@ int vd_get_labels16_async(vd_ctx* ctx, uint16_t* labels);
  * same two snapshot slots as the other asynchronous read-backs.
  */
 int vd_get_labels24_async(vd_ctx* ctx, uint8_t* labels);
+/*
+ * As vd_get_labels_async, into a dense bit stream of `bits`-bit labels
+ * (bits in [1, 32]; the fewest bytes to copy, for pipelines bound by the
+ * host link): label j = y * w + x occupies bits [j * bits, (j + 1) * bits)
+ * of the stream, least significant bit first within little-endian bytes,
+ * the empty label -1 as 2^bits - 1.  `labels` holds ceil(w * h * bits / 8)
+ * bytes.  Needs at most 2^bits - 1 seeds (VD_EINVAL otherwise), so that no
+ * label takes the empty code; the fewest bits for n seeds are the bit length
+ * of n.  Packed on the context's stream into one of the same two snapshot
+ * slots as the other asynchronous read-backs.
+ */
+int vd_get_labels_packed_async(vd_ctx* ctx, uint8_t* labels, int32_t bits);
 /* Waits until every vd_get_labels_async / vd_get_labels16_async /
-   vd_get_labels24_async copy of the context has landed. */
+   vd_get_labels24_async / vd_get_labels_packed_async copy of the context
+   has landed. */
 int vd_wait_labels(vd_ctx* ctx);
 
 /*

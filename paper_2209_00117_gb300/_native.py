@@ -55,6 +55,7 @@ SIGNATURES = {
     "vd_get_labels_async": (_int, [_p, _p]),
     "vd_get_labels16_async": (_int, [_p, _p]),
     "vd_get_labels24_async": (_int, [_p, _p]),
+    "vd_get_labels_packed_async": (_int, [_p, _p, _i32]),
     "vd_wait_labels": (_int, [_p]),
     "vd_similarity": (_int, [_p, _p, _p, _int, _i32, _PU64, _PU64]),
     "vd_similarity_ctx": (_int, [_p, _p, _PU64]),

@@ -2112,6 +2112,105 @@ extern "C" int vd_get_labels24_async(vd_ctx* c, uint8_t* labels) {
   return VD_OK;
 }
 
+// Dense bit-packed copy of a label map (rows of w out of a pitched map):
+// label j = y w + x occupies bits [j b, (j + 1) b) of a little-endian stream
+// of 32-bit words, the empty label -1 as 2^b - 1.  A thread packs 32
+// consecutive labels into b words (32 b bits), staged in shared memory so
+// that the block's words leave in coalesced stores; words past the stream's
+// end (ceil(w h b / 32)) are not written.
+constexpr int kPackThreads = 128;
+static __global__ void __launch_bounds__(kPackThreads)
+    k_pack_bits(const int32_t* __restrict__ src, int pitch, int w, int h, int bits, uint32_t* __restrict__ dst,
+                int64_t words) {
+  __shared__ uint32_t sm[kPackThreads * 32];
+  const int64_t n = static_cast<int64_t>(w) * h;
+  const int64_t j0 = (static_cast<int64_t>(blockIdx.x) * kPackThreads + threadIdx.x) * 32;
+  const uint32_t mask = bits >= 32 ? 0xFFFFFFFFu : (1u << bits) - 1u;
+  uint32_t v[32];
+  if (j0 < n && w % 32 == 0) {
+    // the 32 labels lie in one row (x is a multiple of 32), in 16-byte vectors
+    const int64_t y = j0 / w;
+    const int4* p = reinterpret_cast<const int4*>(src + y * pitch + (j0 - y * w));
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int4 t = __ldg(p + q);
+      v[4 * q] = static_cast<uint32_t>(t.x);
+      v[4 * q + 1] = static_cast<uint32_t>(t.y);
+      v[4 * q + 2] = static_cast<uint32_t>(t.z);
+      v[4 * q + 3] = static_cast<uint32_t>(t.w);
+    }
+  } else {
+    int64_t y = 0;
+    int x = 0;
+    if (j0 < n) {
+      y = j0 / w;
+      x = static_cast<int>(j0 - y * w);
+    }
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+      v[i] = j0 + i < n ? static_cast<uint32_t>(__ldg(src + y * pitch + x)) : 0u;
+      if (++x == w) {
+        x = 0;
+        ++y;
+      }
+    }
+  }
+  uint32_t* s = sm + threadIdx.x * bits;
+  unsigned long long acc = 0;
+  int have = 0, o = 0;
+#pragma unroll
+  for (int i = 0; i < 32; ++i) {
+    acc |= static_cast<unsigned long long>(v[i] & mask) << have;
+    have += bits;
+    if (have >= 32) {
+      s[o++] = static_cast<uint32_t>(acc);
+      acc >>= 32;
+      have -= 32;
+    }
+  }
+  __syncthreads();
+  const int64_t base = static_cast<int64_t>(blockIdx.x) * kPackThreads * bits;
+  for (int i = threadIdx.x; i < kPackThreads * bits; i += kPackThreads)
+    if (base + i < words) dst[base + i] = sm[i];
+}
+
+extern "C" int vd_get_labels_packed_async(vd_ctx* c, uint8_t* labels, int32_t bits) {
+  VD_CHECK_CTX(c);
+  if (!labels) return vd_fail(VD_EINVAL, "null output");
+  if (bits < 1 || bits > 32) return vd_fail(VD_EINVAL, "label width %d outside [1, 32]", bits);
+  if (bits < 32 && static_cast<int64_t>(c->n) > (int64_t{1} << bits) - 1)
+    return vd_fail(VD_EINVAL, "%d-bit labels need at most %lld seeds (have %d)", bits,
+                   static_cast<long long>((int64_t{1} << bits) - 1), c->n);
+  int rc = ensure_async(c);
+  if (rc) return rc;
+  const int i = c->snap_next;
+  c->snap_next ^= 1;
+  if (c->copy_pending[i]) {
+    rc = vd_cuda_check(cudaEventSynchronize(c->copy_done[i]), "wait for read-back");
+    if (rc) return rc;
+    c->copy_pending[i] = false;
+  }
+  // pack the current map into the slot on the compute stream (later frames
+  // rewrite the map), then copy the stream out on the copy stream
+  const int64_t n = static_cast<int64_t>(c->w) * c->h;
+  const int64_t words = (n * bits + 31) / 32;
+  const int64_t blocks = ((n + 31) / 32 + kPackThreads - 1) / kPackThreads;
+  k_pack_bits<<<static_cast<unsigned>(blocks), kPackThreads, 0, c->stream>>>(
+      c->buf[c->cur], c->pitch, c->w, c->h, bits, reinterpret_cast<uint32_t*>(c->snap[i]), words);
+  rc = vd_cuda_check(cudaGetLastError(), "pack labels");
+  if (!rc) rc = vd_cuda_check(cudaEventRecord(c->snap_ready[i], c->stream), "event");
+  if (!rc) rc = vd_cuda_check(cudaStreamWaitEvent(c->copy_stream, c->snap_ready[i], 0), "wait event");
+  const size_t bytes = static_cast<size_t>((n * bits + 7) / 8);
+  if (!rc)
+    rc = vd_cuda_check(cudaMemcpyAsync(labels, c->snap[i], bytes, cudaMemcpyDeviceToHost, c->copy_stream),
+                       "copy labels out");
+  if (!rc) rc = vd_cuda_check(cudaEventRecord(c->copy_done[i], c->copy_stream), "event");
+  if (rc) return rc;
+  ++c->launches;
+  c->copy_pending[i] = true;
+  return VD_OK;
+}
+
 extern "C" int vd_wait_labels(vd_ctx* c) {
   VD_CHECK_CTX(c);
   for (int i = 0; i < 2; ++i) {

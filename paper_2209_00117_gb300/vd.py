@@ -73,6 +73,36 @@ def widen24(packed, h: int, w: int) -> np.ndarray:
     return np.where(v == 0xFFFFFF, -1, v).astype(np.int32).reshape(h, w)
 
 
+def label_bits(n_seeds: int) -> int:
+    """The fewest bits a packed read-back (vd_get_labels_packed_async) takes
+    for n seeds: labels 0 .. n - 1 and the empty code 2^bits - 1 apart."""
+    return max(1, int(n_seeds).bit_length())
+
+
+def unpack_labels(packed, h: int, w: int, bits: int, rows_per_chunk: int = 1024) -> np.ndarray:
+    """int32 labels (h x w) from a packed read-back: label j = y w + x at bits
+    [j bits, (j + 1) bits) of the little-endian stream, 2^bits - 1 the empty
+    label -1.  Unpacked a band of rows at a time."""
+    buf = np.asarray(packed, np.uint8).reshape(-1)
+    n = h * w
+    if buf.size != (n * bits + 7) // 8:
+        raise ValueError(f"expected {(n * bits + 7) // 8} bytes, got {buf.size}")
+    pad = np.zeros(buf.size + 8, np.uint8)
+    pad[:buf.size] = buf
+    empty = (1 << bits) - 1
+    out = np.empty(n, np.int32)
+    step = max(1, rows_per_chunk) * w
+    for j0 in range(0, n, step):
+        j = np.arange(j0, min(n, j0 + step), dtype=np.int64) * bits
+        byte = j >> 3
+        v = np.zeros(j.size, np.uint64)
+        for i in range(5):  # a label spans at most 5 bytes (7 + 32 bits)
+            v |= pad[byte + i].astype(np.uint64) << np.uint64(8 * i)
+        v = (v >> (j & 7).astype(np.uint64)) & np.uint64(empty)
+        out[j0:j0 + j.size] = np.where(v == empty, -1, v.astype(np.int64))
+    return out.reshape(h, w)
+
+
 def _schedule(fn, *args):
     ks = np.zeros(MAX_PASSES, np.int32)
     nbs = np.zeros(MAX_PASSES, np.int32)
@@ -349,6 +379,28 @@ class VoronoiSim:
         if n != 3 * self.w * self.h:
             raise ValueError(f"expected {3 * self.w * self.h} bytes, got {n}")
         N.check(self._lib.vd_get_labels24_async(self._h, ptr))
+        return out
+
+    def labels_packed_async(self, out, bits: int):
+        """As :meth:`labels_async` into a contiguous host uint8 array or tensor
+        of ceil(h * w * bits / 8) bytes: a bit stream of `bits`-bit labels,
+        the empty label as 2^bits - 1 (at most 2^bits - 1 seeds; see
+        :func:`label_bits`); :func:`unpack_labels` turns it back into int32
+        labels."""
+        if _is_torch(out):
+            if str(out.dtype) != "torch.uint8" or not out.is_contiguous() or out.is_cuda:
+                raise TypeError("out must be a contiguous host uint8 tensor")
+            n, ptr = out.numel(), out.data_ptr()
+        else:
+            if not isinstance(out, np.ndarray) or out.dtype != np.uint8 or not out.flags.c_contiguous:
+                raise TypeError("out must be a C-contiguous uint8 numpy array")
+            if not out.flags.writeable:
+                raise ValueError("output array is read-only")
+            n, ptr = out.size, out.ctypes.data
+        want = (self.w * self.h * int(bits) + 7) // 8
+        if n != want:
+            raise ValueError(f"expected {want} bytes, got {n}")
+        N.check(self._lib.vd_get_labels_packed_async(self._h, ptr, int(bits)))
         return out
 
     def wait_labels(self):

@@ -517,6 +517,73 @@ def test_async_label_readback_24bit_refuses_large_counts(vd):
     sim.close()
 
 
+@pytest.mark.parametrize("w,h,s,extra", [(600, 400, 2500, 0), (601, 403, 70000, 0), (1024, 512, 1 << 18, 0),
+                                         (33, 5, 9, 0), (64, 40, 7, 27), (96, 30, 100, 25)])
+def test_async_label_readback_packed(vd, w, h, s, extra):
+    """The packed read-back at the fewest bits for the seed count (plus
+    `extra`, up to 32 bits a label): every frame's bit stream, interleaved
+    with 32-bit read-backs through the same two slots, equals the
+    synchronous int32 read, unpacked on the host and checked bit by bit
+    against a plain bit-by-bit packing of that read (empty labels as all
+    ones): widths a multiple of 32 (one row a thread) and not (labels of a
+    thread across rows), a stream ending inside a word."""
+    import torch
+
+    bits = vd.label_bits(s) + extra
+    D = 2
+    xy = inputs.uniform_seeds(w, h, s, seed=19)
+    disp = inputs.displacements(s, D, 4, seed=19)
+    a = _sim(vd, w, h, xy)
+    b = _sim(vd, w, h, xy)
+    src = np.random.default_rng(s + 3).integers(-1, s, size=(h, w), dtype=np.int32)
+    a.set_labels(src)
+    b.set_labels(src)
+    nbytes = (w * h * bits + 7) // 8
+    op = [torch.empty(nbytes, dtype=torch.uint8).pin_memory() for _ in range(5)]
+    o32 = [torch.empty((h, w), dtype=torch.int32).pin_memory() for _ in range(5)]
+    want = []
+    for t in range(5):
+        if t:
+            for sim in (a, b):
+                sim.move(disp[t - 1])
+                sim.djfa_step(d_max=D)
+        a.labels_packed_async(op[t], bits)
+        a.labels_async(o32[t])
+        want.append(b.labels())
+    a.wait_labels()
+    for t in range(5):
+        np.testing.assert_array_equal(vd.unpack_labels(op[t].numpy(), h, w, bits, rows_per_chunk=7), want[t],
+                                      err_msg=f"frame {t}")
+        np.testing.assert_array_equal(o32[t].numpy(), want[t], err_msg=f"frame {t}")
+    # bit-exact stream on the last frame against an independent packing
+    codes = want[-1].astype(np.int64).reshape(-1) & ((1 << bits) - 1)
+    bitplanes = ((codes[:, None] >> np.arange(bits)) & 1).astype(np.uint8).reshape(-1)
+    ref = np.packbits(bitplanes, bitorder="little")
+    np.testing.assert_array_equal(op[-1].numpy(), ref)
+    a.close()
+    b.close()
+
+
+def test_async_label_readback_packed_refuses(vd):
+    """A width that cannot hold every label apart from the empty code, or one
+    outside [1, 32]: VD_EINVAL before anything is queued."""
+    from paper_2209_00117_gb300._native import VD_EINVAL, VDError
+
+    w, h, s = 64, 64, 1 << 10
+    sim = vd.VoronoiSim(w, h, s)
+    from paper_2209_00117_gb300 import _native as N
+
+    for bits in (10, 0, 33):
+        buf = np.empty((w * h * 32 + 7) // 8, np.uint8)
+        with pytest.raises(VDError) as ei:
+            N.check(sim._lib.vd_get_labels_packed_async(sim._h, buf.ctypes.data, bits))
+        assert ei.value.code == VD_EINVAL
+    out = np.empty((w * h * 11 + 7) // 8, np.uint8)
+    sim.labels_packed_async(out, 11)
+    sim.wait_labels()
+    sim.close()
+
+
 def test_async_label_readback_16bit_refuses_large_counts(vd):
     """From 65536 seeds on a label no longer fits 16 bits: VD_EINVAL."""
     from paper_2209_00117_gb300._native import VD_EINVAL, VDError
