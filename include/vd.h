@@ -208,10 +208,9 @@ int vd_djfa_step(vd_ctx* ctx, int32_t d_max, int32_t vn_waves, int32_t extra_pas
 /*
  * One whole timestep (Algorithm 1's loop body): the move of vd_move_seeds
  * (same arguments, same result) followed by the frame of vd_djfa_step (same
- * arguments; the repair schedule after a removal).  The stamp's first half is
- * done by the move kernel, and with VD_OPT_USE_GRAPHS the whole step replays
- * as one graph whose move arguments are replaced every call.  Results equal
- * vd_move_seeds + vd_djfa_step bit for bit.
+ * arguments; the repair schedule after a removal).  With VD_OPT_USE_GRAPHS
+ * the whole step replays as one graph whose move arguments are replaced every
+ * call.  Results equal vd_move_seeds + vd_djfa_step bit for bit.
  */
 int vd_step(vd_ctx* ctx, const int32_t* dxy, int dxy_on_device, int32_t max_disp, uint64_t rng_seed,
             uint64_t stream_id, int64_t step, int32_t d_max, int32_t vn_waves, int32_t extra, int32_t metric);

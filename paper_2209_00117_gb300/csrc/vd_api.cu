@@ -534,17 +534,13 @@ int launch_fill(int32_t* buf, int64_t n_elems, int32_t v, cudaStream_t st) {
 
 int launch_stamp(const MapView& m, int32_t* labels, bool mark, cudaStream_t st, int64_t* launches, bool pdl) {
   const int blocks = grid1d(m.n, 256);
-  if (mark) {
-    const cudaError_t e = launch_k(vdk::k_stamp_mark, dim3(blocks), dim3(256), st, false, labels, m.pitch, m.seeds, m.n);
-    if (e != cudaSuccess) return vd_cuda_check(e, "stamp launch");
-    ++*launches;
-  }
-  // the minimum half follows the mark half or a fill: it may start while that drains
-  // (and, for the wide position-tagged layouts, the frame's seed entries of
-  // those passes)
+  // one kernel: on a map with stale labels (mark) the swap-and-restore
+  // stamp, on an emptied one the atomic minimum alone; either may start
+  // while its predecessor drains, and writes the frame's seed entries of the
+  // wide and split position-tagged layouts
   const int pkm = pk_bits(m.n) == 8 ? 0 : pk_bits(m.n);
-  const cudaError_t e = launch_k(vdk::k_stamp_min, dim3(blocks), dim3(256), st, pdl, labels, m.pitch, m.seeds, m.n,
-                                 pkm ? m.pkf : nullptr, m.ptable - 1, pkm);
+  const cudaError_t e = launch_k(mark ? vdk::k_stamp_xchg : vdk::k_stamp_min, dim3(blocks), dim3(256), st, pdl,
+                                 labels, m.pitch, m.seeds, m.n, pkm ? m.pkf : nullptr, m.ptable - 1, pkm);
   if (e != cudaSuccess) return vd_cuda_check(e, "stamp launch");
   ++*launches;
   return vd_cuda_check(cudaGetLastError(), "stamp launch");
@@ -563,8 +559,6 @@ int launch_move(int2* seeds, int2* table, uint32_t* ptable, int n, const int2* d
   a.max_disp = max_disp;
   a.key = key;
   a.step = step;
-  a.mark = nullptr;
-  a.pitch = 0;
   vdk::k_move<<<grid1d(n, 256), 256, 0, st>>>(a);
   return vd_cuda_check(cudaGetLastError(), "move launch");
 }
@@ -1256,7 +1250,7 @@ extern "C" int vd_djfa_step(vd_ctx* c, int32_t d_max, int32_t vn_waves, int32_t 
   const int cur_after = c->cur ^ (nl & 1);
   auto body = [&]() -> int {
     vdi::Profiler* pr = prof_of(c);
-    const int pi = pr ? pr->begin(VD_KERNEL_STAMP, 2 * static_cast<int64_t>(c->n), c->stream) : -1;
+    const int pi = pr ? pr->begin(VD_KERNEL_STAMP, c->n, c->stream) : -1;
     const int rc = vdi::launch_stamp(view(c), c->buf[c->cur], true, c->stream, &c->launches, c->tune.pdl != 0);
     if (pr) pr->end(pi, c->stream);
     if (rc) return rc;
@@ -1266,7 +1260,7 @@ extern "C" int vd_djfa_step(vd_ctx* c, int32_t d_max, int32_t vn_waves, int32_t 
     return vdi::run_passes(view(c), c->buf, &c->cur, ks, nbs, n, metric, c->tune, c->stream, &c->launches, pr,
                            true);
   };
-  const int rc = run_frame(c, std::make_tuple(1, c->cur, d_max, vn_waves, extra, metric, repair ? 1 : 0), nl + 2,
+  const int rc = run_frame(c, std::make_tuple(1, c->cur, d_max, vn_waves, extra, metric, repair ? 1 : 0), nl + 1,
                            cur_after, body);
   if (!rc) c->repair = false;
   return rc;
@@ -1289,8 +1283,6 @@ extern "C" int vd_step(vd_ctx* c, const int32_t* dxy, int dxy_on_device, int32_t
   ma.max_disp = max_disp;
   ma.key = vdi::rng_key(rng_seed, stream_id);
   ma.step = static_cast<uint64_t>(step);
-  ma.mark = c->buf[c->cur];
-  ma.pitch = c->pitch;
   if (dxy) {
     if (dxy_on_device) {
       if (reinterpret_cast<uintptr_t>(dxy) % alignof(int2) != 0)
@@ -1327,7 +1319,7 @@ extern "C" int vd_step(vd_ctx* c, const int32_t* dxy, int dxy_on_device, int32_t
     int rc = vd_cuda_check(cudaGetLastError(), "move launch");
     if (rc) return rc;
     pi = pr ? pr->begin(VD_KERNEL_STAMP, c->n, c->stream) : -1;
-    rc = vdi::launch_stamp(view(c), c->buf[c->cur], false, c->stream, &c->launches, c->tune.pdl != 0);
+    rc = vdi::launch_stamp(view(c), c->buf[c->cur], true, c->stream, &c->launches, c->tune.pdl != 0);
     if (pr) pr->end(pi, c->stream);
     if (rc) return rc;
     return vdi::run_passes(view(c), c->buf, &c->cur, ks, nbs, n, metric, c->tune, c->stream, &c->launches, pr,

@@ -803,13 +803,10 @@ struct MoveArgs {
   const int2* dxy;  // given displacements, or null: SplitMix64 draws in [-max_disp, max_disp]
   int w, h, max_disp;
   uint64_t key, step;
-  int32_t* mark;    // non-null: also the stamp's first half on this map (pitch below)
-  int pitch;
 };
 
 // SimulateParticles (Algorithm 1): p_k <- clamp(p_k + delta_k) on the grid;
-// also refreshes the seed's pass-table entries and, when a.mark is set,
-// writes k at its new pixel (the first half of the stamp that follows).
+// also refreshes the seed's pass-table entries.
 static __global__ void k_move(MoveArgs a) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= a.n) return;
@@ -831,28 +828,59 @@ static __global__ void k_move(MoveArgs a) {
   a.seeds[k] = p;
   a.table[k + 1] = table_entry(p);
   a.ptable[k + 1] = pack_pos(p.x, p.y);
-  if (a.mark != nullptr) a.mark[static_cast<int64_t>(p.y) * a.pitch + p.x] = k;
 }
 
-// Stamp, first half: every seed pixel is overwritten with one of the indices
-// standing on it (which one does not matter), replacing any stale label.
-static __global__ void k_stamp_mark(int32_t* __restrict__ labels, int pitch, const int2* __restrict__ seeds,
-                             int n) {
+// The stamp on a map with stale labels (reading R4: each seed pixel gets the
+// lowest index standing on it; the rest of the map is kept), one random
+// access a seed: seed k swaps itself into its pixel and, when the label it
+// took out is a lower index r whose seed stands on the same pixel, puts r
+// back with an atomic minimum.  Every seed at the pixel swaps once, so after
+// the last write of the lowest of them, m, any later swap takes m out and
+// its seed writes m back: the pixel ends at m.  (A stale label or an empty
+// one is dropped; the positions are the move's, read after it completed.)
+// It replaces an overwrite of every seed pixel followed by an atomic minimum
+// on each: two rounds of scattered sector read-modify-writes in DRAM instead
+// of one (8192^2 with 2^22 seeds: 0.28 ms a frame for the two).  With pk_m
+// it also writes the seed entries of the position-tagged passes, as
+// k_stamp_min.
+__device__ __forceinline__ void stamp_seed_entries(int k, int2 p, uint2* __restrict__ pkf,
+                                                   const uint32_t* __restrict__ parena, int pk_m) {
+  // the word bits of layout pk_m: wide, bit 24 set, x mod 2^m at
+  // [24 - m, 24), y mod 2^m at [32 - m, 32); split (m = 4), label bits
+  // 20-21 at [24, 26), bit 26 set, x mod 16 at [20, 24), y mod 16 at [28, 32)
+  const uint32_t xm = (1u << pk_m) - 1u;
+  const uint32_t f =
+      pk_m == 4 ? ((static_cast<uint32_t>(k) & 0x300000u) << 4) | (1u << 26) |
+                      ((static_cast<uint32_t>(p.x) & 15u) << 20) | ((static_cast<uint32_t>(p.y) & 15u) << 28)
+                : (1u << 24) | ((static_cast<uint32_t>(p.x) & xm) << (24 - pk_m)) |
+                      ((static_cast<uint32_t>(p.y) & xm) << (32 - pk_m));
+  pkf[k + 1] = make_uint2(pack_pos(p.x, p.y), f);
+  if (k == 0) pkf[0] = make_uint2(parena[0], 0u);
+}
+
+static __global__ void k_stamp_xchg(int32_t* __restrict__ labels, int pitch, const int2* __restrict__ seeds, int n,
+                                    uint2* __restrict__ pkf, const uint32_t* __restrict__ parena, int pk_m) {
   pdl_trigger();
   pdl_wait();
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n) return;
   const int2 p = seeds[k];
-  labels[static_cast<int64_t>(p.y) * pitch + p.x] = k;
+  unsigned int* px = reinterpret_cast<unsigned int*>(labels + static_cast<int64_t>(p.y) * pitch + p.x);
+  const int r = static_cast<int>(atomicExch(px, static_cast<unsigned int>(k)));
+  if (r >= 0 && r < k) {
+    const int2 q = seeds[r];
+    if (q.x == p.x && q.y == p.y) atomicMin(px, static_cast<unsigned int>(r));
+  }
+  if (pk_m) stamp_seed_entries(k, p, pkf, parena, pk_m);
 }
 
-// Stamp, second half: the lowest index standing on the pixel wins.  As
-// unsigned, -1 is the largest value, so this also stamps an emptied map.
-// With pk_m = 6, 7 or 4 it also writes the frame's entries of the
-// position-tagged passes' seed table (pkf: n + 1 entries {x | y << 16, the
-// seed's word bits but the label's low bits}, [0] the far position; parena:
-// the packed positions with the far one first): the stamp runs right before
-// every dJFA frame's passes, after the move.
+// The stamp on an emptied map: the lowest index standing on the pixel wins
+// (as unsigned, -1 is the largest value).  With pk_m = 6, 7 or 4 it also
+// writes the frame's entries of the position-tagged passes' seed table (pkf:
+// n + 1 entries {x | y << 16, the seed's word bits but the label's low
+// bits}, [0] the far position; parena: the packed positions with the far one
+// first): the stamp runs right before every dJFA frame's passes, after the
+// move.
 static __global__ void k_stamp_min(int32_t* __restrict__ labels, int pitch, const int2* __restrict__ seeds,
                             int n, uint2* __restrict__ pkf, const uint32_t* __restrict__ parena, int pk_m) {
   pdl_trigger();
@@ -862,19 +890,7 @@ static __global__ void k_stamp_min(int32_t* __restrict__ labels, int pitch, cons
   const int2 p = seeds[k];
   atomicMin(reinterpret_cast<unsigned int*>(labels + static_cast<int64_t>(p.y) * pitch + p.x),
             static_cast<unsigned int>(k));
-  if (pk_m) {
-    // the word bits of layout pk_m: wide, bit 24 set, x mod 2^m at
-    // [24 - m, 24), y mod 2^m at [32 - m, 32); split (m = 4), label bits
-    // 20-21 at [24, 26), bit 26 set, x mod 16 at [20, 24), y mod 16 at [28, 32)
-    const uint32_t xm = (1u << pk_m) - 1u;
-    const uint32_t f =
-        pk_m == 4 ? ((static_cast<uint32_t>(k) & 0x300000u) << 4) | (1u << 26) |
-                        ((static_cast<uint32_t>(p.x) & 15u) << 20) | ((static_cast<uint32_t>(p.y) & 15u) << 28)
-                  : (1u << 24) | ((static_cast<uint32_t>(p.x) & xm) << (24 - pk_m)) |
-                        ((static_cast<uint32_t>(p.y) & xm) << (32 - pk_m));
-    pkf[k + 1] = make_uint2(pack_pos(p.x, p.y), f);
-    if (k == 0) pkf[0] = make_uint2(parena[0], 0u);
-  }
+  if (pk_m) stamp_seed_entries(k, p, pkf, parena, pk_m);
 }
 
 static __global__ void k_fill(int4* __restrict__ p, int64_t n4, int v) {
