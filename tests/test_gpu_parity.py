@@ -155,6 +155,39 @@ def test_stamp_collisions_lowest_index(vd, orc):
     sim.close()
 
 
+@pytest.mark.parametrize("case", ["one_pixel", "stale_seed_labels", "empty_and_large"])
+def test_stamp_swap_and_restore(vd, orc, case):
+    """The stamp on a map with stale labels takes one swap a seed and puts a
+    lower index back when its seed stands on the same pixel: every seed on
+    one pixel (the chain of swaps is as long as it gets), stale labels that
+    name seeds now standing on the pixel (the label taken out by the first
+    swap is itself a seed there), and a map of empty labels with 200000
+    seeds on 64 x 64 pixels; each equal to the oracle's stamp."""
+    w, h = 64, 40
+    g = np.random.default_rng(7)
+    if case == "one_pixel":
+        n = 5000
+        xy = np.tile(np.array([[3, 2]], np.int32), (n, 1))
+        prev = g.integers(0, n, size=(h, w), dtype=np.int32)
+    elif case == "stale_seed_labels":
+        n = 2000
+        xy = inputs.uniform_seeds(6, 4, n, seed=3)
+        # every pixel of the corner names one of the seeds now standing on it
+        prev = g.integers(0, n, size=(h, w), dtype=np.int32)
+        for k in range(n - 1, -1, -1):
+            prev[xy[k, 1], xy[k, 0]] = k if k % 3 else prev[xy[k, 1], xy[k, 0]]
+    else:
+        w, h, n = 64, 64, 200000
+        xy = inputs.uniform_seeds(w, h, n, seed=5)
+        prev = np.full((h, w), -1, np.int32)
+    sim = _sim(vd, w, h, xy)
+    for _ in range(2):
+        sim.set_labels(prev)
+        sim.stamp()
+        np.testing.assert_array_equal(sim.labels(), orc.stamp(w, h, xy, prev))
+    sim.close()
+
+
 def test_move_given_and_rng(vd, orc):
     w, h, s = 500, 300, 4000
     xy = inputs.uniform_seeds(w, h, s, seed=2)
