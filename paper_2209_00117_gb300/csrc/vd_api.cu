@@ -658,6 +658,14 @@ struct vd_ctx {
   uint32_t* ptable = nullptr;  // n + 1 packed positions, [0] = far position
   uint2* pkf = nullptr;        // n + 1 entries of the position-tagged passes, [0] = far position
   int2* dxy_stage = nullptr;
+  // vd_step's host displacements: two device buffers (capacity dxy_in_cap)
+  // filled on h2d_stream while the previous step computes
+  int2* dxy_in[2] = {nullptr, nullptr};
+  int dxy_in_cap = 0;
+  int dxy_next = 0;
+  cudaStream_t h2d_stream = nullptr;
+  cudaEvent_t dxy_ready[2] = {nullptr, nullptr};
+  cudaEvent_t dxy_free[2] = {nullptr, nullptr};
   unsigned long long* counters = nullptr;      // [0] n_exact, [1] n_match, [2] flag
   unsigned long long* host_counters = nullptr;  // pinned mirror
   int32_t* stage_a = nullptr;  // dense w*h staging (exact distances / exact labels)
@@ -739,6 +747,13 @@ static void ctx_free(vd_ctx* c) {
   cudaFree(c->ptable);
   cudaFree(c->pkf);
   cudaFree(c->dxy_stage);
+  if (c->h2d_stream) cudaStreamSynchronize(c->h2d_stream);
+  for (int i = 0; i < 2; ++i) {
+    cudaFree(c->dxy_in[i]);
+    if (c->dxy_ready[i]) cudaEventDestroy(c->dxy_ready[i]);
+    if (c->dxy_free[i]) cudaEventDestroy(c->dxy_free[i]);
+  }
+  if (c->h2d_stream) cudaStreamDestroy(c->h2d_stream);
   cudaFree(c->counters);
   cudaFreeHost(c->host_counters);
   cudaFree(c->stage_a);
@@ -1266,6 +1281,33 @@ extern "C" int vd_djfa_step(vd_ctx* c, int32_t d_max, int32_t vn_waves, int32_t 
   return rc;
 }
 
+// The stream, events and two buffers of vd_step's host displacements.
+static int ensure_h2d(vd_ctx* c) {
+  int rc = VD_OK;
+  if (!c->h2d_stream) {
+    rc = vd_cuda_check(cudaStreamCreateWithFlags(&c->h2d_stream, cudaStreamNonBlocking), "stream");
+    for (int i = 0; i < 2 && !rc; ++i) {
+      rc = vd_cuda_check(cudaEventCreateWithFlags(&c->dxy_ready[i], cudaEventDisableTiming), "event");
+      if (!rc) rc = vd_cuda_check(cudaEventCreateWithFlags(&c->dxy_free[i], cudaEventDisableTiming), "event");
+    }
+    if (rc) return rc;
+  }
+  if (c->dxy_in_cap < c->n) {
+    // (every copy into the old buffers was waited for by the compute stream)
+    rc = vd_cuda_check(cudaStreamSynchronize(c->stream), "synchronize");
+    for (int i = 0; i < 2; ++i) {
+      cudaFree(c->dxy_in[i]);
+      c->dxy_in[i] = nullptr;
+    }
+    c->dxy_in_cap = 0;
+    for (int i = 0; i < 2 && !rc; ++i)
+      rc = ctx_alloc(reinterpret_cast<void**>(&c->dxy_in[i]), sizeof(int2) * static_cast<size_t>(c->cap), "moves");
+    if (rc) return rc;
+    c->dxy_in_cap = c->cap;
+  }
+  return VD_OK;
+}
+
 extern "C" int vd_step(vd_ctx* c, const int32_t* dxy, int dxy_on_device, int32_t max_disp, uint64_t rng_seed,
                        uint64_t stream_id, int64_t step, int32_t d_max, int32_t vn_waves, int32_t extra,
                        int32_t metric) {
@@ -1303,10 +1345,25 @@ extern "C" int vd_step(vd_ctx* c, const int32_t* dxy, int dxy_on_device, int32_t
     n = vd_jfa_schedule(c->w, c->h, extra, ks, nbs, VD_MAX_PASSES);
     if (n < 0) return n;
   }
+  // host displacements come in on their own stream into one of two buffers,
+  // so that the copy overlaps the previous step instead of following it;
+  // the step waits for it, and the copy into a buffer waits for the step
+  // that last read it
+  int dslot = -1;
   if (dxy && !dxy_on_device) {
-    const int rc = vd_cuda_check(cudaMemcpyAsync(c->dxy_stage, dxy, sizeof(int2) * c->n, cudaMemcpyHostToDevice,
-                                                 c->stream), "copy moves");
+    int rc = ensure_h2d(c);
     if (rc) return rc;
+    dslot = c->dxy_next;
+    c->dxy_next ^= 1;
+    rc = vd_cuda_check(cudaStreamWaitEvent(c->h2d_stream, c->dxy_free[dslot], 0), "wait event");
+    if (!rc)
+      rc = vd_cuda_check(cudaMemcpyAsync(c->dxy_in[dslot], dxy, sizeof(int2) * c->n, cudaMemcpyHostToDevice,
+                                         c->h2d_stream),
+                         "copy moves");
+    if (!rc) rc = vd_cuda_check(cudaEventRecord(c->dxy_ready[dslot], c->h2d_stream), "event");
+    if (!rc) rc = vd_cuda_check(cudaStreamWaitEvent(c->stream, c->dxy_ready[dslot], 0), "wait event");
+    if (rc) return rc;
+    ma.dxy = c->dxy_in[dslot];
   }
   const int nl = count_launches(ks, nbs, n, c->tune);
   const int cur_after = c->cur ^ (nl & 1);
@@ -1328,6 +1385,10 @@ extern "C" int vd_step(vd_ctx* c, const int32_t* dxy, int dxy_on_device, int32_t
   const int rc = run_frame(c, std::make_tuple(2, c->cur, d_max, vn_waves, extra, metric, repair ? 1 : 0), nl + 2,
                            cur_after, body, &ma);
   if (!rc) c->repair = false;
+  if (dslot >= 0) {
+    const int erc = vd_cuda_check(cudaEventRecord(c->dxy_free[dslot], c->stream), "event");
+    if (!rc) return erc;
+  }
   return rc;
 }
 
