@@ -1313,7 +1313,7 @@ extern "C" int vd_step(vd_ctx* c, const int32_t* dxy, int dxy_on_device, int32_t
                        int32_t metric) {
   VD_CHECK_CTX(c);
   if (check_metric(metric)) return VD_EINVAL;
-  // the move, as vd_move_seeds, with the stamp's first half folded in
+  // the move, as vd_move_seeds
   vdk::MoveArgs ma;
   ma.seeds = c->seeds;
   ma.table = c->table;
