@@ -669,7 +669,12 @@ def run_batched(args):
     b.set_seeds(np.concatenate(xys))
     b.jfa()
     b.configure(d_max=D)
-    best, cand_ms = b.autotune(steps=3, max_disp=D, rng_seed=0)
+    if args.no_autotune:
+        # the autotuner's usual choice: launch per round, 4 rows a thread
+        b.set_option(vd.BOPT_ROWS_PER_THREAD, 4)
+        best, cand_ms = None, []
+    else:
+        best, cand_ms = b.autotune(steps=3, max_disp=D, rng_seed=0)
     px, pp, n_seeds = b.work()
     for _ in range(W):
         b.step(None, max_disp=D, rng_seed=0)
@@ -756,8 +761,9 @@ def run_batched(args):
 
 
 def b_mode(candidate):
-    """Autotuner candidates 3..5 are the persistent launch shapes."""
-    return candidate >= 3
+    """Autotuner candidates 3 and up are the persistent launch shapes (None:
+    not autotuned, launch per round)."""
+    return candidate is not None and candidate >= 3
 
 
 def run_serve(args):
