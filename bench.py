@@ -761,9 +761,9 @@ def run_batched(args):
 
 
 def b_mode(candidate):
-    """Autotuner candidates 3 and up are the persistent launch shapes (None:
-    not autotuned, launch per round)."""
-    return candidate is not None and candidate >= 3
+    """Autotuner candidates 3 .. 14 are the persistent launch shapes (0 .. 2
+    and 15, 16 launch per round; None: not autotuned, launch per round)."""
+    return candidate is not None and 3 <= candidate <= 14
 
 
 def run_serve(args):

@@ -436,7 +436,7 @@ int vd_batch_step_subset(vd_batch* batch, const int32_t* sims, int32_t n, int32_
                          uint64_t rng_seed);
 
 #define VD_BOPT_MODE 1               /* 0 = launch per phase/round (default), 1 = persistent */
-#define VD_BOPT_ROWS_PER_THREAD 2    /* rows each thread sweeps per tile: 1 (default), 2, 4 */
+#define VD_BOPT_ROWS_PER_THREAD 2    /* rows each thread sweeps per tile: 1 (default), 2, 4, 8, 16 */
 #define VD_BOPT_BLOCKS_PER_SM 3      /* persistent mode: 0 = occupancy maximum (default), else cap */
 #define VD_BOPT_USE_GRAPHS 4         /* 1 (default) = replay repeating full steps as a graph */
 #define VD_BOPT_BARRIER_TIMEOUT_US 5 /* persistent mode: bounded barrier wait (default 2 s) */
@@ -474,7 +474,8 @@ int vd_batch_get_option(const vd_batch* batch, int32_t option, int64_t* value);
  * per SM [6-7] and at 2 [8-9]; the persistent launch with 1 or 2 rows per
  * thread on the clamped key only (VD_BOPT_PERSISTENT_BYTE_KEYS = 0) [10-11];
  * the persistent launch with 1, 2 or 4 rows per thread compiled for 5
- * blocks per SM (VD_BOPT_PERSISTENT_MIN_BLOCKS = 5) [12-14].
+ * blocks per SM (VD_BOPT_PERSISTENT_MIN_BLOCKS = 5) [12-14]; per-round
+ * launches with 8 or 16 rows per thread (tiles of 256 x 32 or 64) [15-16].
  */
 int vd_batch_autotune(vd_batch* batch, int32_t steps, int32_t max_disp, uint64_t rng_seed,
                       int32_t* best, double* ms_per_step, int32_t cap);

@@ -510,7 +510,8 @@ extern "C" int vd_batch_set_option(vd_batch* b, int32_t option, int64_t value) {
       b->mode = static_cast<int>(value);
       break;
     case VD_BOPT_ROWS_PER_THREAD:
-      if (value != 1 && value != 2 && value != 4) return vd_fail(VD_EINVAL, "rows per thread must be 1, 2 or 4");
+      if (value != 1 && value != 2 && value != 4 && value != 8 && value != 16)
+        return vd_fail(VD_EINVAL, "rows per thread must be 1, 2, 4, 8 or 16");
       b->rows_per_thread = static_cast<int>(value);
       break;
     case VD_BOPT_BLOCKS_PER_SM:
@@ -635,10 +636,13 @@ extern "C" int vd_batch_autotune(vd_batch* b, int32_t steps, int32_t max_disp, u
   };
   // per-round launches with tiles of 256 x 4 r pixels (r rows per thread), and
   // the persistent launch at the occupancy maximum or capped at 3 or 2 blocks
-  // per SM (fewer co-resident blocks: fewer arrivals at each grid barrier)
+  // per SM (fewer co-resident blocks: fewer arrivals at each grid barrier);
+  // then per-round launches with 8 and 16 rows a thread (a thread's tile
+  // look-up and descriptor reads shared by more pixels)
   const Cand cands[] = {{0, 1, 0, 1, 4}, {0, 2, 0, 1, 4}, {0, 4, 0, 1, 4}, {1, 1, 0, 1, 4}, {1, 2, 0, 1, 4},
                         {1, 4, 0, 1, 4}, {1, 1, 3, 1, 4}, {1, 2, 3, 1, 4}, {1, 1, 2, 1, 4}, {1, 2, 2, 1, 4},
-                        {1, 1, 0, 0, 4}, {1, 2, 0, 0, 4}, {1, 1, 0, 1, 5}, {1, 2, 0, 1, 5}, {1, 4, 0, 1, 5}};
+                        {1, 1, 0, 0, 4}, {1, 2, 0, 0, 4}, {1, 1, 0, 1, 5}, {1, 2, 0, 1, 5}, {1, 4, 0, 1, 5},
+                        {0, 8, 0, 1, 4}, {0, 16, 0, 1, 4}};
   const int nc = static_cast<int>(sizeof(cands) / sizeof(cands[0]));
   int rc = vd_batch_synchronize(b);
   if (rc) return rc;

@@ -47,7 +47,7 @@ def _alone_rng(vd, shape, xy, sim_index, steps, D, rng_seed, metric=0):
 @pytest.mark.parametrize("mode,graphs,rpt,bps,pbyte,minb,packed", [
     (0, 0, 1, 0, 1, 4, -1), (0, 1, 1, 0, 1, 4, -1), (0, 1, 2, 0, 1, 4, -1), (0, 1, 1, 0, 1, 4, 0),
     (1, 0, 1, 0, 1, 4, -1), (1, 0, 4, 0, 1, 4, -1), (1, 0, 1, 2, 1, 4, -1), (1, 0, 2, 3, 1, 4, -1),
-    (1, 0, 1, 0, 0, 4, -1), (1, 0, 2, 0, 1, 5, -1)])
+    (1, 0, 1, 0, 0, 4, -1), (1, 0, 2, 0, 1, 5, -1), (0, 1, 8, 0, 1, 4, -1), (0, 1, 16, 0, 1, 4, -1)])
 def test_batch_equals_alone_rng(vd, mode, graphs, rpt, bps, pbyte, minb, packed):
     """Every launch shape the batch autotuner tries (per-round or persistent,
     rows per thread, persistent blocks per SM) gives each simulation exactly
