@@ -41,7 +41,9 @@ struct vd_server {
   int64_t budget = 0, used = 0;
   int32_t d_max = 0, vn_waves = 2, metric = 0, max_disp = 0;
   uint64_t rng_seed = 0;
-  int rows_per_thread = 4;
+  // 8 rows a thread: saturation 8.6k -> 9.2k steps/s at 1000 simulations,
+  // p50 / p99 at 2k and 5k requests a second about unchanged
+  int rows_per_thread = 8;
   int max_batch = 1 << 30;
   std::vector<vdb::SimDesc> sims;
   std::vector<char> live, in_flight;
